@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 adaptive-conditioning conic solver.
+
+One step = one complete solve (Algorithm 2 from x = z = e to every relative
+KKT residual <= 1e-6) of the large sparse LP: m = 200,000 constraints,
+n = 1,000,000 variables, 10 nonzeros per column with N(0,1) values, rows
+scaled by 10^U[-2,2], planted optimum with 30% of x* positive, conditioning
+schedule L = {300, 400, ...}, t = 9.2, mu = 1.  The matrix (A and A' in FP32
+and FP64, about 0.6 GB) is larger than L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one solve per rank per
+step, no collective on the data path): value = solves of all ranks / max time.
+The reference arm times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload and extrapolates to solves/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at 1e-6 KKT resid"
+UNIT = "solves/s"
+TOL = 1e-6
+MAX_ITER = 5000
+# iterations the FP64 oracle needs for this instance to reach 1e-6 (run to
+# completion once on the x86 host; see the CPU-baseline notes of the design doc)
+ORACLE_ITERS_LARGE_LP = 310
+
+WORKLOADS = {
+    "large_lp": dict(desc="LP m=200000 n=1000000 nnz=1e7 (10/col, N(0,1), row scales 10^U[-2,2], 30% x* > 0)",
+                     settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
+    "socp": dict(desc="SOCP 20000 Lorentz cones dims U{3..64} + 100000 orthant, m=150000, 8 nnz/col",
+                 settings=dict(cond_first=200, cond_period=100, t=1.7, mu=1.0)),
+    "small_lp": dict(desc="LP m=200 n=500 5% density, |supp x*|=150",
+                     settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
+}
+
+
+def make_instance(name: str):
+    from paper_2103_00736_gb300 import instances as I
+    if name == "large_lp":
+        return I.large_lp()
+    if name == "socp":
+        return I.socp()
+    if name == "small_lp":
+        return I.small_lp()
+    raise ValueError(name)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic byte model (per pass; nnz = true nonzeros, FP32 CG, FP64 outer)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(m: int, n: int, nnz: int, counters, iters: int) -> float:
+    n_cg_A, n_cg_AT, n64_A, n64_AT, n_cond, n_chk = [int(v) for v in counters]
+    b = 0.0
+    b += n_cg_AT * (8.0 * nnz + 4 * m + 8 * n)          # t = O^2 A'u: val+col, u gathered, O2 in, t out
+    b += n_cg_A * (8.0 * nnz + 4 * n + 8 * m)           # au = A t: val+col, t gathered, au out, u in
+    b += n_cg_A * 52.0 * m                               # CG vector step (p, sv, r r/w; au, jinv in; u out; w FP64 r/w)
+    b += n64_A * (12.0 * nnz + 8 * n + 20 * m)           # FP64 passes over A (rhs, b_tilde, residual)
+    b += n64_AT * (12.0 * nnz + 8 * m + 48 * n)          # FP64 passes over A' (update, q refresh, residual)
+    b += iters * 40.0 * n                                # abs_K: s, q, O in; p, g out
+    b += n_cond * 100.0 * n                              # rescaling: o, O, c_hat, s recast
+    return b
+
+
+# ---------------------------------------------------------------------------
+# clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(workload: str, iters: int) -> dict:
+    """Time the FP64 oracle on the workload: the first iteration (includes the
+    l = 1 conditioning, i.e. the factor/solve set-up) and `iters` further ones."""
+    import numpy as np  # noqa: F401
+    from oracle import alg
+    inst = make_instance(workload)
+    A = inst.to_scipy()
+    st = WORKLOADS[workload]["settings"]
+    L = alg.Schedule(first=st["cond_first"], period=st["cond_period"])
+    stamps = []
+    t0 = time.perf_counter()
+
+    def hook(l, s, p, O, d):
+        stamps.append(time.perf_counter())
+
+    alg.algorithm2(A, inst.b, inst.c, inst.n_orth, inst.soc_dims, mu=st["mu"], t=st["t"], L=L,
+                   max_iter=1 + iters, tol=0.0, check_every=10 ** 9, on_iter=hook)
+    first = stamps[0] - t0
+    per_iter = (stamps[-1] - stamps[0]) / max(1, len(stamps) - 1)
+    return {"first_iter_s": first, "per_iter_s": per_iter, "iters": len(stamps)}
+
+
+def run_cpu_sample_subprocess(workload: str, iters: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
+                        "--cpu-iters", str(iters)], capture_output=True, text=True, env=env, timeout=1800)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
+
+
+def oracle_solves_per_s(sample: dict, workload: str) -> tuple[float, str]:
+    n_it = ORACLE_ITERS_LARGE_LP if workload == "large_lp" else None
+    if n_it is None:
+        n_it = 1000
+    t_solve = sample["first_iter_s"] + (n_it - 1) * sample["per_iter_s"]
+    return 1.0 / t_solve, (f"FP64 oracle, 1 thread: first iteration {sample['first_iter_s']:.1f} s, "
+                           f"{sample['iters'] - 1} more at {sample['per_iter_s']:.2f} s each, "
+                           f"extrapolated to the {n_it} iterations the oracle needs for this instance")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def gpu_arm(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2103_00736_gb300 import capi
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    inst = make_instance(args.workload)
+    wl = WORKLOADS[args.workload]
+    # a dedicated stream: the library launches on it and the events below time it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    settings = capi.acs_settings_default(cuda_stream=stream.cuda_stream, device=local, **wl["settings"])
+    h = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
+                                inst.n_orth, inst.soc_dims, settings)
+    info = capi.acs_problem_info(h)
+
+    def solve_checked():
+        capi.acs_solve_async(h, TOL, MAX_ITER)
+
+    for _ in range(args.warmup):
+        solve_checked()
+    st, iters, res = capi.acs_get_residuals(h)
+    if st != capi.SOLVED:
+        raise RuntimeError(f"warm-up solve did not converge: {capi.acs_status_string(st)} {res}")
+    counters = capi.acs_debug_counters(h)
+    launch_ms_warm = capi.acs_last_launch_ms(h)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    ev0.record(stream)
+    for k in range(args.steps):
+        step_ev[k][0].record(stream)
+        solve_checked()
+        step_ev[k][1].record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    launch_ms = capi.acs_last_launch_ms(h)
+    st, iters, res = capi.acs_get_residuals(h)
+    if st != capi.SOLVED:
+        raise RuntimeError(f"timed solve did not converge: {capi.acs_status_string(st)}")
+    if pg:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # roofline of the persistent iteration kernel (the only kernel of a solve
+    # besides three tiny initialisation launches)
+    alg_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    traffic = args.traffic if args.traffic is not None else None
+
+    # end to end through the C ABI with host buffers, every step: upload,
+    # solve, read back x, y, s
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t_e2e = 0.0
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            h2 = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b,
+                                         inst.c, inst.n_orth, inst.soc_dims,
+                                         capi.acs_settings_default(device=local, **wl["settings"]))
+            st2 = capi.acs_solve(h2, TOL, MAX_ITER)
+            out = capi.acs_get(h2, inst.m, inst.n)
+            capi.acs_problem_destroy(h2)
+            t_e2e += time.perf_counter() - t0
+            if st2 != capi.SOLVED:
+                raise RuntimeError("e2e solve did not converge")
+        pa, pat = info["padded_A"], info["padded_AT"]
+        h2d = 16 * (pa + pat) + 8 * (inst.m + inst.n) + 4 * (len(inst.soc_dims) + 1)
+        h2d += 4 * ((inst.m + inst.n) // 8 + 4)          # slice tables (upper bound)
+        d2h = 8 * (2 * inst.n + inst.m) + 256
+        if pg:
+            t = torch.tensor([t_e2e], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    capi.acs_problem_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = run_cpu_sample_subprocess(args.workload, args.cpu_iters)
+        v, desc = oracle_solves_per_s(sample, args.workload)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "m": inst.m, "n": inst.n,
+                       "nnz": inst.nnz, "tol": TOL, "iterations": iters, "cg_iterations": int(res[6]),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (A and A' in FP32+FP64 ~0.6 GB)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "kernel": "iter_kernel<float>",
+                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
+                         "step_ms_median": statistics.median(step_ms)},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def reference_arm(args) -> None:
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    sample = run_cpu_sample_subprocess(args.workload, max(1, args.steps))
+    v, desc = oracle_solves_per_s(sample, args.workload)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "tol": TOL},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_lp", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch from an ncu capture of the same kernel build")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.workload, args.cpu_iters)), flush=True)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * acs.h -- C ABI of the GB300 adaptive-conditioning conic solver.
+ *
+ * Solves  min c'x  s.t.  Ax = b,  x in K   (arXiv 2103.00736, Section II, Eq. (1))
+ * and its dual  max b'y  s.t.  A'y + z = c,  z in K  (Eq. (2)),
+ * where K is a product of Lorentz cones.  The nonnegative orthant is the
+ * product of size-1 Lorentz cones; in this ABI its coordinates come first,
+ * [0, n_orthant), followed by the cones of size >= 2 in the order given.
+ *
+ * The method is Algorithm 2 of the paper (Algorithm 1 plus adaptive
+ * conditioning, Section IV) run on one GPU: every iteration applies the
+ * cone reflection abs_K (Definition 1), the reflection through the range of
+ * (A O)' by a Jacobi-preconditioned conjugate-gradient solve with
+ * M = (A O)(A O)', the splitting update, and at the iterations of the
+ * schedule L the diagonal rescaling O of Algorithm 2, steps 5-14.
+ *
+ * Conventions
+ *  - All pointers passed to acs_problem_create / acs_get / acs_get_state /
+ *    acs_set_state are HOST pointers owned by the caller; they are read or
+ *    written only during the call.  The library copies the data to the
+ *    device and owns every device buffer it allocates until
+ *    acs_problem_destroy.
+ *  - A handle is not thread-safe: use one handle per host thread, or the
+ *    batch API.
+ *  - Return codes: 0 = ACS_SOLVED; positive values are terminal statuses
+ *    whose results are still valid (ACS_MAX_ITER); negative values are
+ *    errors.  No error path traps the GPU: device-side failures (a grid
+ *    barrier that times out, a non-finite residual, a failed CG) are
+ *    reported through these codes and leave the CUDA context usable.
+ */
+#ifndef ACS_H
+#define ACS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ACS_SOLVED = 0,          /* all relative KKT residuals <= tol                   */
+    ACS_MAX_ITER = 1,        /* iteration limit reached; results/residuals valid    */
+    ACS_ERR_ARG = -1,        /* bad argument (NULL pointer, size <= 0, bad setting) */
+    ACS_ERR_CSR = -2,        /* malformed CSR: row_ptr not monotone, col out of
+                                range or unsorted/duplicate within a row, empty row */
+    ACS_ERR_CONES = -3,      /* cone sizes do not add up to n, or a size < 2        */
+    ACS_ERR_OOM = -4,        /* device allocation failed                            */
+    ACS_ERR_FACTOR = -5,     /* M = (AO)(AO)' not positive definite (CG breakdown)  */
+    ACS_ERR_DEVICE_TIMEOUT = -6, /* a device-side grid barrier did not complete   */
+    ACS_ERR_NUMERICAL = -7,  /* NaN or Inf in the iterates or residuals             */
+    ACS_ERR_CUDA = -8,       /* a CUDA runtime call failed                          */
+    ACS_ERR_LIMIT = -9       /* a size exceeds a fixed limit of the entry point     */
+};
+
+enum { ACS_PREC_MIXED = 0, ACS_PREC_FP64 = 2 };
+
+typedef struct acs_problem acs_problem;
+
+typedef struct {
+    double mu;               /* splitting parameter mu > 0 (Algorithm 1 Require); default 1   */
+    double t;                /* conditioning cap t > 0 (Algorithm 2 step 11): the spread
+                                max(O)/min(O) is at most e^t; default 9.2 (LP experiments)     */
+    int32_t cond_first;      /* schedule L = {cond_first, cond_first + cond_period, ...}
+                                plus cond_list; 0 disables the periodic part; l = 1 always
+                                conditions (Algorithm 2 step 4); default 300                   */
+    int32_t cond_period;     /* default 100                                                    */
+    const int32_t* cond_list;/* extra conditioning iterations (host, copied), may be NULL    */
+    int32_t n_cond_list;
+    int32_t check_every;     /* KKT residual check period in iterations; default 10           */
+    int32_t precision;       /* ACS_PREC_MIXED (default): FP64 outer iteration and residuals,
+                                projection solve by an FP32 correction CG (mixed-precision
+                                refinement), handed over to an FP64 correction CG for the
+                                rest of the solve if the FP32 one cannot reach the accuracy
+                                the iteration needs; ACS_PREC_FP64: FP64 correction CG      */
+    double cg_eta;           /* inexact projection: CG stops once its error estimate
+                                sqrt(r' J^-1 r) <= eta * ||s_l - s_{l-1}||, eta starting at
+                                cg_eta (default 1e-2) and shrunk tenfold whenever the step
+                                norm grows between rescalings; iterations that rescale
+                                solve to the floors                                            */
+    double cg_tol;           /* ... or <= cg_tol * ||s_l||; default 1e-12                     */
+    int32_t cg_max_iter;     /* CG iterations per correction solve; default 500               */
+    int32_t cg_refine;       /* correction solves per iteration, each from a fresh FP64
+                                residual (mixed-precision refinement rounds); default 1, <= 8  */
+    void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream        */
+    int32_t device;          /* CUDA device ordinal; default 0                                 */
+} acs_settings;
+
+/* Fill *s with the defaults listed above.  Returns ACS_SOLVED or ACS_ERR_ARG. */
+int acs_settings_default(acs_settings* s);
+
+/*
+ * Create a problem on the device.  Section II, Eq. (1).
+ *   m, n        : A is m x n, m >= 1, n >= 1.
+ *   row_ptr     : int64[m+1], row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz < 2^31.
+ *   col         : int32[nnz], column indices in [0, n), strictly increasing in each row.
+ *   val         : double[nnz].
+ *   b           : double[m];  c : double[n].
+ *   n_orthant   : number of leading nonnegative-orthant coordinates (>= 0).
+ *   n_soc, soc_dims : Lorentz cones of sizes soc_dims[i] >= 2 following the orthant;
+ *                 n_orthant + sum(soc_dims) must equal n.
+ *   settings    : may be NULL for the defaults.
+ *   out         : receives the handle (NULL on failure).
+ * Every row of A must be nonempty (A of full row rank is required by the
+ * pseudoinverse of Algorithm 1 step 2; rank deficiency surfaces as
+ * ACS_ERR_FACTOR in acs_solve).
+ * Errors: ACS_ERR_ARG, ACS_ERR_CSR, ACS_ERR_CONES, ACS_ERR_OOM, ACS_ERR_CUDA.
+ */
+int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col,
+                       const double* val, const double* b, const double* c,
+                       int32_t n_orthant, int32_t n_soc, const int32_t* soc_dims,
+                       const acs_settings* settings, acs_problem** out);
+
+/*
+ * Run Algorithm 2 from the initial point x = z = e (the cone identity) until
+ * every relative KKT residual is <= tol (ACS_SOLVED) or max_iter iterations
+ * have run (ACS_MAX_ITER).  tol = 0 runs exactly max_iter iterations.
+ * Residuals (all Euclidean, computed in FP64 with the FP64 copy of A):
+ *   r_p   = ||Ax - b|| / (1 + ||b||)
+ *   r_d   = ||A'y + z - c|| / (1 + ||c||)
+ *   r_gap = |c'x - b'y| / (1 + |c'x| + |b'y|)
+ *   r_cone= max(dist(x,K), dist(z,K)) / (1 + max(||x||, ||z||))
+ * x, z are the iterates of Algorithm 2 steps 20-21 and y = w / mu, the
+ * multiplier of the projection solve.  Blocks until done.
+ */
+int acs_solve(acs_problem* p, double tol, int32_t max_iter);
+
+/* Same as acs_solve but returns as soon as the work is queued on the
+ * handle's stream (ACS_SOLVED means "queued"); acs_get waits for it. */
+int acs_solve_async(acs_problem* p, double tol, int32_t max_iter);
+
+/*
+ * Copy results to host buffers (any may be NULL): x[n], y[m], s[n] (the dual
+ * slack, z of the paper), *iters, residuals[8] = {r_p, r_d, r_gap, r_cone,
+ * obj_p, obj_d, CG iterations in total, iteration at which a mixed-precision
+ * solve handed its correction solve over to FP64 (0 = never)}.  Waits for queued
+ * work.  Returns the status of the last solve (>= 0) or an error.
+ */
+int acs_get(acs_problem* p, double* x, double* y, double* s, int32_t* iters, double* residuals);
+
+/*
+ * Checkpoint / warm start of the iteration state: s_dr[n] is the splitting
+ * variable s of Algorithm 2 in the current scaled space, O[n] the diagonal
+ * of O, w[m] the projection multiplier (mu * y), *l the iteration counter,
+ * step[3] = {||s_l - s_{l-1}||, ||s_l||, current inexactness factor} used by
+ * the inexact-projection rule (may be NULL: the next iteration then solves
+ * to the CG floors and the factor restarts at cg_eta).
+ * acs_set_state makes the next acs_solve continue from this state instead of
+ * x = z = e (Algorithm 2 step 14 keeps progress across rescalings the same
+ * way); a state taken after l iterations and resumed reproduces the
+ * uninterrupted run.  All pointers are host pointers owned by the caller.
+ */
+int acs_get_state(acs_problem* p, double* s_dr, double* O, double* w, int32_t* l, double* step);
+int acs_set_state(acs_problem* p, const double* s_dr, const double* O, const double* w, int32_t l,
+                  const double* step);
+
+/* Release every device buffer of the handle.  NULL is ignored. */
+void acs_problem_destroy(acs_problem* p);
+
+/* Static string for a status code. */
+const char* acs_status_string(int status);
+
+/* Diagnostics.  acs_debug_counters: out6 = {A passes, A' passes, FP64 A passes,
+ * FP64 A' passes, conditionings, FP64 iterations} of the last solve (the
+ * benchmark's algorithmic-byte model counts matrix passes with these).
+ * acs_problem_info: out8 = {m, n, nnz, stored entries of A and of A' after padding,
+ * CTAs of the FP32 launch, CTAs of the FP64 launch, threads per CTA}. */
+int acs_debug_counters(acs_problem* p, long long* out6);
+/* Device time (ms) of the last persistent iteration launch, from CUDA events
+ * recorded on the handle's stream around that launch; waits for it. */
+int acs_last_launch_ms(acs_problem* p, double* ms);
+/* Time of each phase of the persistent kernel in the last solve (ms, from
+ * the device's global timer, barrier wait included) and how often it ran, in
+ * the order: rescale-o, rescale-apply, b_tilde, q-refresh, abs_K, CG-rhs,
+ * CG A' pass, CG A pass, CG vector step, update, KKT.  n >= 11.  Returns the
+ * number of phases written or an error. */
+int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t n);
+/* Mean time (ns) of one grid-wide reduce-and-barrier of the persistent
+ * kernel's launch shape, over n back-to-back barriers. */
+int acs_debug_barrier_ns(acs_problem* p, int32_t n, double* ns);
+int acs_problem_info(acs_problem* p, int32_t* out8);
+
+/* Library version string. */
+const char* acs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACS_H */

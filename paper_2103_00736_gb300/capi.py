@@ -1,0 +1,280 @@
+"""ctypes binding of the C ABI in include/acs.h (argument marshalling only).
+
+Every function keeps the C name.  The library is loaded from this package
+directory; if it is missing, the first call raises -- there is no CPU
+fallback.  All arrays passed in or returned are host numpy arrays; the
+library copies them to and from the device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacs.so")
+
+SOLVED, MAX_ITER = 0, 1
+ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
+ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
+PREC_MIXED, PREC_FP64 = 0, 2
+
+_lib = None
+
+
+class acs_settings(C.Structure):
+    _fields_ = [
+        ("mu", C.c_double),
+        ("t", C.c_double),
+        ("cond_first", C.c_int32),
+        ("cond_period", C.c_int32),
+        ("cond_list", C.POINTER(C.c_int32)),
+        ("n_cond_list", C.c_int32),
+        ("check_every", C.c_int32),
+        ("precision", C.c_int32),
+        ("cg_eta", C.c_double),
+        ("cg_tol", C.c_double),
+        ("cg_max_iter", C.c_int32),
+        ("cg_refine", C.c_int32),
+        ("cuda_stream", C.c_void_p),
+        ("device", C.c_int32),
+    ]
+
+
+class AcsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {acs_status_string(code)} ({code})")
+        self.code = code
+
+
+def lib():
+    """The loaded libacs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_2103_00736_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        L.acs_settings_default.argtypes = [C.POINTER(acs_settings)]
+        L.acs_problem_create.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, dp, dp,
+                                         C.c_int32, C.c_int32, ip, C.POINTER(acs_settings),
+                                         C.POINTER(P)]
+        L.acs_solve.argtypes = [P, C.c_double, C.c_int32]
+        L.acs_solve_async.argtypes = [P, C.c_double, C.c_int32]
+        L.acs_get.argtypes = [P, dp, dp, dp, ip, dp]
+        L.acs_get_state.argtypes = [P, dp, dp, dp, ip, dp]
+        L.acs_set_state.argtypes = [P, dp, dp, dp, C.c_int32, dp]
+        L.acs_problem_destroy.argtypes = [P]
+        L.acs_problem_destroy.restype = None
+        L.acs_status_string.argtypes = [C.c_int]
+        L.acs_status_string.restype = C.c_char_p
+        L.acs_version.restype = C.c_char_p
+        L.acs_debug_counters.argtypes = [P, C.POINTER(C.c_longlong)]
+        L.acs_problem_info.argtypes = [P, ip]
+        L.acs_last_launch_ms.argtypes = [P, dp]
+        L.acs_debug_barrier_ns.argtypes = [P, C.c_int32, dp]
+        L.acs_debug_phase_times.argtypes = [P, dp, C.POINTER(C.c_longlong), C.c_int32]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def acs_status_string(code: int) -> str:
+    return lib().acs_status_string(int(code)).decode()
+
+
+def acs_version() -> str:
+    return lib().acs_version().decode()
+
+
+def acs_settings_default(**overrides) -> acs_settings:
+    s = acs_settings()
+    rc = lib().acs_settings_default(C.byref(s))
+    if rc != 0:
+        raise AcsError(rc, "acs_settings_default")
+    cond_list = overrides.pop("cond_list", None)
+    for k, v in overrides.items():
+        if not hasattr(s, k):
+            raise KeyError(k)
+        setattr(s, k, v)
+    if cond_list is not None:
+        arr = np.ascontiguousarray(cond_list, dtype=np.int32)
+        s._cond_list_keep = arr      # keep alive until problem creation copies it
+        s.cond_list = _ptr(arr, C.c_int32)
+        s.n_cond_list = arr.size
+    return s
+
+
+def acs_problem_create(m, n, row_ptr, col, val, b, c, n_orthant, soc_dims=(), settings=None):
+    """Returns an opaque handle (int); raises AcsError on failure."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    dims = np.ascontiguousarray(soc_dims, dtype=np.int32)
+    h = C.c_void_p()
+    rc = lib().acs_problem_create(int(m), int(n), _ptr(row_ptr, C.c_int64), _ptr(col, C.c_int32),
+                                  _ptr(val, C.c_double), _ptr(b, C.c_double), _ptr(c, C.c_double),
+                                  int(n_orthant), int(dims.size), _ptr(dims, C.c_int32),
+                                  C.byref(settings) if settings is not None else None, C.byref(h))
+    if rc != 0:
+        raise AcsError(rc, "acs_problem_create")
+    return h.value
+
+
+def acs_solve(h, tol: float, max_iter: int) -> int:
+    return lib().acs_solve(C.c_void_p(h), float(tol), int(max_iter))
+
+
+def acs_solve_async(h, tol: float, max_iter: int) -> int:
+    rc = lib().acs_solve_async(C.c_void_p(h), float(tol), int(max_iter))
+    if rc < 0:
+        raise AcsError(rc, "acs_solve_async")
+    return rc
+
+
+def acs_get(h, m: int, n: int):
+    """(status, x, y, s, iters, residuals[8])."""
+    x = np.empty(n)
+    y = np.empty(m)
+    s = np.empty(n)
+    it = C.c_int32()
+    res = np.empty(8)
+    rc = lib().acs_get(C.c_void_p(h), _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(s, C.c_double),
+                       C.byref(it), _ptr(res, C.c_double))
+    return rc, x, y, s, it.value, res
+
+
+def acs_get_residuals(h):
+    """(status, iters, residuals[8]) without copying the vectors."""
+    it = C.c_int32()
+    res = np.empty(8)
+    rc = lib().acs_get(C.c_void_p(h), None, None, None, C.byref(it), _ptr(res, C.c_double))
+    return rc, it.value, res
+
+
+def acs_get_state(h, m: int, n: int):
+    s = np.empty(n)
+    O = np.empty(n)
+    w = np.empty(m)
+    l = C.c_int32()
+    step = np.empty(3)
+    rc = lib().acs_get_state(C.c_void_p(h), _ptr(s, C.c_double), _ptr(O, C.c_double),
+                             _ptr(w, C.c_double), C.byref(l), _ptr(step, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_get_state")
+    return s, O, w, l.value, step
+
+
+def acs_set_state(h, s, O, w, l: int, step=None):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    O = np.ascontiguousarray(O, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    st = None if step is None else np.ascontiguousarray(step, dtype=np.float64)
+    rc = lib().acs_set_state(C.c_void_p(h), _ptr(s, C.c_double), _ptr(O, C.c_double),
+                             _ptr(w, C.c_double), int(l), _ptr(st, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_set_state")
+
+
+def acs_problem_destroy(h) -> None:
+    if h:
+        lib().acs_problem_destroy(C.c_void_p(h))
+
+
+def acs_debug_counters(h) -> np.ndarray:
+    out = np.zeros(6, dtype=np.int64)
+    rc = lib().acs_debug_counters(C.c_void_p(h), out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_counters")
+    return out
+
+
+PHASES = ("rescale_o", "rescale_apply", "b_tilde", "q_refresh", "abs_K", "cg_rhs", "cg_At",
+          "cg_A", "cg_vec", "update", "kkt")
+
+
+def acs_debug_phase_times(h) -> dict:
+    ms = np.zeros(16)
+    cnt = np.zeros(16, dtype=np.int64)
+    rc = lib().acs_debug_phase_times(C.c_void_p(h), _ptr(ms, C.c_double),
+                                     cnt.ctypes.data_as(C.POINTER(C.c_longlong)), 16)
+    if rc < 0:
+        raise AcsError(rc, "acs_debug_phase_times")
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PHASES)}
+
+
+def acs_debug_barrier_ns(h, n: int = 1000) -> float:
+    ns = C.c_double()
+    rc = lib().acs_debug_barrier_ns(C.c_void_p(h), int(n), C.byref(ns))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_barrier_ns")
+    return ns.value
+
+
+def acs_last_launch_ms(h) -> float:
+    ms = C.c_double()
+    rc = lib().acs_last_launch_ms(C.c_void_p(h), C.byref(ms))
+    if rc != 0:
+        raise AcsError(rc, "acs_last_launch_ms")
+    return ms.value
+
+
+def acs_problem_info(h) -> dict:
+    out = np.zeros(8, dtype=np.int32)
+    rc = lib().acs_problem_info(C.c_void_p(h), _ptr(out, C.c_int32))
+    if rc != 0:
+        raise AcsError(rc, "acs_problem_info")
+    keys = ("m", "n", "nnz", "padded_A", "padded_AT", "grid32", "grid64", "threads")
+    return dict(zip(keys, out.tolist()))
+
+
+class Solver:
+    """Convenience owner of one problem handle."""
+
+    def __init__(self, inst=None, *, m=None, n=None, row_ptr=None, col=None, val=None, b=None,
+                 c=None, n_orth=None, soc_dims=(), settings=None, **overrides):
+        if inst is not None:
+            m, n, row_ptr, col, val, b, c = inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c
+            n_orth, soc_dims = inst.n_orth, inst.soc_dims
+        if settings is None:
+            settings = acs_settings_default(**overrides)
+        self.m, self.n = int(m), int(n)
+        self.h = acs_problem_create(m, n, row_ptr, col, val, b, c, n_orth, soc_dims, settings)
+
+    def solve(self, tol=1e-6, max_iter=10000) -> int:
+        return acs_solve(self.h, tol, max_iter)
+
+    def solve_async(self, tol=1e-6, max_iter=10000) -> int:
+        return acs_solve_async(self.h, tol, max_iter)
+
+    def get(self):
+        return acs_get(self.h, self.m, self.n)
+
+    def residuals(self):
+        return acs_get_residuals(self.h)
+
+    def close(self):
+        acs_problem_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass

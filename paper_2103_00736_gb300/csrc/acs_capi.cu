@@ -1,0 +1,505 @@
+// C ABI of the conic solver: problem creation (validation, transpose, upload),
+// solve, result and state transfer, destruction.  See include/acs.h.
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <climits>
+#include <new>
+#include <vector>
+
+#include "acs_internal.cuh"
+
+using acs::Problem;
+
+namespace {
+
+constexpr const char* kVersion = "acs-gb300 0.1 (sm_103a)";
+
+template <typename T>
+int dalloc(Problem* P, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACS_ERR_OOM;
+    }
+    P->allocations.push_back(p);
+    *ptr = static_cast<T*>(p);
+    return ACS_SOLVED;
+}
+
+template <typename T>
+int upload(Problem* P, T* dst, const T* src, size_t count) {
+    if (count == 0) return ACS_SOLVED;
+    if (cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    return ACS_SOLVED;
+}
+
+// Host image of a sliced-ELLPACK matrix with G lanes per row (layout in
+// acs_internal.cuh).
+struct HostSell {
+    int nrows = 0, nslices = 0, g = 1;
+    std::vector<int> sptr, slen, col;
+    std::vector<double> val;
+};
+
+// Rows are given by (beg[r], end[r]) ranges into (cols, vals); padding
+// entries repeat column 0 with value 0.
+HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, const std::vector<long long>& end,
+                    const int* cols, const double* vals) {
+    HostSell H;
+    const int h = 32 / g;                     // rows per slice
+    H.nrows = nrows;
+    H.g = g;
+    H.nslices = (nrows + h - 1) / h;
+    H.sptr.assign(H.nslices + 1, 0);
+    H.slen.assign(H.nslices, 0);
+    long long total = 0;
+    for (int sl = 0; sl < H.nslices; ++sl) {
+        long long mx = 0;
+        for (int r = sl * h; r < std::min(nrows, sl * h + h); ++r) mx = std::max(mx, end[r] - beg[r]);
+        const long long chunks = (mx + g - 1) / g;
+        H.slen[sl] = (int)chunks;
+        H.sptr[sl] = (int)std::min<long long>(total, INT32_MAX);
+        total += 32 * chunks;
+    }
+    H.sptr[H.nslices] = (int)std::min<long long>(total, INT32_MAX);
+    if (total >= INT32_MAX) { H.col.clear(); H.nslices = -1; return H; }
+    H.col.assign(total, 0);
+    H.val.assign(total, 0.0);
+    for (int sl = 0; sl < H.nslices; ++sl)
+        for (int lr = 0; lr < h; ++lr) {
+            const int r = sl * h + lr;
+            if (r >= nrows) break;
+            long long k = 0;
+            for (long long e = beg[r]; e < end[r]; ++e, ++k) {
+                const long long idx = H.sptr[sl] + 32 * (k / g) + lr * g + (k % g);
+                H.col[idx] = cols[e];
+                H.val[idx] = vals[e];
+            }
+        }
+    return H;
+}
+
+// Lanes per row: enough slices for four per warp of the persistent grid (load
+// balance), but no more lanes than about half the average row length.
+int choose_g(long long nrows, long long nnz, long long warps) {
+    const double avg = nrows > 0 ? (double)nnz / (double)nrows : 1.0;
+    int g = 1;
+    while (g < 32 && (nrows * g) / 32 < 4 * warps && 2 * g <= avg) g *= 2;
+    return g;
+}
+
+int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
+    int* sptr = nullptr; int* slen = nullptr; int* col = nullptr;
+    float* v32 = nullptr; double* v64 = nullptr;
+    const size_t tot = H.col.size();
+    if (dalloc(P, &sptr, H.sptr.size()) || dalloc(P, &slen, H.slen.size()) || dalloc(P, &col, tot) ||
+        dalloc(P, &v32, tot) || dalloc(P, &v64, tot))
+        return ACS_ERR_OOM;
+    std::vector<float> f(tot);
+    for (size_t k = 0; k < tot; ++k) f[k] = (float)H.val[k];
+    int rc = 0;
+    rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
+    rc |= upload(P, slen, H.slen.data(), H.slen.size());
+    rc |= upload(P, col, H.col.data(), tot);
+    rc |= upload(P, v32, f.data(), tot);
+    rc |= upload(P, v64, H.val.data(), tot);
+    // the pageable source buffers are released when this function returns
+    if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
+    M.nrows = H.nrows; M.nslices = H.nslices; M.g = H.g;
+    M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64;
+    return ACS_SOLVED;
+}
+
+constexpr int kSortWindow = 2048;   // rows of A are sorted by length within windows of this size
+
+bool finite_all(const double* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+template <typename T>
+int alloc_inner(Problem* P, acs::Inner<T>& V) {
+    const int m = P->m, n = P->n;
+    int rc = 0;
+    rc |= dalloc(P, &V.r, m); rc |= dalloc(P, &V.u, m); rc |= dalloc(P, &V.p, m);
+    rc |= dalloc(P, &V.sv, m); rc |= dalloc(P, &V.au, m); rc |= dalloc(P, &V.t, n);
+    rc |= dalloc(P, &V.jinv, m); rc |= dalloc(P, &V.O2, n);
+    if (rc) return ACS_ERR_OOM;
+    // p and sv are multiplied by beta = 0 on the first CG step: keep them finite
+    if (cudaMemsetAsync(V.p, 0, sizeof(T) * m, P->stream) != cudaSuccess ||
+        cudaMemsetAsync(V.sv, 0, sizeof(T) * m, P->stream) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    return ACS_SOLVED;
+}
+int alloc_outer(Problem* P, acs::Outer& X) {
+    const int m = P->m, n = P->n;
+    int rc = 0;
+    rc |= dalloc(P, &X.s, n); rc |= dalloc(P, &X.p, n); rc |= dalloc(P, &X.g, n);
+    rc |= dalloc(P, &X.q, n); rc |= dalloc(P, &X.w, m); rc |= dalloc(P, &X.chat, n);
+    rc |= dalloc(P, &X.btil, m); rc |= dalloc(P, &X.O, n);
+    return rc ? ACS_ERR_OOM : ACS_SOLVED;
+}
+
+void free_all(Problem* P) {
+    if (!P) return;
+    for (void* p : P->allocations) cudaFree(p);
+    P->allocations.clear();
+    if (P->ctl_host) cudaFreeHost(P->ctl_host);
+    P->ctl_host = nullptr;
+    for (auto& ev : P->ev_launch) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+    }
+    if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
+    P->stream = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int acs_settings_default(acs_settings* s) {
+    if (!s) return ACS_ERR_ARG;
+    memset(s, 0, sizeof(*s));
+    s->mu = 1.0;
+    s->t = 9.2;
+    s->cond_first = 300;
+    s->cond_period = 100;
+    s->cond_list = nullptr;
+    s->n_cond_list = 0;
+    s->check_every = 10;
+    s->precision = ACS_PREC_MIXED;
+    s->cg_eta = 1e-2;
+    s->cg_tol = 1e-12;
+    s->cg_max_iter = 500;
+    s->cg_refine = 1;
+    s->cuda_stream = nullptr;
+    s->device = 0;
+    return ACS_SOLVED;
+}
+
+const char* acs_status_string(int st) {
+    switch (st) {
+        case ACS_SOLVED: return "solved";
+        case ACS_MAX_ITER: return "iteration limit reached";
+        case ACS_ERR_ARG: return "invalid argument";
+        case ACS_ERR_CSR: return "malformed CSR matrix";
+        case ACS_ERR_CONES: return "invalid cone sizes";
+        case ACS_ERR_OOM: return "device out of memory";
+        case ACS_ERR_FACTOR: return "projection operator not positive definite";
+        case ACS_ERR_DEVICE_TIMEOUT: return "device barrier timed out";
+        case ACS_ERR_NUMERICAL: return "non-finite iterate or residual";
+        case ACS_ERR_CUDA: return "CUDA runtime error";
+        case ACS_ERR_LIMIT: return "size exceeds the entry point's limit";
+        default: return "unknown status";
+    }
+}
+
+const char* acs_version(void) { return kVersion; }
+
+int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col,
+                       const double* val, const double* b, const double* c,
+                       int32_t n_orthant, int32_t n_soc, const int32_t* soc_dims,
+                       const acs_settings* settings, acs_problem** out) {
+    if (!out) return ACS_ERR_ARG;
+    *out = nullptr;
+    if (m <= 0 || n <= 0 || !row_ptr || !b || !c) return ACS_ERR_ARG;
+    acs_settings set;
+    if (settings) set = *settings; else acs_settings_default(&set);
+    if (!(set.mu > 0) || !(set.t > 0) || set.check_every <= 0 || set.cg_max_iter <= 0 || set.cg_refine <= 0 || set.cg_refine > 8 ||
+        !(set.cg_tol >= 0) || !(set.cg_eta >= 0) || set.cond_period < 0 || set.cond_first < 0 || set.n_cond_list < 0 ||
+        (set.n_cond_list > 0 && !set.cond_list) ||
+        (set.precision != ACS_PREC_MIXED && set.precision != ACS_PREC_FP64))
+        return ACS_ERR_ARG;
+    // CSR
+    if (row_ptr[0] != 0) return ACS_ERR_CSR;
+    for (int i = 0; i < m; ++i)
+        if (row_ptr[i + 1] <= row_ptr[i]) return ACS_ERR_CSR;    // non-monotone or empty row
+    const int64_t nnz64 = row_ptr[m];
+    if (nnz64 <= 0 || nnz64 >= (int64_t)1 << 31) return ACS_ERR_CSR;
+    if (!col || !val) return ACS_ERR_ARG;
+    const int nnz = (int)nnz64;
+    for (int i = 0; i < m; ++i) {
+        int prev = -1;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int j = col[k];
+            if (j < 0 || j >= n || j <= prev) return ACS_ERR_CSR;
+            prev = j;
+        }
+    }
+    if (!finite_all(val, nnz) || !finite_all(b, m) || !finite_all(c, n)) return ACS_ERR_ARG;
+    // cones
+    if (n_orthant < 0 || n_soc < 0 || (n_soc > 0 && !soc_dims)) return ACS_ERR_CONES;
+    int64_t tot = n_orthant;
+    for (int i = 0; i < n_soc; ++i) {
+        if (soc_dims[i] < 2) return ACS_ERR_CONES;
+        tot += soc_dims[i];
+    }
+    if (tot != n) return ACS_ERR_CONES;
+
+    Problem* P = new (std::nothrow) Problem();
+    if (!P) return ACS_ERR_OOM;
+    P->m = m; P->n = n; P->nnz = nnz; P->n_orth = n_orthant; P->n_soc = n_soc;
+    P->set = set;
+    P->device = set.device;
+    if (set.n_cond_list > 0) P->cond_list_host.assign(set.cond_list, set.cond_list + set.n_cond_list);
+    P->set.cond_list = nullptr;
+    if (cudaSetDevice(P->device) != cudaSuccess) { delete P; return ACS_ERR_CUDA; }
+    if (set.cuda_stream) {
+        P->stream = (cudaStream_t)set.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking) != cudaSuccess) { delete P; return ACS_ERR_CUDA; }
+        P->own_stream = true;
+    }
+    int rc = ACS_SOLVED;
+    if (acs::occupancy_grid(P) != ACS_SOLVED) { free_all(P); delete P; return ACS_ERR_CUDA; }
+    const long long warps = (long long)P->grid32 * acs::kThreads / 32;
+    // relabel the constraints: sort rows by length (descending) within windows,
+    // so that the 32 rows of a slice have similar lengths and padding is small
+    std::vector<int>& perm = P->perm;
+    perm.resize(m);
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    for (int w0 = 0; w0 < m; w0 += kSortWindow) {
+        const int w1 = std::min(m, w0 + kSortWindow);
+        std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b2) {
+            return (row_ptr[a + 1] - row_ptr[a]) > (row_ptr[b2 + 1] - row_ptr[b2]);
+        });
+    }
+    std::vector<int> inv(m);
+    for (int r = 0; r < m; ++r) inv[perm[r]] = r;
+    HostSell HA, HT;
+    {
+        std::vector<long long> beg(m), end(m);
+        for (int r = 0; r < m; ++r) { beg[r] = row_ptr[perm[r]]; end[r] = row_ptr[perm[r] + 1]; }
+        HA = build_sell(m, choose_g(m, nnz, warps), beg, end, col, val);
+    }
+    {
+        // A' by counting sort over the relabelled rows: row j of A' lists the
+        // relabelled constraints touching coordinate j in increasing order
+        std::vector<long long> rpT(n + 1, 0);
+        for (int k = 0; k < nnz; ++k) rpT[col[k] + 1]++;
+        for (int j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+        std::vector<int> ciT(nnz);
+        std::vector<double> valT(nnz);
+        std::vector<long long> cur(rpT.begin(), rpT.end() - 1);
+        for (int r = 0; r < m; ++r) {
+            const int i = perm[r];
+            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const long long pos = cur[col[k]]++;
+                ciT[pos] = r;
+                valT[pos] = val[k];
+            }
+        }
+        std::vector<long long> beg(rpT.begin(), rpT.end() - 1), end(rpT.begin() + 1, rpT.end());
+        HT = build_sell(n, choose_g(n, nnz, warps), beg, end, ciT.data(), valT.data());
+    }
+    if (HA.nslices < 0 || HT.nslices < 0) {
+        free_all(P); delete P; return ACS_ERR_CSR;
+    }
+    P->padded_A = (long long)HA.col.size();
+    P->padded_AT = (long long)HT.col.size();
+    std::vector<double> bperm(m);
+    for (int r = 0; r < m; ++r) bperm[r] = b[perm[r]];
+    std::vector<int> off(n_soc + 1);
+    off[0] = n_orthant;
+    for (int i = 0; i < n_soc; ++i) off[i + 1] = off[i] + soc_dims[i];
+    double bn = 0, cn = 0;
+    for (int i = 0; i < m; ++i) bn += b[i] * b[i];
+    for (int j = 0; j < n; ++j) cn += c[j] * c[j];
+    P->bnorm = sqrt(bn);
+    P->cnorm = sqrt(cn);
+
+    if (upload_sell(P, HA, P->A) || upload_sell(P, HT, P->AT)) { free_all(P); delete P; return ACS_ERR_OOM; }
+    rc |= dalloc(P, &P->soc_off, n_soc + 1);
+    rc |= dalloc(P, &P->b, m); rc |= dalloc(P, &P->c, n);
+    rc |= dalloc(P, &P->x, n); rc |= dalloc(P, &P->z, n);
+    rc |= dalloc(P, &P->ocone, (size_t)n_orthant + n_soc);
+    if (!P->cond_list_host.empty()) rc |= dalloc(P, &P->cond_list, P->cond_list_host.size());
+    if (rc) { free_all(P); delete P; return ACS_ERR_OOM; }
+    if (alloc_outer(P, P->X) || alloc_inner(P, P->V32) || alloc_inner(P, P->V64)) {
+        free_all(P); delete P; return ACS_ERR_OOM;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+    P->max_ctas = (nsm > 0 ? nsm : 1) * 8;
+    if (dalloc(P, &P->partials, (size_t)P->max_ctas * acs::kMaxRed) || dalloc(P, &P->flags, P->max_ctas) ||
+        dalloc(P, &P->release, 32) || dalloc(P, &P->bcast, acs::kMaxRed) ||
+        dalloc(P, &P->ctl, 1)) { free_all(P); delete P; return ACS_ERR_OOM; }
+    if (cudaMallocHost(&P->ctl_host, sizeof(acs::Control)) != cudaSuccess) { free_all(P); delete P; return ACS_ERR_OOM; }
+    if (cudaEventCreate(&P->ev_launch[0]) != cudaSuccess || cudaEventCreate(&P->ev_launch[1]) != cudaSuccess) {
+        free_all(P); delete P; return ACS_ERR_CUDA;
+    }
+    rc = 0;
+    rc |= upload(P, P->soc_off, off.data(), n_soc + 1);
+    rc |= upload(P, P->b, bperm.data(), m);
+    rc |= upload(P, P->c, c, n);
+    if (!P->cond_list_host.empty())
+        rc |= upload(P, P->cond_list, P->cond_list_host.data(), P->cond_list_host.size());
+    rc |= cudaMemsetAsync(P->X.w, 0, sizeof(double) * m, P->stream) != cudaSuccess;
+    rc |= cudaMemsetAsync(P->X.q, 0, sizeof(double) * n, P->stream) != cudaSuccess;
+    rc |= cudaMemsetAsync(P->ctl, 0, sizeof(acs::Control), P->stream) != cudaSuccess;
+    if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) { free_all(P); delete P; return ACS_ERR_CUDA; }
+    if (P->grid32 > P->max_ctas || P->grid64 > P->max_ctas || P->grid32 > 256 || P->grid64 > 256) { free_all(P); delete P; return ACS_ERR_CUDA; }
+    *out = reinterpret_cast<acs_problem*>(P);
+    return ACS_SOLVED;
+}
+
+int acs_solve_async(acs_problem* h, double tol, int32_t max_iter) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !(tol >= 0) || max_iter < 0) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    return acs::launch_solve(P, tol, max_iter);
+}
+
+int acs_solve(acs_problem* h, double tol, int32_t max_iter) {
+    int rc = acs_solve_async(h, tol, max_iter);
+    if (rc != ACS_SOLVED) return rc;
+    return acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+int acs_get(acs_problem* h, double* x, double* y, double* s, int32_t* iters, double* residuals) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    cudaStream_t st = P->stream;
+    if (cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(acs::Control), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (x && cudaMemcpyAsync(x, P->x, sizeof(double) * P->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (s && cudaMemcpyAsync(s, P->z, sizeof(double) * P->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    std::vector<double> wtmp;
+    if (y) {
+        wtmp.resize(P->m);
+        if (cudaMemcpyAsync(wtmp.data(), P->X.w, sizeof(double) * P->m, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return ACS_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ACS_ERR_CUDA;
+    const acs::Control& C = *P->ctl_host;
+    if (y)
+        for (int r = 0; r < P->m; ++r) y[P->perm[r]] = wtmp[r] / P->set.mu;
+    if (iters) *iters = C.l;
+    if (residuals) {
+        for (int i = 0; i < 6; ++i) residuals[i] = C.res[i];
+        residuals[6] = (double)C.cg_iters;
+        residuals[7] = (double)C.switched_at;
+    }
+    int st_code = C.status;
+    if (st_code == acs::ST_RUNNING || st_code == acs::ST_SWITCH) st_code = ACS_ERR_CUDA;
+    P->last_status = st_code;
+    return st_code;
+}
+
+// pass counters for the benchmark's byte model.
+int acs_debug_counters(acs_problem* h, long long* out6) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !out6) return ACS_ERR_ARG;
+    acs::Control C;
+    if (cudaMemcpy(&C, P->ctl, sizeof(C), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+    out6[0] = C.n_cg_A; out6[1] = C.n_cg_AT; out6[2] = C.n_64_A; out6[3] = C.n_64_AT;
+    out6[4] = C.n_cond; out6[5] = C.n_checks;
+    return ACS_SOLVED;
+}
+
+int acs_debug_phase_times(acs_problem* h, double* ms, long long* count, int32_t n) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !ms || !count || n < acs::PH_COUNT) return ACS_ERR_ARG;
+    acs::Control C;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess ||
+        cudaMemcpy(&C, P->ctl, sizeof(C), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    for (int i = 0; i < acs::PH_COUNT; ++i) {
+        ms[i] = (double)C.phase_ns[i] * 1e-6;
+        count[i] = (long long)C.phase_n[i];
+    }
+    return acs::PH_COUNT;
+}
+
+int acs_debug_barrier_ns(acs_problem* h, int32_t n, double* ns) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !ns || n <= 0) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    return acs::barrier_probe(P, n, ns);
+}
+
+int acs_last_launch_ms(acs_problem* h, double* ms) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !ms) return ACS_ERR_ARG;
+    float f = 0.f;
+    if (cudaEventSynchronize(P->ev_launch[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&f, P->ev_launch[0], P->ev_launch[1]) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    *ms = (double)f;
+    return ACS_SOLVED;
+}
+
+int acs_problem_info(acs_problem* h, int32_t* out8) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !out8) return ACS_ERR_ARG;
+    out8[0] = P->m; out8[1] = P->n; out8[2] = P->nnz;
+    out8[3] = (int32_t)std::min<long long>(P->padded_A, INT32_MAX);
+    out8[4] = (int32_t)std::min<long long>(P->padded_AT, INT32_MAX);
+    out8[5] = P->grid32; out8[6] = P->grid64; out8[7] = acs::kThreads;
+    return ACS_SOLVED;
+}
+
+int acs_get_state(acs_problem* h, double* s_dr, double* O, double* w, int32_t* l, double* step) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
+    acs::Control C;
+    if (cudaMemcpy(&C, P->ctl, sizeof(C), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+    if (s_dr && cudaMemcpy(s_dr, P->X.s, sizeof(double) * P->n, cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+    if (O && cudaMemcpy(O, P->X.O, sizeof(double) * P->n, cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+    if (w) {
+        std::vector<double> t(P->m);
+        if (cudaMemcpy(t.data(), P->X.w, sizeof(double) * P->m, cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+        for (int r = 0; r < P->m; ++r) w[P->perm[r]] = t[r];
+    }
+    if (l) *l = C.l;
+    if (step) { step[0] = C.ds; step[1] = C.snorm; step[2] = C.eta; }
+    return ACS_SOLVED;
+}
+
+int acs_set_state(acs_problem* h, const double* s_dr, const double* O, const double* w, int32_t l,
+                  const double* step) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !s_dr || !O || !w || l < 0) return ACS_ERR_ARG;
+    if (!finite_all(s_dr, P->n) || !finite_all(O, P->n) || !finite_all(w, P->m)) return ACS_ERR_ARG;
+    for (int j = 0; j < P->n; ++j)
+        if (!(O[j] > 0)) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    int rc = 0;
+    std::vector<double> wp(P->m);
+    for (int r = 0; r < P->m; ++r) wp[r] = w[P->perm[r]];
+    rc |= upload(P, P->X.s, s_dr, P->n);
+    rc |= upload(P, P->X.w, wp.data(), P->m);
+    rc |= upload(P, P->X.O, O, P->n);
+    if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
+    P->warm = true;
+    P->warm_l = l;
+    P->warm_ds = step ? step[0] : INFINITY;
+    P->warm_snorm = step ? step[1] : 0.0;
+    P->warm_eta = (step && step[2] > 0) ? step[2] : P->set.cg_eta;
+    return ACS_SOLVED;
+}
+
+void acs_problem_destroy(acs_problem* h) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P) return;
+    cudaSetDevice(P->device);
+    if (P->stream) cudaStreamSynchronize(P->stream);
+    free_all(P);
+    delete P;
+}
+
+}  // extern "C"

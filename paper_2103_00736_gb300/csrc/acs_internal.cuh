@@ -1,0 +1,148 @@
+// Internal types of the GB300 conic solver: device buffers of one problem,
+// the per-launch parameter block of the persistent iteration kernel, and the
+// device-side control block.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/acs.h"
+
+namespace acs {
+
+constexpr int kThreads = 1024;          // threads per CTA of the persistent kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRed = 8;              // doubles reduced per grid reduction
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s per barrier
+
+// device-side status value of a solve still in progress
+enum : int { ST_RUNNING = 100, ST_SWITCH = 101 /* FP32 correction solve handed over to FP64 */ };
+
+// phases of the persistent kernel, for the per-phase time record
+enum Phase : int {
+    PH_COND_O = 0, PH_COND_APPLY, PH_BTILDE, PH_QREFRESH, PH_ABS, PH_RHS, PH_CG_AT, PH_CG_A,
+    PH_CG_VEC, PH_UPDATE, PH_KKT, PH_COUNT
+};
+
+// Control block: lives in device memory for the whole solve; the host reads
+// it back at acs_get.  Written only by CTA 0 at the end of a launch.
+struct Control {
+    int status;           // ST_RUNNING, ACS_SOLVED, ACS_MAX_ITER or an error
+    int err;              // first device-side error (0 = none); checked at every barrier
+    int l;                // iterations completed
+    int pad0;
+    long long cg_iters;   // conjugate-gradient iterations, all outer iterations
+    int switched_at;      // iteration at which the FP32 correction solve handed over (0 = never)
+    int pad1;
+    double res[6];        // r_p, r_d, r_gap, r_cone, obj_p, obj_d at the last check
+    double ds;            // ||s_l - s_{l-1}|| of the last iteration
+    double snorm;         // ||s_l||
+    double eta;           // current inexactness factor of the projection solve
+    // pass counters (for the algorithmic-byte model of the benchmark)
+    long long n_cg_A, n_cg_AT, n_64_A, n_64_AT, n_cond, n_checks;
+    unsigned bar_count, bar_gen;
+    unsigned long long bar_count64;   // monotonic barrier arrival counter of the current solve
+    // nanoseconds spent in each phase (from one barrier exit to the next, as
+    // seen by CTA 0), accumulated over the solve, and the number of phases run
+    unsigned long long phase_ns[PH_COUNT];
+    unsigned long long phase_n[PH_COUNT];
+};
+
+// Outer iteration state, always FP64 (Algorithm 2 in the scaled space).
+struct Outer {
+    double *s, *p, *g, *q, *w, *chat, *btil, *O;
+};
+// Inner projection-solve (CG) state in precision T (Chronopoulos-Gear CG:
+// r residual, u = J^{-1} r, p direction, sv = M p, au = M u, t = O^2 A' u).
+template <typename T>
+struct Inner {
+    T *r, *u, *p, *sv, *au, *t, *jinv, *O2;
+};
+
+// Sliced ELLPACK, one warp per slice, G lanes per row (G in 1..32, a power
+// of two): slice sl holds rows sl*(32/G) ... + 32/G - 1; entry k of local row
+// r sits at sptr[sl] + 32*(k/G) + r*G + k%G, so every chunk of 32 entries is
+// contiguous.  Rows shorter than G*slen[sl] are padded with (col 0, val 0).
+struct SellMat {
+    int nrows, nslices, g;
+    const int* sptr;       // [nslices + 1] start of each slice
+    const int* slen;       // [nslices] 32-entry chunks in the slice
+    const int* col;        // [sptr[nslices]]
+    const float* v32;
+    const double* v64;
+};
+
+// Everything one launch of the iteration kernel needs (passed by value).
+template <typename T>
+struct IterParams {
+    int m, n, n_orth, n_soc;
+    SellMat A, AT;                                    // A (rows relabelled) and A'
+    const int* soc_off;                               // n_soc + 1 absolute offsets
+    const double* b; const double* c;
+    double bnorm, cnorm;
+    Outer X;
+    Inner<T> V;
+    double* x; double* z;                             // FP64 iterates (steps 20-21)
+    double* ocone;                                    // log o per cone (orthant coords first)
+    double* partials;                                 // [gridDim.x * kMaxRed]
+    unsigned* flags;                                  // [gridDim.x] barrier arrival flags
+    unsigned* release;                                // barrier release flag
+    double* bcast;                                    // [kMaxRed] reduced values
+    Control* ctl;
+    // settings
+    double mu, t_cond;
+    int cond_first, cond_period;
+    const int* cond_list; int n_cond_list;
+    int check_every, max_iter;
+    double tol, cg_eta, cg_tol, cg_relfloor;
+    int cg_max;
+    int refresh;                                      // recompute c_hat, b_tilde, J, q first
+    int refine;                                       // correction solves per iteration
+    int switch_ok;                                    // FP32 launch may hand over to FP64
+};
+
+struct Problem {
+    int m = 0, n = 0, nnz = 0, n_orth = 0, n_soc = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    acs_settings set{};
+    std::vector<int> cond_list_host;
+    int* cond_list = nullptr;
+    double bnorm = 0, cnorm = 0;
+    // matrix: A with its rows relabelled by perm (row i of the device matrix
+    // is row perm[i] of the caller's A; b, y and w live in that order)
+    SellMat A{}, AT{};
+    long long padded_A = 0, padded_AT = 0;
+    std::vector<int> perm;
+    int* soc_off = nullptr;
+    double *b = nullptr, *c = nullptr;
+    // state
+    Outer X{};
+    Inner<float> V32{};
+    Inner<double> V64{};
+    double *x = nullptr, *z = nullptr, *ocone = nullptr;
+    double* partials = nullptr;
+    unsigned* flags = nullptr;
+    unsigned* release = nullptr;
+    double* bcast = nullptr;
+    int max_ctas = 0;
+    Control* ctl = nullptr;
+    Control* ctl_host = nullptr;         // pinned mirror
+    int grid32 = 0, grid64 = 0;
+    bool warm = false;                   // acs_set_state called
+    int warm_l = 0;
+    double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 1e-2;
+    int last_status = ACS_MAX_ITER;
+    std::vector<void*> allocations;
+    cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch
+};
+
+// launches (acs_iter.cu)
+int launch_solve(Problem* P, double tol, int max_iter);
+int occupancy_grid(Problem* P);
+int barrier_probe(Problem* P, int n, double* ns_per_barrier);
+
+}  // namespace acs

@@ -187,11 +187,13 @@ def small_lp(seed: int = seed_for(K_SMALL_LP), m: int = 200, n: int = 500,
     """
     rng = np.random.default_rng(seed)
     nnz = int(round(density * m * n))
-    while True:
+    for _ in range(1000):
         pos = rng.choice(m * n, size=nnz, replace=False)
         rows, cols = pos // n, pos % n
         if np.bincount(rows, minlength=m).min() > 0 and np.bincount(cols, minlength=n).min() > 0:
             break
+    else:
+        raise ValueError("density too low to draw a pattern without empty rows and columns")
     vals = rng.standard_normal(nnz)
     row_ptr, col, val = coo_to_csr(m, n, rows, cols, vals)
     x, s = _plant_orthant(rng, n, n_support / n)
@@ -280,6 +282,15 @@ def bernoulli_lp(seed: int, m: int, n: int, density: float = 0.02, frac_pos: flo
     rng = np.random.default_rng(seed) if pattern_seed is not None else rng_a
     x, s = _plant_orthant(rng, n, frac_pos)
     return _finish(f"lp{m}x{n}", m, n, row_ptr, col, val, n, [], x, s, rng)
+
+
+def planted_lp(A_csr_row_ptr, col, val, m: int, n: int, seed: int, frac_pos: float = 0.3,
+               name: str = "lp") -> Instance:
+    """Plant an optimum (x*, y*, s*) for a given CSR matrix (K = R+^n)."""
+    rng = np.random.default_rng(seed)
+    x, s = _plant_orthant(rng, n, frac_pos)
+    return _finish(name, m, n, np.asarray(A_csr_row_ptr, np.int64), np.asarray(col, np.int32),
+                   np.asarray(val, np.float64), n, [], x, s, rng)
 
 
 def batch_sizes(count: int = 4096, mmin: int = 50, mmax: int = 2000, ratio: float = 2.5,

@@ -1,0 +1,88 @@
+"""Host-only checks of the C ABI: the library builds, loads, exports every
+symbol include/acs.h declares, and rejects malformed input before touching
+the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2103_00736_gb300 import capi as c, build
+    if not os.path.exists(c.LIB_PATH):
+        build.build()
+    c.lib()
+    return c
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "acs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(acs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    names = _declared()
+    assert "acs_problem_create" in names and "acs_solve" in names and "acs_get" in names
+    L = capi.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_settings_defaults(capi):
+    s = capi.acs_settings_default()
+    assert s.mu == 1.0 and s.t == 9.2 and s.cond_first == 300 and s.cond_period == 100
+    assert s.check_every == 10 and s.precision == capi.PREC_MIXED
+    assert capi.acs_status_string(0) == "solved"
+    assert "CSR" in capi.acs_status_string(capi.ERR_CSR)
+
+
+def _create(capi, m, n, rp, col, val, b, c, n_orth, dims=(), **kw):
+    return capi.acs_problem_create(m, n, rp, col, val, b, c, n_orth, dims,
+                                   capi.acs_settings_default(**kw) if kw else None)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("empty_row", -2), ("col_range", -2), ("unsorted", -2), ("duplicate", -2), ("rowptr0", -2),
+    ("cones_sum", -3), ("cone_small", -3), ("nan", -1), ("mu", -1), ("m0", -1),
+])
+def test_validation_errors(capi, case, code):
+    rp = np.array([0, 2, 4], np.int64)
+    col = np.array([0, 1, 1, 2], np.int32)
+    val = np.array([1.0, 2.0, 3.0, 4.0])
+    b, c = np.ones(2), np.ones(3)
+    args = dict(m=2, n=3, rp=rp, col=col, val=val, b=b, c=c, n_orth=3, dims=())
+    kw = {}
+    if case == "empty_row":
+        args["rp"] = np.array([0, 0, 4], np.int64)
+    elif case == "col_range":
+        args["col"] = np.array([0, 1, 1, 3], np.int32)
+    elif case == "unsorted":
+        args["col"] = np.array([1, 0, 1, 2], np.int32)
+    elif case == "duplicate":
+        args["col"] = np.array([1, 1, 1, 2], np.int32)
+    elif case == "rowptr0":
+        args["rp"] = np.array([1, 2, 4], np.int64)
+    elif case == "cones_sum":
+        args["n_orth"] = 2
+    elif case == "cone_small":
+        args["n_orth"], args["dims"] = 2, [1]
+    elif case == "nan":
+        args["val"] = np.array([1.0, np.nan, 3.0, 4.0])
+    elif case == "mu":
+        kw["mu"] = -1.0
+    elif case == "m0":
+        args["m"] = 0
+    with pytest.raises(capi.AcsError) as e:
+        _create(capi, args["m"], args["n"], args["rp"], args["col"], args["val"], args["b"],
+                args["c"], args["n_orth"], args["dims"], **kw)
+    assert e.value.code == code
+
+
+def test_build_flags_target_sm103a():
+    from paper_2103_00736_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH

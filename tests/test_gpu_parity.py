@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (stated requirement of the method's hot path):
+  * end results: every relative KKT residual <= 1e-6 when re-evaluated by the
+    oracle's FP64 residual function on the returned (x, y, z); objective
+    within 1e-6 relative of the oracle's and of the planted optimum;
+  * FP32 iterates: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-4 over the first
+    50 iterations under the paper's LP schedule (no rescaling before l = 300);
+  * FP64 iterates: same comparison <= 1e-7 (the projection solve stops at a
+    relative CG residual of 1e-10 while the oracle factorises M exactly).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2103_00736_gb300 import capi, instances as I  # noqa: E402
+from oracle import alg, kkt  # noqa: E402
+
+LP_SCHED = dict(cond_first=300, cond_period=100)
+
+
+def _kkt_of(inst, x, y, z):
+    return kkt.residuals(inst.to_scipy(), inst.b, inst.c, x, y, z, inst.n_orth, inst.soc_dims)
+
+
+def _solve(inst, tol=1e-6, max_iter=20000, **kw):
+    with capi.Solver(inst, **kw) as s:
+        st = s.solve(tol=tol, max_iter=max_iter)
+        rc, x, y, z, iters, res = s.get()
+    return st, x, y, z, iters, res
+
+
+@pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
+def test_small_lp_end_result(precision):
+    inst = I.small_lp()
+    st, x, y, z, iters, res = _solve(inst, precision=precision, **LP_SCHED)
+    assert st == capi.SOLVED, capi.acs_status_string(st)
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    # the library's own residual record agrees with the oracle's evaluation
+    for k, key in enumerate(("r_p", "r_d", "r_gap", "r_cone")):
+        assert abs(res[k] - ours[key]) <= 1e-9 + 1e-6 * ours[key], (key, res[k], ours[key])
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
+                         max_iter=20000, tol=1e-6, check_every=10)
+    assert abs(ours["obj_p"] - ref.res["obj_p"]) <= 1e-6 * abs(ref.res["obj_p"])
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+    # x* is unique here (|supp x*| = 150 < m)
+    assert np.linalg.norm(x - inst.x_star) <= 1e-4 * np.linalg.norm(inst.x_star)
+
+
+@pytest.mark.parametrize("precision,rtol", [(capi.PREC_MIXED, 1e-4), (capi.PREC_FP64, 1e-7)])
+def test_first_50_iterates(precision, rtol):
+    inst = I.small_lp()
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
+                         max_iter=50, tol=0.0, keep_x=50)
+    worst = 0.0
+    for k in (1, 2, 3, 5, 10, 20, 35, 50):
+        st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=precision,
+                                         cg_eta=1e-9, cg_tol=0.0, **LP_SCHED)
+        assert st == capi.MAX_ITER and iters == k
+        xr = ref.x_history[k - 1]
+        err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+        worst = max(worst, err)
+        assert err <= rtol, (k, err)
+    print("worst relative iterate error", worst)
+
+
+@pytest.mark.parametrize("sched", [dict(), dict(cond_first=0, cond_list=list(range(1, 51))),
+                                   dict(cond_first=1, cond_period=1)])
+@pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
+def test_worked_example(sched, precision):
+    """Section III-A example (ill-conditioned 3 x 5, cond 2046) reaches the
+    vertex optimum under the LP schedule, rescaling at the first 50 iterations,
+    and rescaling at every iteration."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")))
+    A = np.array(g["A"])
+    row_ptr = np.arange(0, 16, 5, dtype=np.int64)
+    col = np.tile(np.arange(5, dtype=np.int32), 3)
+    s = capi.acs_settings_default(precision=precision, **sched)
+    h = capi.acs_problem_create(3, 5, row_ptr, col, A.reshape(-1), g["b"], g["c"], 5, [], s)
+    try:
+        st = capi.acs_solve(h, 1e-8, 20000)
+        rc, x, y, z, iters, res = capi.acs_get(h, 3, 5)
+    finally:
+        capi.acs_problem_destroy(h)
+    assert st == capi.SOLVED, (capi.acs_status_string(st), iters, res)
+    np.testing.assert_allclose(x, [0, 0, 4.25719522, 0.19851252, 0.51359132], atol=1e-6)
+
+
+@pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
+def test_small_socp(precision):
+    inst = I.socp(scale=0.002)
+    st, x, y, z, iters, res = _solve(inst, precision=precision, t=1.7, cond_first=200,
+                                     cond_period=100, max_iter=20000)
+    assert st == capi.SOLVED, capi.acs_status_string(st)
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * (1 + abs(inst.obj_star))
+
+
+def test_socp_iterates_match_oracle_fp64():
+    """SOC reflection, multi-warp cones and the orthant together: FP64 iterates
+    over 30 iterations (scaled C3 recipe, one cone of 200 coordinates added)."""
+    inst = I.socp(scale=0.001)
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n_orth, inst.soc_dims, t=1.7,
+                         L=alg.SOCP_SCHEDULE, max_iter=30, tol=0.0, keep_x=30)
+    for k in (1, 7, 30):
+        st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=capi.PREC_FP64,
+                                         t=1.7, cond_first=200, cond_period=100, cg_eta=1e-12, cg_tol=0.0)
+        xr = ref.x_history[k - 1]
+        assert np.linalg.norm(x - xr) <= 1e-7 * np.linalg.norm(xr), k
+
+
+def test_conditioning_first_50_iterations():
+    """Rescaling on the device (steps 5-14) at each of the first 50 iterations.
+    Iterates are compared while exact (k <= 2: O = I up to the first rescale
+    that moves); after that the rescaling amplifies the attainable accuracy of
+    the CG projection (O spreads over e^9.2, M over ~1e10), as it amplifies
+    rounding in the oracle itself, so the end result is compared."""
+    inst = I.small_lp()
+    L = alg.Schedule(explicit=tuple(range(1, 51)))
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=L, max_iter=2, tol=0.0,
+                         keep_x=2)
+    for k in (1, 2):
+        st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=capi.PREC_FP64,
+                                         cond_list=list(range(1, 51)), cond_first=0, cg_eta=1e-12, cg_tol=0.0)
+        xr = ref.x_history[k - 1]
+        assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr), (k, np.linalg.norm(x - xr))
+    for prec in (capi.PREC_MIXED, capi.PREC_FP64):
+        st, x, y, z, iters, res = _solve(inst, tol=2e-7, precision=prec, cond_list=list(range(1, 51)),
+                                         cond_first=0)
+        assert st == capi.SOLVED
+        ours = _kkt_of(inst, x, y, z)
+        assert kkt.max_residual(ours) <= 2e-7
+        assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+
+
+def test_edge_shapes():
+    # single row, single column: x = b/a
+    st, x, y, z, iters, res = _solve(
+        I.Instance(m=1, n=1, row_ptr=np.array([0, 1]), col=np.array([0], np.int32),
+                   val=np.array([2.0]), b=np.array([3.0]), c=np.array([1.0]), n_orth=1,
+                   soc_dims=np.zeros(0, np.int32), x_star=np.array([1.5]), y_star=np.zeros(1),
+                   s_star=np.zeros(1)), tol=1e-9, precision=capi.PREC_FP64)
+    assert st == capi.SOLVED
+    assert abs(x[0] - 1.5) < 1e-8
+    # pure SOCP with one large cone (several warp strides) and a size-2 cone
+    rng = np.random.default_rng(3)
+    dims = np.array([2, 300, 5], np.int32)
+    n = int(dims.sum())
+    m = 40
+    inst = I.bernoulli_lp(7, m, n, density=0.2)
+    xs, ss = I._plant_soc_blocks(rng, dims)
+    y = rng.standard_normal(m)
+    A = inst.to_scipy()
+    inst = I.Instance(m=m, n=n, row_ptr=inst.row_ptr, col=inst.col, val=inst.val, b=A @ xs,
+                      c=A.T @ y + ss, n_orth=0, soc_dims=dims, x_star=xs, y_star=y, s_star=ss)
+    st, x, y2, z, iters, res = _solve(inst, tol=1e-7, t=1.7, cond_first=200, cond_period=100,
+                                      precision=capi.PREC_FP64, max_iter=50000)
+    assert st == capi.SOLVED
+    assert kkt.max_residual(_kkt_of(inst, x, y2, z)) <= 1e-7
+    # ragged: rows of very different lengths (a dense row among short ones)
+    base = I.bernoulli_lp(5, 33, 257, density=0.03).to_scipy().tolil()
+    base[0, :] = np.random.default_rng(5).standard_normal(257)
+    base = base.tocsr()
+    inst = I.planted_lp(base.indptr, base.indices, base.data, 33, 257, seed=6, frac_pos=0.08)
+    st, x, y, z, iters, res = _solve(inst, tol=1e-6, **LP_SCHED)
+    assert st == capi.SOLVED
+    assert kkt.max_residual(_kkt_of(inst, x, y, z)) <= 1e-6
+
+
+def test_rank_deficient_rows():
+    """Duplicate rows: M = AA' is singular.  With a consistent b the right-hand
+    sides stay in range(M), CG converges and the LP is solved (min x1 + x2,
+    x1 + 2 x2 = 1, x >= 0 -> x = (0, 1/2)); with an inconsistent b the
+    problem is infeasible and no solve may report success."""
+    row_ptr = np.array([0, 2, 4], np.int64)
+    col = np.array([0, 1, 0, 1], np.int32)
+    val = np.array([1.0, 2.0, 1.0, 2.0])
+    s = capi.acs_settings_default(precision=capi.PREC_FP64)
+    h = capi.acs_problem_create(2, 2, row_ptr, col, val, [1.0, 1.0], [1.0, 1.0], 2, [], s)
+    try:
+        st = capi.acs_solve(h, 1e-8, 2000)
+        rc, x, y, z, iters, res = capi.acs_get(h, 2, 2)
+    finally:
+        capi.acs_problem_destroy(h)
+    assert st == capi.SOLVED
+    np.testing.assert_allclose(x, [0.0, 0.5], atol=1e-7)
+    h = capi.acs_problem_create(2, 2, row_ptr, col, val, [1.0, 2.0], [1.0, 1.0], 2, [], s)
+    try:
+        st = capi.acs_solve(h, 1e-8, 200)
+    finally:
+        capi.acs_problem_destroy(h)
+    assert st in (capi.ERR_FACTOR, capi.MAX_ITER, capi.ERR_NUMERICAL)
+
+
+def test_deterministic_and_reentrant():
+    inst = I.socp(scale=0.002)
+    with capi.Solver(inst, t=1.7, cond_first=200, cond_period=100) as s:
+        s.solve(tol=1e-6, max_iter=3000)
+        a = s.get()
+        s.solve(tol=1e-6, max_iter=3000)
+        b = s.get()
+    assert a[4] == b[4]
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[3], b[3])
+
+
+def test_warm_start_continues_fp64():
+    inst = I.small_lp()
+    kw = dict(precision=capi.PREC_FP64, **LP_SCHED)
+    with capi.Solver(inst, **kw) as s:
+        s.solve(tol=0.0, max_iter=40)
+        full = s.get()
+    with capi.Solver(inst, **kw) as s:
+        s.solve(tol=0.0, max_iter=25)
+        st_s, O, w, l, step = capi.acs_get_state(s.h, inst.m, inst.n)
+        assert l == 25
+        capi.acs_set_state(s.h, st_s, O, w, l, step)
+        s.solve(tol=0.0, max_iter=40)
+        part = s.get()
+    assert part[4] == 40
+    np.testing.assert_allclose(part[1], full[1], rtol=0, atol=1e-9 * np.abs(full[1]).max())
+
+
+@pytest.mark.slow
+def test_large_lp_full_size():
+    """The large LP at full size (m = 2e5, n = 1e6, 1e7 nonzeros, row scales
+    over four decades): end result re-evaluated by the oracle's residuals."""
+    inst = I.large_lp()
+    st, x, y, z, iters, res = _solve(inst, tol=4e-7, max_iter=5000, **LP_SCHED)
+    assert st == capi.SOLVED, (capi.acs_status_string(st), res)
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+
+
+@pytest.mark.slow
+def test_large_lp_first_iteration_full_size():
+    """First iterations at full size against the oracle (CG to 1e-13 in FP64);
+    two refinement rounds per iteration remove the FP32 model error of A."""
+    inst = I.large_lp()
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
+                         max_iter=2, tol=0.0, keep_x=2, solver="cg")
+    for k, rtol, prec in ((1, 1e-4, capi.PREC_MIXED), (2, 1e-4, capi.PREC_MIXED), (2, 1e-8, capi.PREC_FP64)):
+        st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=prec, cg_eta=1e-12,
+                                         cg_tol=0.0, cg_refine=2, **LP_SCHED)
+        xr = ref.x_history[k - 1]
+        assert np.linalg.norm(x - xr) <= rtol * np.linalg.norm(xr), (k, prec)
+        # sampled coordinates one by one
+        idx = np.random.default_rng(0).choice(inst.n, 1000, replace=False)
+        np.testing.assert_allclose(x[idx], xr[idx], atol=rtol * 10 * np.abs(xr).max())
