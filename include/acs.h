@@ -179,6 +179,38 @@ int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t 
 int acs_debug_barrier_ns(acs_problem* p, int32_t n, double* ns);
 int acs_problem_info(acs_problem* p, int32_t* out8);
 
+/*
+ * KKT residuals of a caller-supplied point, for callers that cannot allocate
+ * device memory (the paper has no counterpart; it is a service of this
+ * library).  It allocates nothing: the caller passes every input and the
+ * output in device memory it already owns, and the temporary data live in
+ * one file-scope device array of fixed size, held by every GPU that loads the
+ * library until the process exits.  Computes, in FP64 and in the order of
+ * acs_get's residuals[0..5]: r_p, r_d, r_gap, r_cone, c'x, b'y (definitions
+ * at acs_solve).
+ *   m, n            : A is m x n, 1 <= n <= 1,048,576 (larger n: ACS_ERR_LIMIT);
+ *                     the array is 8.06 MiB (n doubles for A'y plus 1024 x 8
+ *                     block partials).
+ *   row_ptr, col, val : DEVICE CSR of A: int32[m+1], int32[nnz], double[nnz].
+ *   b[m], c[n], x[n], y[m], z[n] : DEVICE vectors (z is the dual slack).
+ *   n_orthant, n_soc, soc_offsets : cones as in acs_problem_create, with
+ *                     soc_offsets a DEVICE int32[n_soc+1] array of absolute
+ *                     start offsets (soc_offsets[0] = n_orthant, last = n).
+ *   residuals       : DEVICE double[6], written asynchronously.
+ *   cuda_stream     : stream to run on (NULL = legacy default stream).
+ * The call is asynchronous: results are ready when the stream reaches them.
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.
+ * Every call clears the part of the array it accumulates into; calls that
+ * overlap on the GPU share the array and race, so order them.  The A'y part
+ * is accumulated with atomic adds, so r_d may differ in its last bits from
+ * call to call.  Errors: ACS_ERR_ARG, ACS_ERR_LIMIT, ACS_ERR_CUDA.
+ */
+int acs_kkt_residuals_noalloc(int32_t m, int32_t n, const int32_t* row_ptr, const int32_t* col,
+                              const double* val, const double* b, const double* c, const double* x,
+                              const double* y, const double* z, int32_t n_orthant, int32_t n_soc,
+                              const int32_t* soc_offsets, double* residuals, void* cuda_stream);
+
 /* Library version string. */
 const char* acs_version(void);
 

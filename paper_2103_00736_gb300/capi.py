@@ -77,6 +77,8 @@ def lib():
         L.acs_problem_info.argtypes = [P, ip]
         L.acs_last_launch_ms.argtypes = [P, dp]
         L.acs_debug_barrier_ns.argtypes = [P, C.c_int32, dp]
+        L.acs_kkt_residuals_noalloc.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, P, P,
+                                                C.c_int32, C.c_int32, P, P, P]
         L.acs_debug_phase_times.argtypes = [P, dp, C.POINTER(C.c_longlong), C.c_int32]
         _lib = L
     return _lib
@@ -235,6 +237,13 @@ def acs_problem_info(h) -> dict:
         raise AcsError(rc, "acs_problem_info")
     keys = ("m", "n", "nnz", "padded_A", "padded_AT", "grid32", "grid64", "threads")
     return dict(zip(keys, out.tolist()))
+
+
+def acs_kkt_residuals_noalloc(m, n, row_ptr, col, val, b, c, x, y, z, n_orthant, n_soc,
+                              soc_offsets, residuals, stream=0) -> int:
+    """All array arguments are DEVICE addresses (ints, e.g. torch tensor data_ptr())."""
+    return lib().acs_kkt_residuals_noalloc(int(m), int(n), row_ptr, col, val, b, c, x, y, z,
+                                           int(n_orthant), int(n_soc), soc_offsets, residuals, stream)
 
 
 class Solver:
