@@ -54,6 +54,21 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes of one launch of the persistent kernel, from one ncu capture
+# (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
+# taken from: reported as null once acs_iter.cu or acs_internal.cuh change.
+TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "08b7d34618b7e1fe", "bytes": 569.34e9}
+
+
+def kernel_source_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("acs_iter.cu", "acs_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_00736_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def make_instance(name: str):
     from paper_2103_00736_gb300 import instances as I
     if name == "large_lp":
@@ -281,7 +296,10 @@ def gpu_arm(args) -> None:
     alg_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    traffic = args.traffic if args.traffic is not None else None
+    traffic = args.traffic
+    if traffic is None and args.workload == TRAFFIC_RECORD["workload"] and tol > 0 \
+            and kernel_source_sha16() == TRAFFIC_RECORD["source_sha16"]:
+        traffic = TRAFFIC_RECORD["bytes"]
 
     # end to end through the C ABI with host buffers, every step: upload,
     # solve, read back x, y, s
