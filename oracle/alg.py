@@ -24,9 +24,13 @@ Readings (the paper is silent or ambiguous on these):
     s = (1 - mu) e.
   * o is the same for every coordinate of one cone, so O is constant on each
     cone and O^{-1} K = K, abs_{O^{-1} K} = abs_K; O' A_cal = range((A O)').
-  * Non-finite o (some o_j in {0, inf, nan}): exponent 0, i.e. O = I
-    (MATLAB semantics 0^0 = inf^0 = 1, with nan treated the same way).
-    All o_j equal: exponent 1.
+  * o_j = 0, inf or nan (x_{h+1} = ||xbar|| or z_{h+1} = 0, e.g. a
+    coordinate with x_j = z_j = 0): such entries carry no scale, so the
+    exponent of step 11 is computed from the finite positive o only, and the
+    others take the limits of the rule under the cap: o = 0 the smallest
+    scale min(o)^alpha, o = inf the largest max(o)^alpha, o = nan the
+    geometric middle.  No finite positive o at all: O = I.  All finite o
+    equal: exponent 1.
   * O is recomputed from the current x, z at each conditioning (not composed).
   * Steps 20-21 use p from the old s and the updated s, as printed.
   * The schedule L continues with its period up to max_iter.
@@ -88,22 +92,30 @@ def conditioning_vector(x: np.ndarray, z: np.ndarray, n_orth: int, soc_dims) -> 
 
 
 def conditioning_exponent(o: np.ndarray, t: float) -> float:
-    """min(1, t / (log max o - log min o)) of step 11, with the non-finite reading."""
-    if o.size == 0 or not np.all(np.isfinite(o)) or np.any(o <= 0.0):
+    """min(1, t / (log max o - log min o)) of step 11 over the finite positive o."""
+    ok = np.isfinite(o) & (o > 0.0)
+    if not np.any(ok):
         return 0.0
-    spread = math.log(float(o.max())) - math.log(float(o.min()))
+    spread = math.log(float(o[ok].max())) - math.log(float(o[ok].min()))
     if spread <= 0.0:
         return 1.0
     return min(1.0, t / spread)
 
 
 def conditioning_matrix(x, z, n_orth, soc_dims, t):
-    """diag(O) of step 11: |o|^alpha (alpha = 0 gives O = I)."""
+    """diag(O) of step 11: |o|^alpha, with the limits above for o in {0, inf, nan}."""
     o = conditioning_vector(x, z, n_orth, soc_dims)
     alpha = conditioning_exponent(o, t)
-    if alpha == 0.0:
+    ok = np.isfinite(o) & (o > 0.0)
+    if not np.any(ok):
         return np.ones_like(o), alpha
-    return np.abs(o) ** alpha, alpha
+    lo = np.empty_like(o)
+    lo[ok] = np.log(o[ok])
+    lmin, lmax = lo[ok].min(), lo[ok].max()
+    lo[~ok & (o == 0.0)] = lmin
+    lo[~ok & np.isinf(o)] = lmax
+    lo[np.isnan(o)] = 0.5 * (lmin + lmax)
+    return np.exp(alpha * lo), alpha
 
 
 @dataclass

@@ -221,10 +221,20 @@ def test_conditioning_rule():
     O, a = alg.conditioning_matrix(x, z, n_orth, dims, 100.0)
     assert a == 1.0
     np.testing.assert_allclose(O, o)
-    # non-finite o: O = I
-    z0 = z.copy(); z0[0] = 0.0
-    O, a = alg.conditioning_matrix(x, z0, n_orth, dims, 9.2)
-    assert a == 0.0 and np.all(O == 1.0)
+    # o in {0, inf, nan} carries no scale: the exponent comes from the finite o,
+    # and o = inf / 0 / nan take the largest / smallest / middle scale under the cap
+    z0 = z.copy(); z0[0] = 0.0                      # o_0 = inf
+    x0 = x.copy(); x0[1] = 0.0                      # o_1 = 0
+    x0[2] = 0.0; z0[2] = 0.0                        # o_2 = nan
+    O, a = alg.conditioning_matrix(x0, z0, n_orth, dims, 9.2)
+    fin = alg.conditioning_vector(x, z, n_orth, dims)[3:]
+    assert a == alg.conditioning_exponent(fin, 9.2) and 0.0 < a <= 1.0
+    assert O[0] == O[3:].max() and O[1] == O[3:].min()
+    np.testing.assert_allclose(O[2], np.sqrt(O[3:].max() * O[3:].min()))
+    assert np.all(np.isfinite(O)) and math.log(O.max() / O.min()) <= 9.2 * (1 + 1e-12)
+    # nothing finite at all: O = I
+    O, a = alg.conditioning_matrix(np.zeros(12), np.zeros(12), n_orth, dims, 9.2)
+    assert np.all(O == 1.0)
     # all equal: exponent 1
     assert alg.conditioning_exponent(np.full(5, 3.0), 9.2) == 1.0
 
