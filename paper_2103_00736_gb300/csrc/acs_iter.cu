@@ -427,17 +427,20 @@ __device__ __forceinline__ bool in_schedule(const IterParams<T>& P, int l) {
 // ---------------------------------------------------------------------------
 
 // Conditioning, steps 5-10: o per cone, o = |x_h - ||xbar||| / |z_h|, stored
-// as log o; partials: max log o, max(-log o), count of o not in (0, inf).
+// as log o (log 0 = -inf, log inf = inf, nan stays nan); partials over the
+// finite positive o: max log o, max(-log o), and their count.
 template <typename T>
 __device__ __noinline__ void phase_cond_o(const IterParams<T>& P) {
-    double vmax = -INFINITY, vneg = -INFINITY, bad = 0.0;
+    double vmax = -INFINITY, vneg = -INFINITY, good = 0.0;
     for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
         const double o = fabs(P.x[j]) / fabs(P.z[j]);
-        if (!(o > 0.0) || !(o < INFINITY)) { bad += 1.0; P.ocone[j] = 0.0; continue; }
         const double lo = log(o);
         P.ocone[j] = lo;
-        vmax = fmax(vmax, lo);
-        vneg = fmax(vneg, -lo);
+        if (o > 0.0 && o < INFINITY) {
+            good += 1.0;
+            vmax = fmax(vmax, lo);
+            vneg = fmax(vneg, -lo);
+        }
     }
     const int lane = threadIdx.x & 31;
     for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
@@ -447,23 +450,39 @@ __device__ __noinline__ void phase_cond_o(const IterParams<T>& P) {
         ss = warp_sum(ss);
         if (lane == 0) {
             const double o = fabs(P.x[a] - sqrt(ss)) / fabs(P.z[a]);
-            if (!(o > 0.0) || !(o < INFINITY)) {
-                bad += 1.0;
-                P.ocone[P.n_orth + cI] = 0.0;
-            } else {
-                const double lo = log(o);
-                P.ocone[P.n_orth + cI] = lo;
+            const double lo = log(o);
+            P.ocone[P.n_orth + cI] = lo;
+            if (o > 0.0 && o < INFINITY) {
+                good += 1.0;
                 vmax = fmax(vmax, lo);
                 vneg = fmax(vneg, -lo);
             }
         }
     }
-    const double v[3] = {vmax, vneg, bad};
+    const double v[3] = {vmax, vneg, good};
     const int op[3] = {1, 1, 0};
     block_partials<3>(v, op, P.partials);
 }
 
-// Steps 11-14 per coordinate: O = exp(alpha log o) (alpha = 0 -> O = I),
+// Exponent range of step 11 over the finite positive o.  An o of 0, inf or
+// nan (x_h = ||xbar||, z_h = 0, or both) carries no scale: it takes the
+// limit of the rule under the e^t cap -- the smallest scale for o = 0, the
+// largest for o = inf, the geometric middle for nan.  With no finite
+// positive o at all, O = I.
+struct CondRange {
+    double alpha, lmin, lmax;
+    bool any;
+};
+__device__ __forceinline__ double cond_scale(double lo, const CondRange& R) {
+    if (!R.any) return 1.0;
+    double e = lo;
+    if (isnan(lo)) e = 0.5 * (R.lmin + R.lmax);
+    else if (lo == -INFINITY) e = R.lmin;
+    else if (lo == INFINITY) e = R.lmax;
+    return exp(R.alpha * e);
+}
+
+// Steps 11-14 per coordinate: O = exp(alpha log o) (see cond_scale),
 // c_hat = O c, s = x/O - mu O z; g = O c_hat (input of the b_tilde pass).
 template <typename T>
 __device__ __forceinline__ void cond_apply_coord(const IterParams<T>& P, int j, double Oj, bool recast) {
@@ -476,16 +495,16 @@ __device__ __forceinline__ void cond_apply_coord(const IterParams<T>& P, int j, 
 }
 
 template <typename T>
-__device__ __noinline__ void phase_cond_apply(const IterParams<T>& P, double alpha, bool recompute_O, bool recast) {
+__device__ __noinline__ void phase_cond_apply(const IterParams<T>& P, const CondRange& R, bool recompute_O,
+                                              bool recast) {
     for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
-        const double Oj = recompute_O ? (alpha == 0.0 ? 1.0 : exp(alpha * P.ocone[j])) : P.X.O[j];
+        const double Oj = recompute_O ? cond_scale(P.ocone[j], R) : P.X.O[j];
         cond_apply_coord(P, j, Oj, recast);
     }
     const int lane = threadIdx.x & 31;
     for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
         const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
-        const double Oc = recompute_O ? (alpha == 0.0 ? 1.0 : exp(alpha * P.ocone[P.n_orth + cI]))
-                                      : P.X.O[a];
+        const double Oc = recompute_O ? cond_scale(P.ocone[P.n_orth + cI], R) : P.X.O[a];
         for (int j = a + lane; j < e; j += 32) cond_apply_coord(P, j, Oc, recast);
     }
 }
@@ -766,16 +785,19 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(IterParams<T> P) {
             double mm[3];
             const int op[3] = {1, 1, 0};
             grid_combine<3>(P.partials, op, mm);
-            const double spread = mm[0] + mm[1];               // log max o - log min o
-            double alpha;
-            if (mm[2] > 0.0) alpha = 0.0;
-            else if (!(spread > 0.0)) alpha = 1.0;
-            else alpha = fmin(1.0, P.t_cond / spread);
-            phase_cond_apply(P, alpha, true, true);
+            CondRange R;
+            R.any = mm[2] > 0.0;                               // some o finite and positive
+            R.lmax = mm[0];
+            R.lmin = -mm[1];
+            const double spread = R.lmax - R.lmin;             // log max o - log min o
+            if (!R.any) R.alpha = 0.0;
+            else if (!(spread > 0.0)) R.alpha = 1.0;
+            else R.alpha = fmin(1.0, P.t_cond / spread);
+            phase_cond_apply(P, R, true, true);
             ACS_SYNC(PH_COND_APPLY);
             ++ncond;
         } else if (refresh) {
-            phase_cond_apply(P, 0.0, false, false);
+            phase_cond_apply(P, CondRange{0.0, 0.0, 0.0, false}, false, false);
             ACS_SYNC(PH_COND_APPLY);
         }
         if (cond || refresh) {

@@ -257,3 +257,47 @@ def test_large_lp_first_iteration_full_size():
         # sampled coordinates one by one
         idx = np.random.default_rng(0).choice(inst.n, 1000, replace=False)
         np.testing.assert_allclose(x[idx], xr[idx], atol=rtol * 10 * np.abs(xr).max())
+
+
+def _with_empty_columns(inst, c_extra):
+    """The instance with one empty column of A appended per entry of c_extra.
+    Column with c = 0: x_j = z_j = 0 from the first iteration on (o = nan);
+    column with c > 0: x_j = 0, z_j = c_j from the second one on (o = 0)."""
+    k = len(c_extra)
+    n = inst.n + k
+    x_star = np.concatenate([inst.x_star, np.zeros(k)])
+    s_star = np.concatenate([inst.s_star, np.asarray(c_extra, float)])
+    return I.Instance(m=inst.m, n=n, row_ptr=inst.row_ptr, col=inst.col, val=inst.val, b=inst.b,
+                      c=np.concatenate([inst.c, c_extra]), n_orth=n, soc_dims=inst.soc_dims,
+                      x_star=x_star, y_star=inst.y_star, s_star=s_star)
+
+
+def test_rescaling_with_degenerate_o():
+    """Algorithm 2 step 11 when some o_j is nan or 0: the exponent comes from
+    the finite positive o, the nan entry takes the middle scale and the o = 0
+    entry the smallest; iterates and O match the oracle through the rescale."""
+    inst = _with_empty_columns(I.small_lp(), [0.0, 0.7])
+    j_nan, j_zero = inst.n - 2, inst.n - 1
+    L = alg.Schedule(explicit=(3,))
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=L, max_iter=4, tol=0.0,
+                         keep_x=4)
+    l3, O_ref, a_ref = ref.O_history[1]
+    assert l3 == 3 and 0.0 < a_ref <= 1.0
+    kw = dict(precision=capi.PREC_FP64, cond_list=[3], cond_first=0, cg_eta=1e-12, cg_tol=0.0)
+    for k in (3, 4):
+        with capi.Solver(inst, **kw) as s:
+            s.solve(tol=0.0, max_iter=k)
+            rc, x, y, z, iters, res = s.get()
+            _, O, _, l, _ = capi.acs_get_state(s.h, inst.m, inst.n)
+        assert iters == k and l == k
+        xr = ref.x_history[k - 1]
+        assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr), (k, np.linalg.norm(x - xr))
+        np.testing.assert_allclose(O, O_ref, rtol=1e-9)
+        fin = np.delete(O, [j_nan, j_zero])
+        assert O[j_zero] == fin.min()
+        assert abs(O[j_nan] - math.sqrt(fin.max() * fin.min())) <= 1e-12 * O[j_nan]
+    st, x, y, z, iters, res = _solve(inst, tol=1e-6, cond_list=[3], **LP_SCHED)
+    assert st == capi.SOLVED
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
