@@ -211,6 +211,89 @@ int acs_kkt_residuals_noalloc(int32_t m, int32_t n, const int32_t* row_ptr, cons
                               const double* y, const double* z, int32_t n_orthant, int32_t n_soc,
                               const int32_t* soc_offsets, double* residuals, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent programs of uneven sizes in one
+ * persistent launch (replayed from a captured CUDA graph).
+ *
+ * Every member is an instance of Eq. (1) solved by Algorithm 2 exactly as
+ * acs_solve does (same settings for all members).  The launch is split into
+ * fixed teams of CTAs; a team takes the next member (largest first), runs
+ * its whole solve with team-local barriers and reductions (no grid-wide
+ * synchronisation), then takes the next.  Members that share one A (same
+ * pattern and values) keep a single device copy of it.
+ * ------------------------------------------------------------------------ */
+typedef struct acs_batch acs_batch;
+
+typedef struct {
+    int32_t m, n;            /* as in acs_problem_create                                  */
+    const int64_t* row_ptr;  /* host CSR of A (ignored when share_A_with >= 0)            */
+    const int32_t* col;
+    const double* val;
+    const double* b;         /* host, [m]                                                 */
+    const double* c;         /* host, [n]                                                 */
+    int32_t n_orthant, n_soc;
+    const int32_t* soc_dims; /* host, [n_soc]                                             */
+    int32_t share_A_with;    /* -1, or the index of an EARLIER member whose A this member
+                                reuses (same m and n; the caller guarantees equal data)   */
+} acs_instance;
+
+typedef struct {
+    int32_t threads_per_cta; /* 256, 512 or 1024                                          */
+    int32_t team_ctas;       /* CTAs per team: 1, 2, 4 or 8                               */
+} acs_batch_mapping;
+
+/*
+ * Create a batch of `count` >= 1 members (host data, copied; the pointers are
+ * read only during the call).  settings: as for acs_problem_create (NULL =
+ * defaults), shared by all members.  mapping: NULL = {1024, 1} until
+ * acs_batch_autotune picks one.
+ * Errors: ACS_ERR_ARG (also a bad share_A_with), ACS_ERR_CSR, ACS_ERR_CONES
+ * (the first failing member's code; *bad_member receives its index if not
+ * NULL), ACS_ERR_OOM, ACS_ERR_CUDA.
+ */
+int acs_batch_create(int32_t count, const acs_instance* members, const acs_settings* settings,
+                     const acs_batch_mapping* mapping, acs_batch** out, int32_t* bad_member);
+
+/* Solve every member from x = z = e to tol / max_iter (as acs_solve).  The
+ * first call with a given (tol, max_iter, mapping) captures the reset and
+ * the persistent launch into a CUDA graph; later calls replay it.  Blocks
+ * until done and returns ACS_SOLVED if every member was solved, ACS_MAX_ITER
+ * if some reached the limit, else the first member error.  The _async form
+ * only queues the work on the batch's stream. */
+int acs_batch_solve(acs_batch* b, double tol, int32_t max_iter);
+int acs_batch_solve_async(acs_batch* b, double tol, int32_t max_iter);
+
+/* Results of member i (as acs_get; any pointer may be NULL).  Waits for
+ * queued work.  Returns that member's status. */
+int acs_batch_get(acs_batch* b, int32_t i, double* x, double* y, double* s, int32_t* iters,
+                  double* residuals);
+
+/* Status, iterations and residuals[8] (as acs_get) of every member at once:
+ * status[count], iters[count], residuals[8 * count]; any may be NULL. */
+int acs_batch_results(acs_batch* b, int32_t* status, int32_t* iters, double* residuals);
+
+/* Time every candidate mapping (threads per CTA in {256, 512, 1024} x team
+ * sizes in {1, 2, 4}) on a truncated solve of the whole batch (max_iter
+ * iterations, no stopping test), keep the fastest and return it in *chosen
+ * (may be NULL); ms[9] (may be NULL) receives each candidate's time in the
+ * order threads-major, team-minor (negative = not launchable). */
+int acs_batch_autotune(acs_batch* b, int32_t max_iter, acs_batch_mapping* chosen, double* ms);
+
+/* Set the mapping explicitly (invalidates the captured graph). */
+int acs_batch_set_mapping(acs_batch* b, const acs_batch_mapping* mapping);
+
+/* Device time (ms) of the last batched launch (graph replay), from CUDA
+ * events on the batch's stream; waits for it. */
+int acs_batch_last_ms(acs_batch* b, double* ms);
+
+/* out8 = {members, distinct matrices, sum m, sum n, sum of stored nonzeros of
+ * distinct matrices, teams of the current mapping, CTAs, 1 if the last solve
+ * was replayed from a CUDA graph}.  counters6 (may be NULL): acs_debug_counters
+ * summed over members. */
+int acs_batch_info(acs_batch* b, long long* out8, long long* counters6);
+
+void acs_batch_destroy(acs_batch* b);
+
 /* Library version string. */
 const char* acs_version(void);
 

@@ -42,6 +42,20 @@ class acs_settings(C.Structure):
     ]
 
 
+class acs_instance(C.Structure):
+    _fields_ = [
+        ("m", C.c_int32), ("n", C.c_int32),
+        ("row_ptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+        ("val", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
+        ("c", C.POINTER(C.c_double)), ("n_orthant", C.c_int32), ("n_soc", C.c_int32),
+        ("soc_dims", C.POINTER(C.c_int32)), ("share_A_with", C.c_int32),
+    ]
+
+
+class acs_batch_mapping(C.Structure):
+    _fields_ = [("threads_per_cta", C.c_int32), ("team_ctas", C.c_int32)]
+
+
 class AcsError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {acs_status_string(code)} ({code})")
@@ -80,6 +94,19 @@ def lib():
         L.acs_kkt_residuals_noalloc.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, P, P,
                                                 C.c_int32, C.c_int32, P, P, P]
         L.acs_debug_phase_times.argtypes = [P, dp, C.POINTER(C.c_longlong), C.c_int32]
+        llp = C.POINTER(C.c_longlong)
+        L.acs_batch_create.argtypes = [C.c_int32, C.POINTER(acs_instance), C.POINTER(acs_settings),
+                                       C.POINTER(acs_batch_mapping), C.POINTER(P), ip]
+        L.acs_batch_solve.argtypes = [P, C.c_double, C.c_int32]
+        L.acs_batch_solve_async.argtypes = [P, C.c_double, C.c_int32]
+        L.acs_batch_get.argtypes = [P, C.c_int32, dp, dp, dp, ip, dp]
+        L.acs_batch_results.argtypes = [P, ip, ip, dp]
+        L.acs_batch_autotune.argtypes = [P, C.c_int32, C.POINTER(acs_batch_mapping), dp]
+        L.acs_batch_set_mapping.argtypes = [P, C.POINTER(acs_batch_mapping)]
+        L.acs_batch_last_ms.argtypes = [P, dp]
+        L.acs_batch_info.argtypes = [P, llp, llp]
+        L.acs_batch_destroy.argtypes = [P]
+        L.acs_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -273,6 +300,183 @@ class Solver:
 
     def close(self):
         acs_problem_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# batched solves
+# ---------------------------------------------------------------------------
+
+def acs_batch_create(instances, settings=None, mapping=None, share=None):
+    """instances: objects with m, n, row_ptr, col, val, b, c, n_orth, soc_dims.
+    share[i] = index of an earlier member whose A member i reuses, or -1.
+    Returns an opaque handle; raises AcsError (with .member) on failure."""
+    count = len(instances)
+    arr = (acs_instance * count)()
+    keep = []
+    for i, inst in enumerate(instances):
+        j = -1 if share is None else int(share[i])
+        a = arr[i]
+        a.m, a.n = int(inst.m), int(inst.n)
+        if j < 0:
+            rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(inst.col, dtype=np.int32)
+            vl = np.ascontiguousarray(inst.val, dtype=np.float64)
+            keep += [rp, cl, vl]
+            a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)
+        b = np.ascontiguousarray(inst.b, dtype=np.float64)
+        c = np.ascontiguousarray(inst.c, dtype=np.float64)
+        d = np.ascontiguousarray(inst.soc_dims, dtype=np.int32)
+        keep += [b, c, d]
+        a.b, a.c = _ptr(b, C.c_double), _ptr(c, C.c_double)
+        a.n_orthant, a.n_soc = int(inst.n_orth), int(d.size)
+        a.soc_dims = _ptr(d, C.c_int32)
+        a.share_A_with = j
+    h = C.c_void_p()
+    bad = C.c_int32(-1)
+    mp = None
+    if mapping is not None:
+        mp = acs_batch_mapping(int(mapping[0]), int(mapping[1]))
+    rc = lib().acs_batch_create(count, arr, C.byref(settings) if settings is not None else None,
+                                C.byref(mp) if mp is not None else None, C.byref(h), C.byref(bad))
+    if rc != 0:
+        err = AcsError(rc, f"acs_batch_create (member {bad.value})")
+        err.member = bad.value
+        raise err
+    return h.value
+
+
+def acs_batch_solve(h, tol: float, max_iter: int) -> int:
+    return lib().acs_batch_solve(C.c_void_p(h), float(tol), int(max_iter))
+
+
+def acs_batch_solve_async(h, tol: float, max_iter: int) -> int:
+    rc = lib().acs_batch_solve_async(C.c_void_p(h), float(tol), int(max_iter))
+    if rc < 0:
+        raise AcsError(rc, "acs_batch_solve_async")
+    return rc
+
+
+def acs_batch_get(h, i: int, m: int, n: int):
+    """(status, x, y, s, iters, residuals[8]) of member i."""
+    x, y, s, res = np.empty(n), np.empty(m), np.empty(n), np.empty(8)
+    it = C.c_int32()
+    rc = lib().acs_batch_get(C.c_void_p(h), int(i), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                             _ptr(s, C.c_double), C.byref(it), _ptr(res, C.c_double))
+    return rc, x, y, s, it.value, res
+
+
+def acs_batch_results(h, count: int):
+    """(worst status, status[count], iters[count], residuals[count, 8])."""
+    st = np.empty(count, np.int32)
+    it = np.empty(count, np.int32)
+    res = np.empty((count, 8))
+    rc = lib().acs_batch_results(C.c_void_p(h), _ptr(st, C.c_int32), _ptr(it, C.c_int32),
+                                 _ptr(res, C.c_double))
+    return rc, st, it, res
+
+
+def acs_batch_autotune(h, max_iter: int = 30):
+    """(chosen (threads, team), ms[3, 3]: rows threads 256/512/1024, cols team 1/2/4)."""
+    m = acs_batch_mapping()
+    ms = np.empty(9)
+    rc = lib().acs_batch_autotune(C.c_void_p(h), int(max_iter), C.byref(m), _ptr(ms, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_autotune")
+    return (m.threads_per_cta, m.team_ctas), ms.reshape(3, 3)
+
+
+def acs_batch_set_mapping(h, threads: int, team: int) -> None:
+    m = acs_batch_mapping(int(threads), int(team))
+    rc = lib().acs_batch_set_mapping(C.c_void_p(h), C.byref(m))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_set_mapping")
+
+
+def acs_batch_last_ms(h) -> float:
+    ms = C.c_double()
+    rc = lib().acs_batch_last_ms(C.c_void_p(h), C.byref(ms))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_last_ms")
+    return ms.value
+
+
+def acs_batch_info(h) -> dict:
+    out = np.zeros(8, dtype=np.int64)
+    cnt = np.zeros(6, dtype=np.int64)
+    llp = C.POINTER(C.c_longlong)
+    rc = lib().acs_batch_info(C.c_void_p(h), out.ctypes.data_as(llp), cnt.ctypes.data_as(llp))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_info")
+    keys = ("members", "matrices", "sum_m", "sum_n", "stored_nnz", "teams", "ctas", "graph")
+    d = dict(zip(keys, out.tolist()))
+    d["counters"] = cnt
+    return d
+
+
+def acs_batch_destroy(h) -> None:
+    if h:
+        lib().acs_batch_destroy(C.c_void_p(h))
+
+
+def shared_A_index(instances):
+    """share[i] for acs_batch_create: the first earlier member whose A has the
+    same shape, pattern and values (compared exactly), else -1."""
+    share = [-1] * len(instances)
+    seen = {}
+    for i, inst in enumerate(instances):
+        key = (inst.m, inst.n, inst.row_ptr[-1])
+        for j in seen.get(key, ()):
+            o = instances[j]
+            if (np.array_equal(o.row_ptr, inst.row_ptr) and np.array_equal(o.col, inst.col)
+                    and np.array_equal(o.val, inst.val)):
+                share[i] = j
+                break
+        else:
+            seen.setdefault(key, []).append(i)
+    return share
+
+
+class Batch:
+    """Owner of one batch handle."""
+
+    def __init__(self, instances, settings=None, mapping=None, share="auto", **overrides):
+        if settings is None:
+            settings = acs_settings_default(**overrides)
+        if share == "auto":
+            share = shared_A_index(instances)
+        self.count = len(instances)
+        self.shapes = [(int(i.m), int(i.n)) for i in instances]
+        self.h = acs_batch_create(instances, settings, mapping, share)
+
+    def solve(self, tol=1e-6, max_iter=10000) -> int:
+        return acs_batch_solve(self.h, tol, max_iter)
+
+    def solve_async(self, tol=1e-6, max_iter=10000) -> int:
+        return acs_batch_solve_async(self.h, tol, max_iter)
+
+    def get(self, i):
+        m, n = self.shapes[i]
+        return acs_batch_get(self.h, i, m, n)
+
+    def results(self):
+        return acs_batch_results(self.h, self.count)
+
+    def close(self):
+        acs_batch_destroy(self.h)
         self.h = None
 
     def __enter__(self):

@@ -10,9 +10,12 @@
 #include <new>
 #include <vector>
 
+#include "acs_host.cuh"
 #include "acs_internal.cuh"
 
 using acs::Problem;
+using acs::host::HostSell;
+using acs::host::finite_all;
 
 namespace {
 
@@ -40,61 +43,6 @@ int upload(Problem* P, T* dst, const T* src, size_t count) {
     return ACS_SOLVED;
 }
 
-// Host image of a sliced-ELLPACK matrix with G lanes per row (layout in
-// acs_internal.cuh).
-struct HostSell {
-    int nrows = 0, nslices = 0, g = 1;
-    std::vector<int> sptr, slen, col;
-    std::vector<double> val;
-};
-
-// Rows are given by (beg[r], end[r]) ranges into (cols, vals); padding
-// entries repeat column 0 with value 0.
-HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, const std::vector<long long>& end,
-                    const int* cols, const double* vals) {
-    HostSell H;
-    const int h = 32 / g;                     // rows per slice
-    H.nrows = nrows;
-    H.g = g;
-    H.nslices = (nrows + h - 1) / h;
-    H.sptr.assign(H.nslices + 1, 0);
-    H.slen.assign(H.nslices, 0);
-    long long total = 0;
-    for (int sl = 0; sl < H.nslices; ++sl) {
-        long long mx = 0;
-        for (int r = sl * h; r < std::min(nrows, sl * h + h); ++r) mx = std::max(mx, end[r] - beg[r]);
-        const long long chunks = (mx + g - 1) / g;
-        H.slen[sl] = (int)chunks;
-        H.sptr[sl] = (int)std::min<long long>(total, INT32_MAX);
-        total += 32 * chunks;
-    }
-    H.sptr[H.nslices] = (int)std::min<long long>(total, INT32_MAX);
-    if (total >= INT32_MAX) { H.col.clear(); H.nslices = -1; return H; }
-    H.col.assign(total, 0);
-    H.val.assign(total, 0.0);
-    for (int sl = 0; sl < H.nslices; ++sl)
-        for (int lr = 0; lr < h; ++lr) {
-            const int r = sl * h + lr;
-            if (r >= nrows) break;
-            long long k = 0;
-            for (long long e = beg[r]; e < end[r]; ++e, ++k) {
-                const long long idx = H.sptr[sl] + 32 * (k / g) + lr * g + (k % g);
-                H.col[idx] = cols[e];
-                H.val[idx] = vals[e];
-            }
-        }
-    return H;
-}
-
-// Lanes per row: enough slices for four per warp of the persistent grid (load
-// balance), but no more lanes than about half the average row length.
-int choose_g(long long nrows, long long nnz, long long warps) {
-    const double avg = nrows > 0 ? (double)nnz / (double)nrows : 1.0;
-    int g = 1;
-    while (g < 32 && (nrows * g) / 32 < 4 * warps && 2 * g <= avg) g *= 2;
-    return g;
-}
-
 int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     int* sptr = nullptr; int* slen = nullptr; int* col = nullptr;
     float* v32 = nullptr; double* v64 = nullptr;
@@ -115,14 +63,6 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     M.nrows = H.nrows; M.nslices = H.nslices; M.g = H.g;
     M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64;
     return ACS_SOLVED;
-}
-
-constexpr int kSortWindow = 2048;   // rows of A are sorted by length within windows of this size
-
-bool finite_all(const double* v, size_t n) {
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
 }
 
 template <typename T>
@@ -219,32 +159,9 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         (set.n_cond_list > 0 && !set.cond_list) ||
         (set.precision != ACS_PREC_MIXED && set.precision != ACS_PREC_FP64))
         return ACS_ERR_ARG;
-    // CSR
-    if (row_ptr[0] != 0) return ACS_ERR_CSR;
-    for (int i = 0; i < m; ++i)
-        if (row_ptr[i + 1] <= row_ptr[i]) return ACS_ERR_CSR;    // non-monotone or empty row
-    const int64_t nnz64 = row_ptr[m];
-    if (nnz64 <= 0 || nnz64 >= (int64_t)1 << 31) return ACS_ERR_CSR;
-    if (!col || !val) return ACS_ERR_ARG;
-    const int nnz = (int)nnz64;
-    for (int i = 0; i < m; ++i) {
-        int prev = -1;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            const int j = col[k];
-            if (j < 0 || j >= n || j <= prev) return ACS_ERR_CSR;
-            prev = j;
-        }
-    }
-    if (!finite_all(val, nnz) || !finite_all(b, m) || !finite_all(c, n)) return ACS_ERR_ARG;
-    // cones
-    if (n_orthant < 0 || n_soc < 0 || (n_soc > 0 && !soc_dims)) return ACS_ERR_CONES;
-    int64_t tot = n_orthant;
-    for (int i = 0; i < n_soc; ++i) {
-        if (soc_dims[i] < 2) return ACS_ERR_CONES;
-        tot += soc_dims[i];
-    }
-    if (tot != n) return ACS_ERR_CONES;
-
+    const int vrc = acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims);
+    if (vrc != ACS_SOLVED) return vrc;
+    const int nnz = (int)row_ptr[m];
     Problem* P = new (std::nothrow) Problem();
     if (!P) return ACS_ERR_OOM;
     P->m = m; P->n = n; P->nnz = nnz; P->n_orth = n_orthant; P->n_soc = n_soc;
@@ -262,60 +179,19 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     int rc = ACS_SOLVED;
     if (acs::occupancy_grid(P) != ACS_SOLVED) { free_all(P); delete P; return ACS_ERR_CUDA; }
     const long long warps = (long long)P->grid32 * acs::kThreads / 32;
-    // relabel the constraints: sort rows by length (descending) within windows,
-    // so that the 32 rows of a slice have similar lengths and padding is small
-    std::vector<int>& perm = P->perm;
-    perm.resize(m);
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int w0 = 0; w0 < m; w0 += kSortWindow) {
-        const int w1 = std::min(m, w0 + kSortWindow);
-        std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b2) {
-            return (row_ptr[a + 1] - row_ptr[a]) > (row_ptr[b2 + 1] - row_ptr[b2]);
-        });
-    }
-    std::vector<int> inv(m);
-    for (int r = 0; r < m; ++r) inv[perm[r]] = r;
-    HostSell HA, HT;
-    {
-        std::vector<long long> beg(m), end(m);
-        for (int r = 0; r < m; ++r) { beg[r] = row_ptr[perm[r]]; end[r] = row_ptr[perm[r] + 1]; }
-        HA = build_sell(m, choose_g(m, nnz, warps), beg, end, col, val);
-    }
-    {
-        // A' by counting sort over the relabelled rows: row j of A' lists the
-        // relabelled constraints touching coordinate j in increasing order
-        std::vector<long long> rpT(n + 1, 0);
-        for (int k = 0; k < nnz; ++k) rpT[col[k] + 1]++;
-        for (int j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
-        std::vector<int> ciT(nnz);
-        std::vector<double> valT(nnz);
-        std::vector<long long> cur(rpT.begin(), rpT.end() - 1);
-        for (int r = 0; r < m; ++r) {
-            const int i = perm[r];
-            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const long long pos = cur[col[k]]++;
-                ciT[pos] = r;
-                valT[pos] = val[k];
-            }
-        }
-        std::vector<long long> beg(rpT.begin(), rpT.end() - 1), end(rpT.begin() + 1, rpT.end());
-        HT = build_sell(n, choose_g(n, nnz, warps), beg, end, ciT.data(), valT.data());
-    }
-    if (HA.nslices < 0 || HT.nslices < 0) {
+    acs::host::HostProblem H;
+    if (acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H) != ACS_SOLVED) {
         free_all(P); delete P; return ACS_ERR_CSR;
     }
-    P->padded_A = (long long)HA.col.size();
-    P->padded_AT = (long long)HT.col.size();
-    std::vector<double> bperm(m);
-    for (int r = 0; r < m; ++r) bperm[r] = b[perm[r]];
-    std::vector<int> off(n_soc + 1);
-    off[0] = n_orthant;
-    for (int i = 0; i < n_soc; ++i) off[i + 1] = off[i] + soc_dims[i];
-    double bn = 0, cn = 0;
-    for (int i = 0; i < m; ++i) bn += b[i] * b[i];
-    for (int j = 0; j < n; ++j) cn += c[j] * c[j];
-    P->bnorm = sqrt(bn);
-    P->cnorm = sqrt(cn);
+    P->perm = H.perm;
+    P->padded_A = (long long)H.A.col.size();
+    P->padded_AT = (long long)H.AT.col.size();
+    P->bnorm = H.bnorm;
+    P->cnorm = H.cnorm;
+    const HostSell& HA = H.A;
+    const HostSell& HT = H.AT;
+    const std::vector<double>& bperm = H.bperm;
+    const std::vector<int>& off = H.soc_off;
 
     if (upload_sell(P, HA, P->A) || upload_sell(P, HT, P->AT)) { free_all(P); delete P; return ACS_ERR_OOM; }
     rc |= dalloc(P, &P->soc_off, n_soc + 1);

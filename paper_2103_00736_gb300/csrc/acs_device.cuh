@@ -1,0 +1,951 @@
+// Device code of the conic solver shared by the single-problem launch
+// (acs_iter.cu: one team = the whole grid) and the batched launch
+// (acs_batch.cu: one team of CTAs per problem): grid/team barriers and
+// reductions, sliced-ELLPACK products, the phases of Algorithm 2 and the
+// solve loop.  See acs_iter.cu for the method and the precision scheme.
+#pragma once
+
+#include <math.h>
+#include <stdio.h>
+
+#include "acs_internal.cuh"
+
+namespace acs {
+
+// ---------------------------------------------------------------------------
+// synchronisation and reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+
+// Grid-wide reduction and barrier.
+//
+// A phase leaves its contributions to a reduction in shared memory
+// (block_partials: warp shuffles, then one warp combines the warps in fixed
+// order).  grid_sync then publishes this CTA's partials followed by an
+// arrival flag holding the barrier generation; thread b of every CTA waits
+// for the flag of CTA b and loads CTA b's partials, and the CTA combines them
+// in CTA order (a fixed shuffle tree, then the warps in order).  Every CTA
+// thus computes bit-identical reduced values (deterministic for a given
+// launch shape) after a single one-way flag latency.  All waits are bounded
+// (kBarrierTimeoutNs): on expiry, or when another CTA has recorded an error,
+// the wait records ACS_ERR_DEVICE_TIMEOUT and grid_sync returns false in
+// every thread; the caller then leaves the kernel.
+constexpr int kMaxGrid = 256;   // CTAs of a persistent launch (one per SM)
+
+struct SyncShared {
+    int team_rank;            // this CTA's rank in the team working on one problem
+    int team_size;            // CTAs in the team (the whole grid for a single solve)
+    unsigned long long* bar;  // the team's monotonic barrier arrival counter
+    double* tpart;            // the team's partials, [team_size * kMaxRed]
+    double blk[kMaxRed];      // this CTA's partials
+    double out[kMaxRed];      // grid-reduced values of the last barrier
+    double wsum[kWarps][kMaxRed];
+    double gath[kMaxRed][kMaxGrid];   // every CTA's partials, gathered
+    int op[kMaxRed];          // 0 = sum, 1 = max
+    int nv;                   // number of values reduced at the next barrier
+    int fail;
+    unsigned gen;             // barrier generation (same sequence in every CTA)
+};
+
+__device__ __forceinline__ SyncShared& sync_smem() {
+    __shared__ SyncShared s;
+    return s;
+}
+
+// A team is the set of CTAs that work on one problem: the whole grid of a
+// single-problem launch, or a group of CTAs (often one) of a batched launch.
+// Phases index coordinates, rows and cones by the thread's rank in its team.
+__device__ __forceinline__ void team_set(int rank, int size, unsigned long long* bar, double* partials) {
+    SyncShared& S = sync_smem();
+    if (threadIdx.x == 0) {
+        S.team_rank = rank;
+        S.team_size = size;
+        S.bar = bar;
+        S.tpart = partials;
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ int team_rank() { return sync_smem().team_rank; }
+__device__ __forceinline__ int team_size() { return sync_smem().team_size; }
+__device__ __forceinline__ int global_tid() { return team_rank() * (int)blockDim.x + (int)threadIdx.x; }
+__device__ __forceinline__ int global_threads() { return team_size() * (int)blockDim.x; }
+__device__ __forceinline__ int global_warp() { return global_tid() >> 5; }
+__device__ __forceinline__ int global_warps() { return global_threads() >> 5; }
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Stage this CTA's contribution to the values reduced at the next grid_sync.
+template <int NV>
+__device__ void block_partials(const double (&v)[NV], const int (&op)[NV], double* /*unused*/) {
+    SyncShared& S = sync_smem();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double x = op[k] ? warp_max(v[k]) : warp_sum(v[k]);
+        if (lane == 0) S.wsum[warp][k] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = (lane < (int)(blockDim.x >> 5)) ? S.wsum[lane][k] : (op[k] ? -INFINITY : 0.0);
+            x = op[k] ? warp_max(x) : warp_sum(x);
+            if (lane == 0) {
+                S.blk[k] = x;
+                S.op[k] = op[k];
+            }
+        }
+        if (lane == 0) S.nv = NV;
+    }
+}
+
+// Start (or resume, with the generation reached so far) the team's barrier
+// sequence and clear the failure flag.
+static __device__ void sync_init(unsigned gen) {
+    SyncShared& S = sync_smem();
+    if (threadIdx.x == 0) {
+        S.nv = 0;
+        S.fail = 0;
+        S.gen = gen;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void red_add_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier: thread 0 of every CTA of the team publishes the CTA's partials,
+// adds 1 to the team's monotonic arrival counter with release semantics and
+// spins (acquire) until the counter reaches (generation) * (CTAs in the team).
+// A team of one CTA needs no counter: its partials are already combined.  One thread per CTA polls a
+// single word, which keeps the barrier at about the latency of two L2 round
+// trips.  The partials of all CTAs are then read once, in parallel.
+static __device__ __noinline__ bool grid_sync(int* err) {
+    SyncShared& S = sync_smem();
+    __syncthreads();                                   // the phase's writes and S.blk are complete
+    const unsigned target = S.gen + 1u;
+    const int nv = S.nv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rank = S.team_rank, size = S.team_size;
+    if (size == 1) {
+        // writes of the phase are visible to the CTA after __syncthreads; the
+        // error word is still checked so that a failed problem stops
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < nv; ++k) S.out[k] = S.blk[k];
+            if (ld_volatile_int(err) != 0) S.fail = 1;
+        }
+        __syncthreads();
+        const bool ok1 = S.fail == 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.gen = target;
+            S.nv = 0;
+        }
+        return ok1;
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < nv; ++k) S.tpart[rank * kMaxRed + k] = S.blk[k];
+        red_add_release(S.bar, 1ull);
+        const unsigned long long want = (unsigned long long)target * size;
+        const unsigned long long t0 = gtimer();
+        int spins = 0;
+        while (ld_acquire64(S.bar) < want) {
+            if (++spins == 64) {
+                spins = 0;
+                if (ld_volatile_int(err) != 0) { S.fail = 1; break; }
+                if (gtimer() - t0 > kBarrierTimeoutNs) {
+                    atomicCAS(err, 0, ACS_ERR_DEVICE_TIMEOUT);
+                    S.fail = 1;
+                    break;
+                }
+            }
+        }
+        if (ld_volatile_int(err) != 0) S.fail = 1;
+    }
+    __syncthreads();
+    if (nv > 0) {
+        // gather every CTA's partials, combine in CTA order: lanes by a fixed
+        // shuffle tree, then the warps in order
+        const int b = threadIdx.x;
+        if (b < size)
+            for (int k = 0; k < nv; ++k) S.gath[k][b] = __ldcg(S.tpart + b * kMaxRed + k);
+        __syncthreads();
+        const int nwarp = (size + 31) >> 5;
+        if (warp < nwarp) {
+            for (int k = 0; k < nv; ++k) {
+                const int opk = S.op[k];
+                double x = (b < size) ? S.gath[k][b] : (opk ? -INFINITY : 0.0);
+                x = opk ? warp_max(x) : warp_sum(x);
+                if (lane == 0) S.wsum[warp][k] = x;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            const int k = threadIdx.x;
+            const int opk = S.op[k];
+            double x = S.wsum[0][k];
+            for (int w = 1; w < nwarp; ++w) x = opk ? fmax(x, S.wsum[w][k]) : x + S.wsum[w][k];
+            S.out[k] = x;
+        }
+    }
+    __syncthreads();
+    const bool ok = S.fail == 0;
+    __syncthreads();                                   // everyone has read S.fail and S.out is final
+    if (threadIdx.x == 0) {
+        S.gen = target;
+        S.nv = 0;
+    }
+    return ok;
+}
+
+// Values reduced at the last grid_sync.
+template <int NV>
+__device__ void grid_combine(const double* /*unused*/, const int (&)[NV], double (&out)[NV]) {
+    SyncShared& S = sync_smem();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = S.out[k];
+}
+
+// ---------------------------------------------------------------------------
+// row-parallel sparse products (sliced ELLPACK with G lanes per row)
+// ---------------------------------------------------------------------------
+
+// Matrix entries are read once per pass: stream them past L1.
+__device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+
+template <typename T> __device__ __forceinline__ const T* sell_vals(const SellMat& M);
+template <> __device__ __forceinline__ const float* sell_vals<float>(const SellMat& M) { return M.v32; }
+template <> __device__ __forceinline__ const double* sell_vals<double>(const SellMat& M) { return M.v64; }
+
+// Layout (see SellMat): a slice holds 32/G rows; chunk c of the slice is 32
+// consecutive entries, entry k of local row r at chunk k/G, lane r*G + k%G.
+// Warp w handles slices w, w + nwarps, ..., in batches of U chunks; each lane
+// accumulates its entries in chunk order, and the G partial sums of a row are
+// combined by a fixed shuffle tree, so the result does not depend on the
+// launch shape.  epi(row, sum) runs once per real row.
+//
+// Software pipeline: the column/value loads of the next batch (and the slice
+// table entries of the next slice) are issued before the gathers of the
+// current batch, so a warp keeps one matrix round trip and one gather round
+// trip in flight at the same time instead of one after the other.
+template <int U, typename T>
+__device__ __forceinline__ void sell_load_batch(const int* __restrict__ col, const T* __restrict__ val,
+                                                int base, int k, int len, int (&c)[U], T (&a)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (k + u < len) {
+            c[u] = ld_stream(col + base + 32 * (k + u));
+            a[u] = ld_stream(val + base + 32 * (k + u));
+        } else {
+            c[u] = 0;
+            a[u] = T(0);
+        }
+    }
+}
+
+template <int G, int U, typename T, typename Gather, typename Epi>
+__device__ __forceinline__ void sell_rows_g(const SellMat& M, Gather gather, Epi epi) {
+    const T* __restrict__ val = sell_vals<T>(M);
+    const int* __restrict__ col = M.col;
+    const int lane = threadIdx.x & 31;
+    const int nw = global_warps();
+    int sl = global_warp();
+    if (sl >= M.nslices) return;                        // warp-uniform
+    int len = __ldg(M.slen + sl);
+    int base = __ldg(M.sptr + sl) + lane;
+    int k = 0;
+    // slice table entries of the following slice, loaded one slice ahead
+    int nsl = sl + nw;
+    int nlen = 0, nbase = 0;
+    if (nsl < M.nslices) {
+        nlen = __ldg(M.slen + nsl);
+        nbase = __ldg(M.sptr + nsl) + lane;
+    }
+    int c[U];
+    T a[U];
+    sell_load_batch<U>(col, val, base, k, len, c, a);
+    T acc = T(0);
+    while (true) {
+        // next batch: more chunks of this slice, or the first of the next slice
+        const bool same = k + U < len;
+        const bool have_next = same || nsl < M.nslices;
+        int c2[U];
+        T a2[U];
+        if (same) sell_load_batch<U>(col, val, base, k + U, len, c2, a2);
+        else if (have_next) sell_load_batch<U>(col, val, nbase, 0, nlen, c2, a2);
+        T x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = gather(c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc = fma(a[u], x[u], acc);
+        if (!same) {                                    // slice finished
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const int row = sl * (32 / G) + lane / G;
+            if ((lane & (G - 1)) == 0 && row < M.nrows) epi(row, acc);
+            acc = T(0);
+            if (!have_next) break;
+            sl = nsl;
+            len = nlen;
+            base = nbase;
+            k = 0;
+            nsl = sl + nw;
+            if (nsl < M.nslices) {
+                nlen = __ldg(M.slen + nsl);
+                nbase = __ldg(M.sptr + nsl) + lane;
+            }
+        } else {
+            k += U;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = c2[u];
+            a[u] = a2[u];
+        }
+    }
+}
+
+template <typename T, typename Gather, typename Epi>
+__device__ __forceinline__ void sell_rows(const SellMat& M, Gather gather, Epi epi) {
+    constexpr int U = 4;
+    switch (M.g) {
+        case 1: sell_rows_g<1, U, T>(M, gather, epi); break;
+        case 2: sell_rows_g<2, U, T>(M, gather, epi); break;
+        case 4: sell_rows_g<4, U, T>(M, gather, epi); break;
+        case 8: sell_rows_g<8, U, T>(M, gather, epi); break;
+        case 16: sell_rows_g<16, U, T>(M, gather, epi); break;
+        default: sell_rows_g<32, U, T>(M, gather, epi); break;
+    }
+}
+
+// Two sums per row: sum a*g1(j) and sum a*a*g2(j) (FP64 values).
+template <int G, typename G1, typename G2, typename Epi>
+__device__ __forceinline__ void sell_rows2_g(const SellMat& M, G1 g1, G2 g2, Epi epi) {
+    const int lane = threadIdx.x & 31;
+    const int nw = global_warps();
+    for (int sl = global_warp(); sl < M.nslices; sl += nw) {
+        const int len = __ldg(M.slen + sl);
+        int idx = __ldg(M.sptr + sl) + lane;
+        double acc1 = 0.0, acc2 = 0.0;
+        for (int k = 0; k < len; ++k, idx += 32) {
+            const int j = ld_stream(M.col + idx);
+            const double a = ld_stream(M.v64 + idx);
+            acc1 = fma(a, g1(j), acc1);
+            acc2 = fma(a * a, g2(j), acc2);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+        }
+        const int row = sl * (32 / G) + lane / G;
+        if ((lane & (G - 1)) == 0 && row < M.nrows) epi(row, acc1, acc2);
+    }
+}
+
+template <typename G1, typename G2, typename Epi>
+__device__ __forceinline__ void sell_rows2(const SellMat& M, G1 g1, G2 g2, Epi epi) {
+    switch (M.g) {
+        case 1: sell_rows2_g<1>(M, g1, g2, epi); break;
+        case 2: sell_rows2_g<2>(M, g1, g2, epi); break;
+        case 4: sell_rows2_g<4>(M, g1, g2, epi); break;
+        case 8: sell_rows2_g<8>(M, g1, g2, epi); break;
+        case 16: sell_rows2_g<16>(M, g1, g2, epi); break;
+        default: sell_rows2_g<32>(M, g1, g2, epi); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cone helpers
+// ---------------------------------------------------------------------------
+
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Is iteration l in the schedule L (Algorithm 2 step 4, without the {1})?
+template <typename T>
+__device__ __forceinline__ bool in_schedule(const IterParams<T>& P, int l) {
+    for (int i = 0; i < P.n_cond_list; ++i)
+        if (__ldg(P.cond_list + i) == l) return true;
+    if (P.cond_first > 0 && l >= P.cond_first) {
+        if (P.cond_period <= 0) return l == P.cond_first;
+        return (l - P.cond_first) % P.cond_period == 0;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// phases
+// ---------------------------------------------------------------------------
+
+// Conditioning, steps 5-10: o per cone, o = |x_h - ||xbar||| / |z_h|, stored
+// as log o (log 0 = -inf, log inf = inf, nan stays nan); partials over the
+// finite positive o: max log o, max(-log o), and their count.
+template <typename T>
+__device__ __noinline__ void phase_cond_o(const IterParams<T>& P) {
+    double vmax = -INFINITY, vneg = -INFINITY, good = 0.0;
+    for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
+        const double o = fabs(P.x[j]) / fabs(P.z[j]);
+        const double lo = log(o);
+        P.ocone[j] = lo;
+        if (o > 0.0 && o < INFINITY) {
+            good += 1.0;
+            vmax = fmax(vmax, lo);
+            vneg = fmax(vneg, -lo);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
+        const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
+        double ss = 0.0;
+        for (int j = a + 1 + lane; j < e; j += 32) ss = fma(P.x[j], P.x[j], ss);
+        ss = warp_sum(ss);
+        if (lane == 0) {
+            const double o = fabs(P.x[a] - sqrt(ss)) / fabs(P.z[a]);
+            const double lo = log(o);
+            P.ocone[P.n_orth + cI] = lo;
+            if (o > 0.0 && o < INFINITY) {
+                good += 1.0;
+                vmax = fmax(vmax, lo);
+                vneg = fmax(vneg, -lo);
+            }
+        }
+    }
+    const double v[3] = {vmax, vneg, good};
+    const int op[3] = {1, 1, 0};
+    block_partials<3>(v, op, P.partials);
+}
+
+// Exponent range of step 11 over the finite positive o.  An o of 0, inf or
+// nan (x_h = ||xbar||, z_h = 0, or both) carries no scale: it takes the
+// limit of the rule under the e^t cap -- the smallest scale for o = 0, the
+// largest for o = inf, the geometric middle for nan.  With no finite
+// positive o at all, O = I.
+struct CondRange {
+    double alpha, lmin, lmax;
+    bool any;
+};
+__device__ __forceinline__ double cond_scale(double lo, const CondRange& R) {
+    if (!R.any) return 1.0;
+    double e = lo;
+    if (isnan(lo)) e = 0.5 * (R.lmin + R.lmax);
+    else if (lo == -INFINITY) e = R.lmin;
+    else if (lo == INFINITY) e = R.lmax;
+    return exp(R.alpha * e);
+}
+
+// Steps 11-14 per coordinate: O = exp(alpha log o) (see cond_scale),
+// c_hat = O c, s = x/O - mu O z; g = O c_hat (input of the b_tilde pass).
+template <typename T>
+__device__ __forceinline__ void cond_apply_coord(const IterParams<T>& P, int j, double Oj, bool recast) {
+    P.X.O[j] = Oj;
+    P.V.O2[j] = (T)(Oj * Oj);
+    const double ch = Oj * P.c[j];
+    P.X.chat[j] = ch;
+    P.X.g[j] = Oj * ch;
+    if (recast) P.X.s[j] = P.x[j] / Oj - P.mu * Oj * P.z[j];
+}
+
+template <typename T>
+__device__ __noinline__ void phase_cond_apply(const IterParams<T>& P, const CondRange& R, bool recompute_O,
+                                              bool recast) {
+    for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
+        const double Oj = recompute_O ? cond_scale(P.ocone[j], R) : P.X.O[j];
+        cond_apply_coord(P, j, Oj, recast);
+    }
+    const int lane = threadIdx.x & 31;
+    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
+        const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
+        const double Oc = recompute_O ? cond_scale(P.ocone[P.n_orth + cI], R) : P.X.O[a];
+        for (int j = a + lane; j < e; j += 32) cond_apply_coord(P, j, Oc, recast);
+    }
+}
+
+// b_tilde = b + mu A (O c_hat), J^{-1} = 1 / diag(A_hat A_hat') (FP64 pass);
+// partial count of nonpositive diagonal entries.
+template <typename T>
+__device__ __noinline__ void phase_btilde(const IterParams<T>& P) {
+    double bad = 0.0;
+    const double* g = P.X.g;
+    const double* O = P.X.O;
+    auto g1 = [g](int j) { return g[j]; };
+    auto g2 = [O](int j) { const double o = O[j]; return o * o; };
+    auto epi = [&](int i, double s1, double s2) {
+        P.X.btil[i] = P.b[i] + P.mu * s1;
+        if (!(s2 > 0.0)) { bad += 1.0; P.V.jinv[i] = T(1); }
+        else P.V.jinv[i] = (T)(1.0 / s2);
+    };
+    sell_rows2(P.A, g1, g2, epi);
+    const double v[1] = {bad};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// Step 17: p = abs_K(s); g = O (p + q) for the warm-started right-hand side.
+// Lorentz cone (v1, vbar), t = ||vbar||: inside (t <= v1) abs = v; polar
+// (t <= -v1) abs = -v; otherwise abs = (t, (v1/t) vbar), which is 2 proj - v
+// for proj = ((v1 + t)/2)(1, vbar/t).
+template <typename T>
+__device__ __noinline__ void phase_abs(const IterParams<T>& P) {
+    const Outer& X = P.X;
+    for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
+        const double pj = fabs(X.s[j]);
+        X.p[j] = pj;
+        X.g[j] = X.O[j] * (pj + X.q[j]);
+    }
+    const int lane = threadIdx.x & 31;
+    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
+        const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
+        double ss = 0.0;
+        for (int j = a + 1 + lane; j < e; j += 32) ss = fma(X.s[j], X.s[j], ss);
+        ss = warp_sum(ss);
+        const double t = sqrt(ss);
+        const double v1 = X.s[a];
+        double ftail, head;
+        if (t <= v1) { ftail = 1.0; head = v1; }
+        else if (t <= -v1) { ftail = -1.0; head = -v1; }
+        else { ftail = v1 / t; head = t; }
+        const double Oc = X.O[a];
+        for (int j = a + lane; j < e; j += 32) {
+            const double pj = (j == a) ? head : ftail * X.s[j];
+            X.p[j] = pj;
+            X.g[j] = Oc * (pj + X.q[j]);
+        }
+    }
+}
+
+// FP64 residual of the projection system r0 = b_tilde - A g (g = O(p + q),
+// i.e. b_tilde - A_hat p - M w); the correction CG starts from it:
+// r = r0, u = J^{-1} r.  Partial gamma = r'u.
+template <typename T>
+__device__ __noinline__ void phase_rhs(const IterParams<T>& P) {
+    double gam = 0.0;
+    const double* g = P.X.g;
+    auto gather = [g](int j) { return g[j]; };
+    auto epi = [&](int i, double sum) {
+        const T r = (T)(P.X.btil[i] - sum);
+        const T u = P.V.jinv[i] * r;
+        P.V.r[i] = r;
+        P.V.u[i] = u;
+        gam += (double)r * (double)u;
+    };
+    sell_rows<double>(P.A, gather, epi);
+    const double v[1] = {gam};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// CG, first half of M u: t = O^2 (A' u) over the rows of A'.
+template <typename T>
+__device__ __noinline__ void phase_cg_At(const IterParams<T>& P) {
+    const T* u = P.V.u;
+    auto gather = [u](int i) { return u[i]; };
+    auto epi = [&](int j, T sum) { P.V.t[j] = P.V.O2[j] * sum; };
+    sell_rows<T>(P.AT, gather, epi);
+}
+
+// CG, second half: au = A t (= M u); partial delta = au'u.
+template <typename T>
+__device__ __noinline__ void phase_cg_A(const IterParams<T>& P) {
+    double delta = 0.0;
+    const T* t = P.V.t;
+    auto gather = [t](int j) { return t[j]; };
+    auto epi = [&](int i, T sum) {
+        P.V.au[i] = sum;
+        delta += (double)sum * (double)P.V.u[i];
+    };
+    sell_rows<T>(P.A, gather, epi);
+    const double v[1] = {delta};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// Chronopoulos-Gear vector step: p = u + beta p, sv = au + beta sv,
+// w += alpha p (FP64), r -= alpha sv, u = J^{-1} r; partial gamma = r'u.
+template <typename T>
+__device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, T beta) {
+    double gam = 0.0;
+    const Inner<T>& V = P.V;
+    const T a = (T)alpha;
+    for (int i = global_tid(); i < P.m; i += global_threads()) {
+        const T pi = fma(beta, V.p[i], V.u[i]);
+        const T si = fma(beta, V.sv[i], V.au[i]);
+        V.p[i] = pi;
+        V.sv[i] = si;
+        P.X.w[i] += alpha * (double)pi;
+        const T r = fma(-a, si, V.r[i]);
+        V.r[i] = r;
+        const T u = V.jinv[i] * r;
+        V.u[i] = u;
+        gam += (double)r * (double)u;
+    }
+    const double v[1] = {gam};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// q = O (A' w) over the rows of A' (FP64); with update: s <- (s + p)/2 -
+// mu c_hat + q (steps 18-19) and, if want_xz, x = O (p + s)/2 and
+// z = (p - s)/(2 mu O) (steps 20-21).  Partials ||s_new - s||^2, ||s_new||^2.
+template <typename T>
+__device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, bool want_xz) {
+    double ds2 = 0.0, ss2 = 0.0;
+    const double* w = P.X.w;
+    auto gather = [w](int i) { return w[i]; };
+    auto epi = [&](int j, double sum) {
+        const double Oj = P.X.O[j];
+        const double qj = Oj * sum;
+        P.X.q[j] = qj;
+        if (!update) P.X.g[j] = Oj * (P.X.p[j] + qj);   // right-hand side input of a refinement round
+        if (update) {
+            const double pj = P.X.p[j];
+            const double so = P.X.s[j];
+            const double sj = (0.5 * (so + pj) - P.mu * P.X.chat[j]) + qj;
+            P.X.s[j] = sj;
+            ds2 += (sj - so) * (sj - so);
+            ss2 += sj * sj;
+            if (want_xz) {
+                P.x[j] = Oj * (pj + sj) * 0.5;
+                P.z[j] = (pj - sj) / (2.0 * P.mu * Oj);
+            }
+        }
+    };
+    sell_rows<double>(P.AT, gather, epi);
+    const double v[2] = {ds2, ss2};
+    const int op[2] = {0, 0};
+    block_partials<2>(v, op, P.partials);
+}
+
+// FP64 residual partials: ||Ax - b||^2, ||A'y + z - c||^2 (y = w/mu), c'x, b'y,
+// dist(x,K)^2, dist(z,K)^2, ||x||^2, ||z||^2.
+__device__ __forceinline__ double soc_dist2(double v1, double t) {
+    // squared distance from (v1, vbar) with ||vbar|| = t to the Lorentz cone
+    if (t <= v1) return 0.0;
+    if (t <= -v1) return v1 * v1 + t * t;
+    const double d = 0.5 * (t - v1);      // distance = |t - v1| / sqrt 2
+    return 2.0 * d * d;
+}
+
+template <typename T>
+__device__ __noinline__ void phase_kkt(const IterParams<T>& P) {
+    double rp = 0.0, rd = 0.0, cx = 0.0, by = 0.0, dx = 0.0, dz = 0.0, xx = 0.0, zz = 0.0;
+    const double* x = P.x;
+    const double* z = P.z;
+    const double* w = P.X.w;
+    const double inv_mu = 1.0 / P.mu;
+    {
+        auto gather = [x](int j) { return x[j]; };
+        auto epi = [&](int i, double sum) {
+            const double d = sum - P.b[i];
+            rp += d * d;
+            by += P.b[i] * (w[i] * inv_mu);
+        };
+        sell_rows<double>(P.A, gather, epi);
+    }
+    {
+        auto gather = [w, inv_mu](int i) { return w[i] * inv_mu; };
+        auto epi = [&](int j, double sum) {
+            const double d = sum + z[j] - P.c[j];
+            rd += d * d;
+        };
+        sell_rows<double>(P.AT, gather, epi);
+    }
+    for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
+        const double xj = x[j], zj = z[j];
+        cx += P.c[j] * xj;
+        xx += xj * xj;
+        zz += zj * zj;
+        if (xj < 0.0) dx += xj * xj;
+        if (zj < 0.0) dz += zj * zj;
+    }
+    const int lane = threadIdx.x & 31;
+    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
+        const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
+        double sx = 0.0, sz = 0.0, scx = 0.0;
+        for (int j = a + 1 + lane; j < e; j += 32) {
+            sx = fma(x[j], x[j], sx);
+            sz = fma(z[j], z[j], sz);
+            scx = fma(P.c[j], x[j], scx);
+        }
+        sx = warp_sum(sx);
+        sz = warp_sum(sz);
+        scx = warp_sum(scx);
+        if (lane == 0) {
+            const double xa = x[a], za = z[a];
+            cx += scx + P.c[a] * xa;
+            xx += sx + xa * xa;
+            zz += sz + za * za;
+            dx += soc_dist2(xa, sqrt(sx));
+            dz += soc_dist2(za, sqrt(sz));
+        }
+    }
+    const double v[8] = {rp, rd, cx, by, dx, dz, xx, zz};
+    const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    block_partials<8>(v, op, P.partials);
+}
+
+// ---------------------------------------------------------------------------
+// the solve loop
+// ---------------------------------------------------------------------------
+
+// Algorithm 2 from the state in P (fresh, resumed, or handed over by an FP32
+// loop when status0 = ST_SWITCH) until the KKT test passes, the iteration
+// limit is reached, or the FP32 correction solve hands over.  Run by every
+// thread of every CTA of the problem's team (team_set first); the team's
+// barrier generation must be current in shared memory (sync_init).  Returns
+// the loop's status, the same in every thread of the team; the team's rank-0
+// CTA writes it, the residuals and the counters to P.ctl.
+template <typename T>
+__device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
+    Control* ctl = P.ctl;
+    // per-phase time record, kept by thread 0 of the team's CTA 0 in shared memory
+    __shared__ unsigned long long s_ph_ns[PH_COUNT], s_ph_n[PH_COUNT], s_last;
+    const bool clock_owner = team_rank() == 0 && threadIdx.x == 0;
+    if (clock_owner) {
+        for (int i = 0; i < PH_COUNT; ++i) { s_ph_ns[i] = 0; s_ph_n[i] = 0; }
+        s_last = gtimer();
+    }
+
+    // state left by the reset or by an earlier loop (written by the team's
+    // rank 0 before a barrier): read past L1
+    int l = __ldcg(&ctl->l);
+    bool refresh = P.refresh != 0 || status0 == ST_SWITCH;
+    int status = ST_RUNNING;
+    long long cg_total = 0;
+    long long nA = 0, nAT = 0, nA64 = 0, nAT64 = 0, ncond = 0, nchk = 0;
+    double res[6];
+    for (int i = 0; i < 6; ++i) res[i] = __ldcg(&ctl->res[i]);
+    double ds = __ldcg(&ctl->ds), snorm = __ldcg(&ctl->snorm);
+    double eta = __ldcg(&ctl->eta);
+    bool ok = true;
+
+// grid barrier that ends phase `ph`; leaves the enclosing loop on error
+#define ACS_SYNC(ph)                                                      \
+    {                                                                     \
+        if (!(ok = grid_sync(&ctl->err))) break;                                \
+        if (clock_owner) {                                                \
+            const unsigned long long t_ = gtimer();                       \
+            s_ph_ns[ph] += t_ - s_last;                                   \
+            s_ph_n[ph] += 1;                                              \
+            s_last = t_;                                                  \
+        }                                                                 \
+    }
+
+    while (ok) {
+        if (l >= P.max_iter) { status = ACS_MAX_ITER; break; }
+        const int lnext = l + 1;
+        const bool cond = (lnext == 1) || in_schedule(P, lnext);
+        if (cond) {                                             // steps 5-14
+            phase_cond_o(P);
+            ACS_SYNC(PH_COND_O);
+            double mm[3];
+            const int op[3] = {1, 1, 0};
+            grid_combine<3>(P.partials, op, mm);
+            CondRange R;
+            R.any = mm[2] > 0.0;                               // some o finite and positive
+            R.lmax = mm[0];
+            R.lmin = -mm[1];
+            const double spread = R.lmax - R.lmin;             // log max o - log min o
+            if (!R.any) R.alpha = 0.0;
+            else if (!(spread > 0.0)) R.alpha = 1.0;
+            else R.alpha = fmin(1.0, P.t_cond / spread);
+            phase_cond_apply(P, R, true, true);
+            ACS_SYNC(PH_COND_APPLY);
+            ++ncond;
+        } else if (refresh) {
+            phase_cond_apply(P, CondRange{0.0, 0.0, 0.0, false}, false, false);
+            ACS_SYNC(PH_COND_APPLY);
+        }
+        if (cond || refresh) {
+            phase_btilde(P);
+            ++nA64;
+            ACS_SYNC(PH_BTILDE);
+            double bb[1];
+            const int op[1] = {0};
+            grid_combine<1>(P.partials, op, bb);
+            if (bb[0] > 0.0) { atomicCAS(&ctl->err, 0, ACS_ERR_FACTOR); ok = false; break; }
+            phase_update(P, false, false);                      // q = A_hat' w for the warm start
+            ++nAT64;
+            ACS_SYNC(PH_QREFRESH);
+            refresh = false;
+        }
+
+        phase_abs(P);                                           // step 17
+        ACS_SYNC(PH_ABS);
+        // Projection solve: `refine` rounds of (FP64 residual, correction CG in
+        // precision T); a round after the first refreshes q = A_hat' w first.
+        bool trouble = false;                                   // FP32 solve cannot keep up
+        for (int round = 0; round < P.refine; ++round) {
+            if (round > 0) {
+                phase_update(P, false, false);
+                ++nAT64;
+                ACS_SYNC(PH_QREFRESH);
+            }
+            phase_rhs(P);                                       // r0 in FP64
+            ++nA64;
+            ACS_SYNC(PH_RHS);
+            double gam;
+            {
+                double t1[1];
+                const int op[1] = {0};
+                grid_combine<1>(P.partials, op, t1);
+                gam = t1[0];
+            }
+            if (!isfinite(gam)) { status = ACS_ERR_NUMERICAL; break; }
+            // the step-relative rule needs a previous step in the same scaling;
+            // on the first iteration and whenever O changes only the floors apply
+            const double rel = (isfinite(ds) && !cond && round == 0) ? eta * ds : 0.0;
+            const double thr = fmax(fmax(rel, P.cg_tol * snorm), P.cg_relfloor * sqrt(fmax(gam, 0.0)));
+            double gam_prev = 1.0, alpha_prev = 1.0;
+            int k = 0;
+            bool broke = false;
+            while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
+                phase_cg_At(P);                                 // t = O^2 A' u
+                ++nAT;
+                ACS_SYNC(PH_CG_AT);
+                phase_cg_A(P);                                  // au = A t = M u
+                ++nA;
+                ACS_SYNC(PH_CG_A);
+                double dl[1];
+                const int op1[1] = {0};
+                grid_combine<1>(P.partials, op1, dl);
+                const double beta = (k == 0) ? 0.0 : gam / gam_prev;
+                const double denom = dl[0] - ((k == 0) ? 0.0 : beta * gam / alpha_prev);
+                if (!(denom > 0.0)) {
+                    // p'Mp <= 0 in finite precision: the solve has reached its
+                    // attainable accuracy (or M is singular along p); keep w --
+                    // the next FP64 residual carries on from it
+                    broke = true;
+                    break;
+                }
+                const double alpha = gam / denom;
+                phase_cg_vec(P, alpha, (T)beta);
+                ACS_SYNC(PH_CG_VEC);
+                double gn[1];
+                grid_combine<1>(P.partials, op1, gn);
+                gam_prev = gam;
+                alpha_prev = alpha;
+                gam = gn[0];
+                ++k;
+                if (!isfinite(gam)) { status = ACS_ERR_NUMERICAL; break; }
+            }
+            if (!ok || status == ACS_ERR_NUMERICAL) break;
+            cg_total += k;
+            // an FP32 solve that stalls far above its target cannot refine this M
+            if ((broke || k >= P.cg_max) && sqrt(fmax(gam, 0.0)) > 100.0 * thr) trouble = true;
+        }
+        if (!ok || status == ACS_ERR_NUMERICAL) break;
+
+        const bool check = (lnext % P.check_every == 0) || (lnext == P.max_iter);
+        const bool want_xz = check || in_schedule(P, lnext + 1);
+        phase_update(P, true, want_xz);                         // steps 18-21
+        ++nAT64;
+        ACS_SYNC(PH_UPDATE);
+        {
+            double d2[2];
+            const int op[2] = {0, 0};
+            grid_combine<2>(P.partials, op, d2);
+            const double ds_new = sqrt(d2[0]);
+            snorm = sqrt(d2[1]);
+            if (!isfinite(ds_new) || !isfinite(snorm)) { status = ACS_ERR_NUMERICAL; l = lnext; break; }
+            // With exact projections the step norm ||s_l - s_{l-1}|| never grows
+            // between rescalings (the iteration map is firmly nonexpansive,
+            // Lemma 3); growth beyond what the allowed error explains means the
+            // CG error estimate (J-norm of the residual) is too optimistic for
+            // this M, so the rule is tightened for the rest of the solve.
+            // In the FP32 solve a factor below 1e-4 * cg_eta means the FP32
+            // correction cannot reach the accuracy this M needs: the solve
+            // continues with an FP64 correction solve instead.
+            if (!cond && isfinite(ds) && ds_new > (1.0 + 4.0 * eta) * ds && eta > 1e-8) {
+                if (sizeof(T) == 4 && eta <= 1e-4 * P.cg_eta * 1.0000001) trouble = true;
+                else eta *= 0.1;
+            }
+            ds = ds_new;
+        }
+        l = lnext;
+        if (sizeof(T) == 4 && trouble && P.switch_ok) { status = ST_SWITCH; break; }
+
+        if (check) {
+            phase_kkt(P);
+            ++nA64;
+            ++nAT64;
+            ++nchk;
+            ACS_SYNC(PH_KKT);
+            double r8[8];
+            const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            grid_combine<8>(P.partials, op, r8);
+            res[0] = sqrt(r8[0]) / (1.0 + P.bnorm);
+            res[1] = sqrt(r8[1]) / (1.0 + P.cnorm);
+            res[2] = fabs(r8[2] - r8[3]) / (1.0 + fabs(r8[2]) + fabs(r8[3]));
+            res[3] = fmax(sqrt(r8[4]), sqrt(r8[5])) / (1.0 + fmax(sqrt(r8[6]), sqrt(r8[7])));
+            res[4] = r8[2];
+            res[5] = r8[3];
+            const double mx = fmax(fmax(res[0], res[1]), fmax(res[2], res[3]));
+            if (!isfinite(mx)) { status = ACS_ERR_NUMERICAL; break; }
+            if (mx <= P.tol) { status = ACS_SOLVED; break; }
+        }
+    }
+#undef ACS_SYNC
+
+    if (clock_owner) {
+        const int err = ld_volatile_int(&ctl->err);
+        ctl->status = err != 0 ? err : status;
+        if (status == ST_SWITCH && err == 0) ctl->switched_at = l;
+        ctl->l = l;
+        ctl->cg_iters += cg_total;
+        for (int i = 0; i < 6; ++i) ctl->res[i] = res[i];
+        ctl->ds = ds;
+        ctl->snorm = snorm;
+        ctl->eta = eta;
+        ctl->n_cg_A += nA;
+        ctl->n_cg_AT += nAT;
+        ctl->n_64_A += nA64;
+        ctl->n_64_AT += nAT64;
+        ctl->n_cond += ncond;
+        ctl->n_checks += nchk;
+        ctl->bar_gen = sync_smem().gen;
+        for (int i = 0; i < PH_COUNT; ++i) {
+            ctl->phase_ns[i] += s_ph_ns[i];
+            ctl->phase_n[i] += s_ph_n[i];
+        }
+    }
+    return status;
+}
+
+}  // namespace acs

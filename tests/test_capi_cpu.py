@@ -86,3 +86,32 @@ def test_validation_errors(capi, case, code):
 def test_build_flags_target_sm103a():
     from paper_2103_00736_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_batch_rejects_malformed_members_before_the_device(capi):
+    from paper_2103_00736_gb300 import instances as I
+    good = I.bernoulli_lp(11, 6, 15, density=0.3)
+    bad = I.bernoulli_lp(12, 6, 15, density=0.3)
+    bad.row_ptr = bad.row_ptr.copy()
+    bad.row_ptr[2] = bad.row_ptr[1]            # empty row 1
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_batch_create([good, good, bad])
+    assert e.value.code == capi.ERR_CSR and e.value.member == 2
+    with pytest.raises(capi.AcsError) as e:      # share index must point at an earlier member
+        capi.acs_batch_create([good, good], share=[1, -1])
+    assert e.value.code == capi.ERR_ARG and e.value.member == 0
+    cones = I.bernoulli_lp(13, 6, 15, density=0.3)
+    cones.n_orth = 10                           # 10 + 0 cones != n = 15
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_batch_create([good, cones])
+    assert e.value.code == capi.ERR_CONES and e.value.member == 1
+    with pytest.raises(capi.AcsError) as e:      # mapping outside the supported set
+        capi.acs_batch_create([good], mapping=(384, 1))
+    assert e.value.code == capi.ERR_ARG
+
+
+def test_shared_A_detection(capi):
+    from paper_2103_00736_gb300 import instances as I
+    mem = I.batch(count=8, m_shared=60, mmin=20, mmax=80)
+    share = capi.shared_A_index(mem)
+    assert share[:2] == [-1, 0] and all(s == -1 for s in share[2:])
