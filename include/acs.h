@@ -83,7 +83,19 @@ typedef struct {
                                 residual (mixed-precision refinement rounds); default 1, <= 8  */
     void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream        */
     int32_t device;          /* CUDA device ordinal; default 0                                 */
+    int32_t projection;      /* how the projection onto range((A O)') is applied:
+                                ACS_PROJ_AUTO (default): the cached operator when
+                                m <= dense_max_m, else CG; ACS_PROJ_CG; ACS_PROJ_DENSE: the
+                                cached operator whenever m <= 4096.  The cached operator is
+                                the FP64 Cholesky factor of M = (A O)(A O)', formed at every
+                                rescaling, with L^{-1} kept so that each iteration's solve is
+                                exact up to rounding (two dense products); a factorisation
+                                that fails (M singular) switches that solve to CG          */
+    int32_t dense_max_m;     /* largest m for the cached operator under ACS_PROJ_AUTO;
+                                default 256, at most 4096                                      */
 } acs_settings;
+
+enum { ACS_PROJ_AUTO = 0, ACS_PROJ_CG = 1, ACS_PROJ_DENSE = 2 };
 
 /* Fill *s with the defaults listed above.  Returns ACS_SOLVED or ACS_ERR_ARG. */
 int acs_settings_default(acs_settings* s);

@@ -19,6 +19,7 @@ SOLVED, MAX_ITER = 0, 1
 ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
 ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
 PREC_MIXED, PREC_FP64 = 0, 2
+PROJ_AUTO, PROJ_CG, PROJ_DENSE = 0, 1, 2
 
 _lib = None
 
@@ -39,6 +40,8 @@ class acs_settings(C.Structure):
         ("cg_refine", C.c_int32),
         ("cuda_stream", C.c_void_p),
         ("device", C.c_int32),
+        ("projection", C.c_int32),
+        ("dense_max_m", C.c_int32),
     ]
 
 

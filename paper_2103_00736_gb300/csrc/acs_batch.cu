@@ -49,6 +49,8 @@ struct BatchArgs {
     unsigned long long* team_bar;     // [teams] barrier arrival counters
     double* team_part;                // [CTAs * kMaxRed] partials
     int* team_err;                    // [teams] barrier failures outside a member's solve
+    double* dense;                    // [teams * 2 * dense_m2] scratch of the cached operator
+    long long dense_m2;               // (largest m among members that use it)^2
     int g;                            // CTAs per team
     int fp64;                         // FP64 correction solve from the start
 };
@@ -108,7 +110,9 @@ __device__ void init_member(const IterParams<T>& P) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B) {
     const int team = (int)blockIdx.x / B.g, rank = (int)blockIdx.x % B.g;
-    team_set(rank, B.g, B.team_bar + team, B.team_part + (size_t)team * B.g * kMaxRed);
+    double* scratch = B.dense ? B.dense + (size_t)team * 2 * B.dense_m2 : nullptr;
+    team_set(rank, B.g, B.team_bar + team, B.team_part + (size_t)team * B.g * kMaxRed, scratch,
+             scratch ? scratch + B.dense_m2 : nullptr);
     sync_init(0u);
     __shared__ int s_k;
     while (true) {
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B)
         Control* ctl = B.ctl + i;
         sync_init(sync_smem().gen);                      // clear a failure of the previous member
         int st;
-        if (B.fp64) {
+        if (B.fp64 || B.p64[i].dense) {                  // the cached operator runs in the FP64 loop
             const IterParams<double>& P = B.p64[i];
             init_member(P);
             if (!grid_sync(&ctl->err)) return;
@@ -179,6 +183,7 @@ struct Matrix {       // one distinct A of the batch
 
 struct Member {
     int m = 0, n = 0, n_orth = 0, n_soc = 0, mat = 0;
+    bool dense = false;               // cached dense projection operator
     long long nnz = 0;
     std::vector<double> b, c;
     std::vector<int> soc_off;
@@ -215,6 +220,8 @@ struct Batch {
     unsigned long long* d_team_bar = nullptr;
     double* d_team_part = nullptr;
     int* d_team_err = nullptr;
+    double* d_dense = nullptr;
+    long long dense_m2 = 0;
     int max_ctas = 0;
     // mapping and launch
     acs_batch_mapping map{1024, 1};
@@ -286,6 +293,8 @@ IterParams<T> member_params(const Batch* B, const Member& M, const Matrix& X, co
     Q.refresh = 0;
     Q.refine = B->set.cg_refine > 0 ? B->set.cg_refine : 1;
     Q.switch_ok = B->set.precision == ACS_PREC_MIXED ? 1 : 0;
+    Q.dense = (sizeof(T) == 8 && M.dense) ? 1 : 0;
+    Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
     return Q;
 }
 
@@ -323,6 +332,8 @@ BatchArgs batch_args(Batch* B) {
     a.team_bar = B->d_team_bar;
     a.team_part = B->d_team_part;
     a.team_err = B->d_team_err;
+    a.dense = B->dense_m2 > 0 ? B->d_dense : nullptr;
+    a.dense_m2 = B->dense_m2;
     a.g = B->map.team_ctas;
     a.fp64 = B->set.precision == ACS_PREC_FP64 ? 1 : 0;
     return a;
@@ -463,6 +474,7 @@ void layout(Batch* B, Pool& P) {
     B->d_team_bar = P.take<unsigned long long>(B->max_ctas);
     B->d_team_part = P.take<double>((size_t)B->max_ctas * kMaxRed);
     B->d_team_err = P.take<int>(B->max_ctas);
+    B->d_dense = P.take<double>(B->dense_m2 > 0 ? (size_t)B->max_ctas * 2 * B->dense_m2 : 1);
     B->total_bytes = P.off;
 }
 
@@ -505,11 +517,7 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
     if (count <= 0 || !members) return ACS_ERR_ARG;
     acs_settings set;
     if (settings) set = *settings; else acs_settings_default(&set);
-    if (!(set.mu > 0) || !(set.t > 0) || set.check_every <= 0 || set.cg_max_iter <= 0 || set.cg_refine <= 0 ||
-        set.cg_refine > 8 || !(set.cg_tol >= 0) || !(set.cg_eta >= 0) || set.cond_period < 0 || set.cond_first < 0 ||
-        set.n_cond_list < 0 || (set.n_cond_list > 0 && !set.cond_list) ||
-        (set.precision != ACS_PREC_MIXED && set.precision != ACS_PREC_FP64))
-        return ACS_ERR_ARG;
+    if (!host::valid_settings(set)) return ACS_ERR_ARG;
     acs_batch_mapping map0 = mapping ? *mapping : acs_batch_mapping{1024, 1};
     if (!valid_mapping(map0)) return ACS_ERR_ARG;
 
@@ -560,6 +568,8 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         }
         const Matrix& X = B->mats[mat_of[i]];
         M.m = I.m; M.n = I.n; M.n_orth = I.n_orthant; M.n_soc = I.n_soc; M.mat = mat_of[i];
+        M.dense = host::use_dense(set, I.m);
+        if (M.dense) B->dense_m2 = std::max(B->dense_m2, (long long)I.m * I.m);
         M.nnz = X.stored;
         M.b.resize(I.m);
         for (int r = 0; r < I.m; ++r) M.b[r] = I.b[X.H.perm[r]];
@@ -586,7 +596,11 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
     if (cudaSetDevice(B->device) != cudaSuccess) return fail(ACS_ERR_CUDA, -1);
     if (cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess)
         return fail(ACS_ERR_CUDA, -1);
-    B->max_ctas = B->nsm * 8;            // 256-thread CTAs: at most 2048 threads per SM
+    {
+        int bps = 0;                      // the most CTAs any mapping launches: 256-thread ones
+        if (occupancy_for(256, &bps) != ACS_SOLVED) return fail(ACS_ERR_CUDA, -1);
+        B->max_ctas = B->nsm * bps;
+    }
     if (set.cuda_stream) {
         B->stream = (cudaStream_t)set.cuda_stream;
     } else {
@@ -671,6 +685,7 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
     B->d_team_bar = rebase(B->d_team_bar, base);
     B->d_team_part = rebase(B->d_team_part, base);
     B->d_team_err = rebase(B->d_team_err, base);
+    B->d_dense = rebase(B->d_dense, base);
     // the host images are no longer needed (keep the row relabelling)
     for (Matrix& X : B->mats) {
         std::vector<int> perm = std::move(X.H.perm);

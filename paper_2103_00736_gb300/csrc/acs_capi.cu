@@ -123,6 +123,8 @@ int acs_settings_default(acs_settings* s) {
     s->cg_refine = 1;
     s->cuda_stream = nullptr;
     s->device = 0;
+    s->projection = ACS_PROJ_AUTO;
+    s->dense_max_m = 256;
     return ACS_SOLVED;
 }
 
@@ -154,11 +156,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (m <= 0 || n <= 0 || !row_ptr || !b || !c) return ACS_ERR_ARG;
     acs_settings set;
     if (settings) set = *settings; else acs_settings_default(&set);
-    if (!(set.mu > 0) || !(set.t > 0) || set.check_every <= 0 || set.cg_max_iter <= 0 || set.cg_refine <= 0 || set.cg_refine > 8 ||
-        !(set.cg_tol >= 0) || !(set.cg_eta >= 0) || set.cond_period < 0 || set.cond_first < 0 || set.n_cond_list < 0 ||
-        (set.n_cond_list > 0 && !set.cond_list) ||
-        (set.precision != ACS_PREC_MIXED && set.precision != ACS_PREC_FP64))
-        return ACS_ERR_ARG;
+    if (!acs::host::valid_settings(set)) return ACS_ERR_ARG;
     const int vrc = acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims);
     if (vrc != ACS_SOLVED) return vrc;
     const int nnz = (int)row_ptr[m];
@@ -201,6 +199,10 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (!P->cond_list_host.empty()) rc |= dalloc(P, &P->cond_list, P->cond_list_host.size());
     if (rc) { free_all(P); delete P; return ACS_ERR_OOM; }
     if (alloc_outer(P, P->X) || alloc_inner(P, P->V32) || alloc_inner(P, P->V64)) {
+        free_all(P); delete P; return ACS_ERR_OOM;
+    }
+    P->dense = acs::host::use_dense(set, m);
+    if (P->dense && (dalloc(P, &P->dM, (size_t)m * m) || dalloc(P, &P->dX, (size_t)m * m))) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }
     int nsm = 0;

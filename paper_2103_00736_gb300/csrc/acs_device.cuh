@@ -51,6 +51,8 @@ struct SyncShared {
     int team_size;            // CTAs in the team (the whole grid for a single solve)
     unsigned long long* bar;  // the team's monotonic barrier arrival counter
     double* tpart;            // the team's partials, [team_size * kMaxRed]
+    double* dM;               // the team's dense scratch for the cached projection operator:
+    double* dX;               //   M / its Cholesky factor and L^{-1}, [m * m] each
     double blk[kMaxRed];      // this CTA's partials
     double out[kMaxRed];      // grid-reduced values of the last barrier
     double wsum[kWarps][kMaxRed];
@@ -69,13 +71,16 @@ __device__ __forceinline__ SyncShared& sync_smem() {
 // A team is the set of CTAs that work on one problem: the whole grid of a
 // single-problem launch, or a group of CTAs (often one) of a batched launch.
 // Phases index coordinates, rows and cones by the thread's rank in its team.
-__device__ __forceinline__ void team_set(int rank, int size, unsigned long long* bar, double* partials) {
+__device__ __forceinline__ void team_set(int rank, int size, unsigned long long* bar, double* partials,
+                                         double* dense_M = nullptr, double* dense_X = nullptr) {
     SyncShared& S = sync_smem();
     if (threadIdx.x == 0) {
         S.team_rank = rank;
         S.team_size = size;
         S.bar = bar;
         S.tpart = partials;
+        S.dM = dense_M;
+        S.dX = dense_X;
     }
     __syncthreads();
 }
@@ -721,6 +726,137 @@ __device__ __noinline__ void phase_kkt(const IterParams<T>& P) {
 }
 
 // ---------------------------------------------------------------------------
+// cached projection operator (small m): M = A_hat A_hat' factored once per
+// rescaling, then every projection solve is two dense FP64 products
+// ---------------------------------------------------------------------------
+//
+// The operator of the projection (Algorithm 1 step 2 / Algorithm 2 step 12:
+// the pseudoinverse of A_hat through M = A_hat A_hat') changes only when O
+// does.  For small m it is cached as the explicit inverse factor
+// X = L^{-1} of the Cholesky factorisation M = L L' (FP64), so that the
+// correction of every iteration, dw = M^{-1} r0 = X' (X r0), is exact up to
+// rounding, like the oracle's dense solve, and costs two triangular matrix-
+// vector products with no sequential dependence.
+// Storage: M row-major [m x m] (lower triangle used, overwritten by L);
+// X column-major (X[c * m + i] = (L^{-1})_{ic}, i >= c).
+
+// M = A O^2 A' (lower triangle), from row i of A and the columns of A it
+// touches (rows of A'): M_ik = sum_j O_j^2 a_ij a_kj.  Warp per row i, the
+// lanes over the entries of one column j at a time, in a fixed order.
+template <typename T>
+__device__ __noinline__ void phase_dense_assemble(const IterParams<T>& P) {
+    double* M = sync_smem().dM;
+    const int m = P.m;
+    const int lane = threadIdx.x & 31;
+    const SellMat& A = P.A;
+    const SellMat& AT = P.AT;
+    for (int i = global_warp(); i < m; i += global_warps()) {
+        double* Mi = M + (size_t)i * m;
+        for (int k = lane; k <= i; k += 32) Mi[k] = 0.0;
+        __syncwarp();
+        const int ga = A.g, ha = 32 / ga;
+        const int sl = i / ha, lr = i % ha;
+        const int base = __ldg(A.sptr + sl), len = __ldg(A.slen + sl) * ga;
+        for (int e = 0; e < len; ++e) {
+            const int idx = base + 32 * (e / ga) + lr * ga + (e % ga);
+            const double aij = __ldg(A.v64 + idx);
+            if (aij == 0.0) continue;                         // padding
+            const int j = __ldg(A.col + idx);
+            const double Oj = P.X.O[j];
+            const double f = aij * Oj * Oj;
+            // column j of A = row j of A' (relabelled rows, increasing)
+            const int gt = AT.g, ht = 32 / gt;
+            const int slt = j / ht, lrt = j % ht;
+            const int bt = __ldg(AT.sptr + slt), lt = __ldg(AT.slen + slt) * gt;
+            for (int q = lane; q < lt; q += 32) {
+                const int it = bt + 32 * (q / gt) + lrt * gt + (q % gt);
+                const double akj = __ldg(AT.v64 + it);
+                const int k = __ldg(AT.col + it);
+                if (akj != 0.0 && k <= i) Mi[k] = fma(f, akj, Mi[k]);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Step k of the right-looking Cholesky factorisation (one team barrier per
+// step): scale column k-1 by its pivot, and update the trailing lower
+// triangle with column k: M_ij -= M_ik M_jk / M_kk for k < j <= i.  The two
+// touch disjoint columns.  The diagonal keeps the pivots d_k (L_kk = sqrt(d_k));
+// below it the columns hold L.  Row i belongs to the same warp at every
+// step; other rows are read past L1.  Returns false if a pivot is not
+// positive and finite.
+__device__ __forceinline__ bool dense_chol_step(double* M, int m, int k) {
+    const int lane = threadIdx.x & 31;
+    const double s = (k > 0) ? 1.0 / sqrt(__ldcg(M + (size_t)(k - 1) * m + (k - 1))) : 0.0;
+    const double d = (k < m) ? __ldcg(M + (size_t)k * m + k) : 1.0;
+    if (!(d > 0.0) || !(d < INFINITY)) return false;
+    const double inv = 1.0 / d;
+    for (int i = global_warp(); i < m; i += global_warps()) {
+        double* Mi = M + (size_t)i * m;
+        if (k < i && k < m) {
+            const double f = __ldcg(Mi + k) * inv;
+            for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, __ldcg(M + (size_t)j * m + k), Mi[j]);
+        }
+        if (k > 0 && i >= k && lane == 0) Mi[k - 1] *= s;
+    }
+    return true;
+}
+
+// X = L^{-1} (column-major) by forward substitution, warp per column c:
+// x_i = (delta_ic - sum_{c <= t < i} L_it x_t) / L_ii for i >= c, with
+// L_ii = sqrt(d_i) from the pivot kept on the diagonal.
+template <typename T>
+__device__ __noinline__ void phase_dense_inverse(const IterParams<T>& P) {
+    const double* M = sync_smem().dM;
+    double* X = sync_smem().dX;
+    const int m = P.m;
+    const int lane = threadIdx.x & 31;
+    for (int c = global_warp(); c < m; c += global_warps()) {
+        double* Xc = X + (size_t)c * m;
+        for (int i = c; i < m; ++i) {
+            const double* Li = M + (size_t)i * m;
+            double acc = 0.0;
+            for (int t = c + lane; t < i; t += 32) acc = fma(__ldcg(Li + t), Xc[t], acc);
+            acc = warp_sum(acc);
+            const double xi = ((i == c ? 1.0 : 0.0) - acc) / sqrt(__ldcg(Li + i));
+            if (lane == 0) Xc[i] = xi;
+            __syncwarp();
+        }
+    }
+}
+
+// y = X r0 (r0 = the FP64 residual of the projection system, in V.r), thread
+// per row; y is kept in V.p (unused by the dense path).
+template <typename T>
+__device__ __noinline__ void phase_dense_y(const IterParams<T>& P) {
+    const double* X = sync_smem().dX;
+    const int m = P.m;
+    const T* r = P.V.r;
+    for (int i = global_tid(); i < m; i += global_threads()) {
+        double acc = 0.0;
+        for (int c = 0; c <= i; ++c) acc = fma(__ldcg(X + (size_t)c * m + i), (double)__ldcg(r + c), acc);
+        P.V.p[i] = (T)acc;
+    }
+}
+
+// w += X' y: warp per column c, x_c = sum_{i >= c} X_ic y_i.
+template <typename T>
+__device__ __noinline__ void phase_dense_x(const IterParams<T>& P) {
+    const double* X = sync_smem().dX;
+    const int m = P.m;
+    const int lane = threadIdx.x & 31;
+    const T* y = P.V.p;
+    for (int c = global_warp(); c < m; c += global_warps()) {
+        const double* Xc = X + (size_t)c * m;
+        double acc = 0.0;
+        for (int i = c + lane; i < m; i += 32) acc = fma(__ldcg(Xc + i), (double)__ldcg(y + i), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) P.X.w[c] += acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // the solve loop
 // ---------------------------------------------------------------------------
 
@@ -754,6 +890,10 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     double ds = __ldcg(&ctl->ds), snorm = __ldcg(&ctl->snorm);
     double eta = __ldcg(&ctl->eta);
     bool ok = true;
+    // cached projection operator (FP64 loops only); a factorisation that fails
+    // (M singular: rank-deficient A) hands this solve to the CG projection
+    bool dense = sizeof(T) == 8 && P.dense != 0 && sync_smem().dM != nullptr;
+    long long ndense = 0, nfactor = 0;
 
 // grid barrier that ends phase `ph`; leaves the enclosing loop on error
 #define ACS_SYNC(ph)                                                      \
@@ -800,6 +940,20 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             const int op[1] = {0};
             grid_combine<1>(P.partials, op, bb);
             if (bb[0] > 0.0) { atomicCAS(&ctl->err, 0, ACS_ERR_FACTOR); ok = false; break; }
+            if (dense) {
+                phase_dense_assemble(P);
+                ACS_SYNC(PH_DENSE_FACTOR);
+                for (int k = 0; k <= P.m && dense; ++k) {
+                    if (!dense_chol_step(sync_smem().dM, P.m, k)) dense = false;
+                    ACS_SYNC(PH_DENSE_FACTOR);
+                }
+                if (!ok) break;
+                if (dense) {
+                    phase_dense_inverse(P);
+                    ACS_SYNC(PH_DENSE_FACTOR);
+                    ++nfactor;
+                }
+            }
             phase_update(P, false, false);                      // q = A_hat' w for the warm start
             ++nAT64;
             ACS_SYNC(PH_QREFRESH);
@@ -811,7 +965,18 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         // Projection solve: `refine` rounds of (FP64 residual, correction CG in
         // precision T); a round after the first refreshes q = A_hat' w first.
         bool trouble = false;                                   // FP32 solve cannot keep up
-        for (int round = 0; round < P.refine; ++round) {
+        if (dense) {
+            // one exact correction: dw = X'(X r0)
+            phase_rhs(P);
+            ++nA64;
+            ACS_SYNC(PH_RHS);
+            phase_dense_y(P);
+            ACS_SYNC(PH_DENSE_SOLVE);
+            phase_dense_x(P);
+            ACS_SYNC(PH_DENSE_SOLVE);
+            ++ndense;
+        }
+        for (int round = 0; round < (dense ? 0 : P.refine); ++round) {
             if (round > 0) {
                 phase_update(P, false, false);
                 ++nAT64;
@@ -939,6 +1104,8 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ctl->n_64_AT += nAT64;
         ctl->n_cond += ncond;
         ctl->n_checks += nchk;
+        ctl->n_dense_solve += ndense;
+        ctl->n_dense_factor += nfactor;
         ctl->bar_gen = sync_smem().gen;
         for (int i = 0; i < PH_COUNT; ++i) {
             ctl->phase_ns[i] += s_ph_ns[i];

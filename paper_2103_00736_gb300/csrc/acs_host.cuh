@@ -26,6 +26,25 @@ inline bool finite_all(const double* v, size_t n) {
     return true;
 }
 
+constexpr int kDenseLimit = 4096;   // largest m for the cached dense projection operator
+
+// Settings checks shared by every entry point that takes acs_settings.
+inline bool valid_settings(const acs_settings& set) {
+    return set.mu > 0 && set.t > 0 && set.check_every > 0 && set.cg_max_iter > 0 && set.cg_refine > 0 &&
+           set.cg_refine <= 8 && set.cg_tol >= 0 && set.cg_eta >= 0 && set.cond_period >= 0 && set.cond_first >= 0 &&
+           set.n_cond_list >= 0 && !(set.n_cond_list > 0 && !set.cond_list) &&
+           (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP64) &&
+           (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
+           set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit;
+}
+
+// Does a problem with m constraints use the cached dense projection operator?
+inline bool use_dense(const acs_settings& set, int m) {
+    if (set.projection == ACS_PROJ_DENSE) return m <= kDenseLimit;
+    if (set.projection == ACS_PROJ_AUTO) return m <= set.dense_max_m;
+    return false;
+}
+
 // Checks of the problem statement (Section II, Eq. (1)) as the ABI states
 // them: CSR shape and order, finite data, cone sizes adding up to n.
 inline int validate(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,

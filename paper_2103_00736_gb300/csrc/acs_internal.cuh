@@ -23,7 +23,7 @@ enum : int { ST_RUNNING = 100, ST_SWITCH = 101 /* FP32 correction solve handed o
 // phases of the persistent kernel, for the per-phase time record
 enum Phase : int {
     PH_COND_O = 0, PH_COND_APPLY, PH_BTILDE, PH_QREFRESH, PH_ABS, PH_RHS, PH_CG_AT, PH_CG_A,
-    PH_CG_VEC, PH_UPDATE, PH_KKT, PH_COUNT
+    PH_CG_VEC, PH_UPDATE, PH_KKT, PH_DENSE_FACTOR, PH_DENSE_SOLVE, PH_COUNT
 };
 
 // Control block: lives in device memory for the whole solve; the host reads
@@ -42,6 +42,7 @@ struct Control {
     double eta;           // current inexactness factor of the projection solve
     // pass counters (for the algorithmic-byte model of the benchmark)
     long long n_cg_A, n_cg_AT, n_64_A, n_64_AT, n_cond, n_checks;
+    long long n_dense_solve, n_dense_factor;   // cached-operator corrections and factorisations
     unsigned bar_count, bar_gen;
     unsigned long long bar_count64;   // monotonic barrier arrival counter of the current solve
     // nanoseconds spent in each phase (from one barrier exit to the next, as
@@ -101,6 +102,8 @@ struct IterParams {
     int refresh;                                      // recompute c_hat, b_tilde, J, q first
     int refine;                                       // correction solves per iteration
     int switch_ok;                                    // FP32 launch may hand over to FP64
+    int dense;                                        // cached dense projection operator (FP64 loop)
+    double* dM; double* dX;                           // its scratch in a single-problem launch
 };
 
 struct Problem {
@@ -136,6 +139,8 @@ struct Problem {
     int warm_l = 0;
     double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 1e-2;
     int last_status = ACS_MAX_ITER;
+    bool dense = false;                  // cached dense projection operator
+    double *dM = nullptr, *dX = nullptr; // its scratch, [m * m] each
     std::vector<void*> allocations;
     cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch
 };

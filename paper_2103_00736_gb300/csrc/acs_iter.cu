@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(IterParams<T> P) {
     // the FP32 launch runs from a fresh or resumed state; the FP64 launch of a
     // mixed-precision solve runs only if the FP32 launch handed over
     if (sizeof(T) == 4 ? status0 != ST_RUNNING : (status0 != ST_RUNNING && status0 != ST_SWITCH)) return;
-    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials);
+    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, P.dense ? P.dM : nullptr,
+             P.dense ? P.dX : nullptr);
     sync_init(P.ctl->bar_gen);
     solve_loop<T>(P, status0);
 }
@@ -144,6 +145,9 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.refresh = P->warm ? 1 : 0;
     Q.refine = P->set.cg_refine > 0 ? P->set.cg_refine : 1;
     Q.switch_ok = P->set.precision == ACS_PREC_MIXED ? 1 : 0;
+    Q.dense = (sizeof(T) == 8 && P->dense) ? 1 : 0;
+    Q.dM = P->dM;
+    Q.dX = P->dX;
     return Q;
 }
 
@@ -202,7 +206,8 @@ int launch_solve(Problem* P, double tol, int max_iter) {
     if (cudaGetLastError() != cudaSuccess) return ACS_ERR_CUDA;
     cudaError_t e;
     if (P->ev_launch[0]) cudaEventRecord(P->ev_launch[0], st);
-    if (P->set.precision == ACS_PREC_FP64) {
+    if (P->set.precision == ACS_PREC_FP64 || P->dense) {
+        // the cached operator runs in the FP64 loop (exact corrections)
         IterParams<double> Q = make_params<double>(P, tol, max_iter, P->V64);
         e = launch_iter<double>(P, Q, P->grid64);
     } else {

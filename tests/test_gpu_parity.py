@@ -37,10 +37,12 @@ def _solve(inst, tol=1e-6, max_iter=20000, **kw):
     return st, x, y, z, iters, res
 
 
+@pytest.mark.parametrize("projection", [capi.PROJ_AUTO, capi.PROJ_CG])
 @pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
-def test_small_lp_end_result(precision):
+def test_small_lp_end_result(precision, projection):
+    """m = 200: the cached dense operator by default, CG when forced."""
     inst = I.small_lp()
-    st, x, y, z, iters, res = _solve(inst, precision=precision, **LP_SCHED)
+    st, x, y, z, iters, res = _solve(inst, precision=precision, projection=projection, **LP_SCHED)
     assert st == capi.SOLVED, capi.acs_status_string(st)
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
@@ -55,15 +57,19 @@ def test_small_lp_end_result(precision):
     assert np.linalg.norm(x - inst.x_star) <= 1e-4 * np.linalg.norm(inst.x_star)
 
 
-@pytest.mark.parametrize("precision,rtol", [(capi.PREC_MIXED, 1e-4), (capi.PREC_FP64, 1e-7)])
-def test_first_50_iterates(precision, rtol):
+@pytest.mark.parametrize("precision,projection,rtol", [(capi.PREC_MIXED, capi.PROJ_CG, 1e-4),
+                                                        (capi.PREC_FP64, capi.PROJ_CG, 1e-7),
+                                                        (capi.PREC_MIXED, capi.PROJ_DENSE, 1e-9)])
+def test_first_50_iterates(precision, projection, rtol):
+    """FP32 correction CG within 1e-4 of the oracle, FP64 CG within 1e-7, the
+    cached FP64 operator (exact solves, like the oracle's) within 1e-9."""
     inst = I.small_lp()
     ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
                          max_iter=50, tol=0.0, keep_x=50)
     worst = 0.0
     for k in (1, 2, 3, 5, 10, 20, 35, 50):
         st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=precision,
-                                         cg_eta=1e-9, cg_tol=0.0, **LP_SCHED)
+                                         projection=projection, cg_eta=1e-9, cg_tol=0.0, **LP_SCHED)
         assert st == capi.MAX_ITER and iters == k
         xr = ref.x_history[k - 1]
         err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
@@ -72,10 +78,11 @@ def test_first_50_iterates(precision, rtol):
     print("worst relative iterate error", worst)
 
 
+@pytest.mark.parametrize("projection", [capi.PROJ_AUTO, capi.PROJ_CG])
 @pytest.mark.parametrize("sched", [dict(), dict(cond_first=0, cond_list=list(range(1, 51))),
                                    dict(cond_first=1, cond_period=1)])
 @pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
-def test_worked_example(sched, precision):
+def test_worked_example(sched, precision, projection):
     """Section III-A example (ill-conditioned 3 x 5, cond 2046) reaches the
     vertex optimum under the LP schedule, rescaling at the first 50 iterations,
     and rescaling at every iteration."""
@@ -83,7 +90,7 @@ def test_worked_example(sched, precision):
     A = np.array(g["A"])
     row_ptr = np.arange(0, 16, 5, dtype=np.int64)
     col = np.tile(np.arange(5, dtype=np.int32), 3)
-    s = capi.acs_settings_default(precision=precision, **sched)
+    s = capi.acs_settings_default(precision=precision, projection=projection, **sched)
     h = capi.acs_problem_create(3, 5, row_ptr, col, A.reshape(-1), g["b"], g["c"], 5, [], s)
     try:
         st = capi.acs_solve(h, 1e-8, 20000)
@@ -118,7 +125,8 @@ def test_socp_iterates_match_oracle_fp64():
         assert np.linalg.norm(x - xr) <= 1e-7 * np.linalg.norm(xr), k
 
 
-def test_conditioning_first_50_iterations():
+@pytest.mark.parametrize("projection", [capi.PROJ_AUTO, capi.PROJ_CG])
+def test_conditioning_first_50_iterations(projection):
     """Rescaling on the device (steps 5-14) at each of the first 50 iterations.
     Iterates are compared while exact (k <= 2: O = I up to the first rescale
     that moves); after that the rescaling amplifies the attainable accuracy of
@@ -130,12 +138,13 @@ def test_conditioning_first_50_iterations():
                          keep_x=2)
     for k in (1, 2):
         st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, precision=capi.PREC_FP64,
-                                         cond_list=list(range(1, 51)), cond_first=0, cg_eta=1e-12, cg_tol=0.0)
+                                         projection=projection, cond_list=list(range(1, 51)),
+                                         cond_first=0, cg_eta=1e-12, cg_tol=0.0)
         xr = ref.x_history[k - 1]
         assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr), (k, np.linalg.norm(x - xr))
     for prec in (capi.PREC_MIXED, capi.PREC_FP64):
-        st, x, y, z, iters, res = _solve(inst, tol=2e-7, precision=prec, cond_list=list(range(1, 51)),
-                                         cond_first=0)
+        st, x, y, z, iters, res = _solve(inst, tol=2e-7, precision=prec, projection=projection,
+                                         cond_list=list(range(1, 51)), cond_first=0)
         assert st == capi.SOLVED
         ours = _kkt_of(inst, x, y, z)
         assert kkt.max_residual(ours) <= 2e-7
@@ -177,7 +186,8 @@ def test_edge_shapes():
 
 
 def test_rank_deficient_rows():
-    """Duplicate rows: M = AA' is singular.  With a consistent b the right-hand
+    """Duplicate rows: M = AA' is singular.  The cached dense factorisation
+    fails and the solve continues with CG; with a consistent b the right-hand
     sides stay in range(M), CG converges and the LP is solved (min x1 + x2,
     x1 + 2 x2 = 1, x >= 0 -> x = (0, 1/2)); with an inconsistent b the
     problem is infeasible and no solve may report success."""
