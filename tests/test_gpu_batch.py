@@ -171,11 +171,13 @@ def test_batch_autotune_picks_a_valid_mapping(mixed):
 
 def test_batch_dense_and_cg_projection_agree(mixed):
     """Members with m <= 256 use the cached dense operator by default; the same
-    batch with CG projections everywhere reaches the same optima."""
+    batch with CG projections everywhere reaches the same optima.  Solved to a
+    KKT residual of 1e-7: a residual of 1e-6 alone does not bound the
+    objective error by 1e-6 (one member ends 1.7e-6 away at 2e-7 residuals)."""
     sub = [m for m in mixed if m.m <= 256][:8]
     objs = []
     for proj in (capi.PROJ_AUTO, capi.PROJ_CG):
         with capi.Batch(sub, projection=proj, **LP) as B:
-            assert B.solve(tol=1e-6, max_iter=30000) == capi.SOLVED
+            assert B.solve(tol=1e-7, max_iter=50000) == capi.SOLVED
             objs.append([_check_member(inst, *B.get(i)[1:4])["obj_p"] for i, inst in enumerate(sub)])
     np.testing.assert_allclose(objs[0], objs[1], rtol=2e-6, atol=1e-6)
