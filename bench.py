@@ -51,7 +51,11 @@ WORKLOADS = {
                  settings=dict(cond_first=200, cond_period=100, t=1.7, mu=1.0)),
     "small_lp": dict(desc="LP m=200 n=500 5% density, |supp x*|=150",
                      settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
+    "batch": dict(desc="4096 LPs in one persistent launch: m log-uniform [50,2000], n=2.5m, 2% density, "
+                       "N(0,1); members 0..1023 share one 1000x2500 A",
+                  settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
 }
+BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
 
 
 # DRAM bytes of one launch of the persistent kernel, from one ncu capture
@@ -361,6 +365,143 @@ def gpu_arm(args) -> None:
         pg.destroy_process_group()
 
 
+def member_bytes(m: int, n: int, nnz: int, c) -> float:
+    """Algorithmic bytes of one member's solve from its pass counters c[8]
+    (the byte model of algorithmic_bytes, plus the cached operator: each
+    correction reads the inverse factor twice, m^2 doubles in all)."""
+    n_cg_A, n_cg_AT, n64_A, n64_AT, n_cond, n_chk, n_dense, n_fact = [float(v) for v in c]
+    b = n_cg_AT * (8.0 * nnz + 4 * m + 8 * n) + n_cg_A * (8.0 * nnz + 4 * n + 8 * m + 52.0 * m)
+    b += n64_A * (12.0 * nnz + 8 * n + 20 * m) + n64_AT * (12.0 * nnz + 8 * m + 48 * n)
+    iters = n64_AT - n_chk - n_cond                 # one FP64 A' update pass per iteration
+    b += max(iters, 0.0) * 40.0 * n + n_cond * 100.0 * n
+    b += n_dense * 8.0 * m * m
+    return b
+
+
+def batch_arm(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2103_00736_gb300 import capi, instances as I
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    wl = WORKLOADS["batch"]
+    t0 = time.perf_counter()
+    mem = I.batch(count=args.batch_count)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    settings = capi.acs_settings_default(cuda_stream=stream.cuda_stream, device=local, **wl["settings"])
+    share = capi.shared_A_index(mem)
+    t0 = time.perf_counter()
+    h = capi.acs_batch_create(mem, settings, None, share)
+    t_create = time.perf_counter() - t0
+    info0 = capi.acs_batch_info(h)
+    tol, max_iter = args.tol, args.batch_max_iter
+    (th, team), tune_ms = capi.acs_batch_autotune(h, max_iter=args.autotune_iters)
+    for _ in range(args.warmup):
+        capi.acs_batch_solve_async(h, tol, max_iter)
+    capi.acs_batch_results(h, len(mem))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        capi.acs_batch_solve_async(h, tol, max_iter)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launch_ms = capi.acs_batch_last_ms(h)
+    worst, st, iters, res = capi.acs_batch_results(h, len(mem))
+    solved = int(np.sum(st == capi.SOLVED))
+    info = capi.acs_batch_info(h)
+    cnt = capi.acs_batch_counters(h, len(mem))
+    alg_bytes = sum(member_bytes(x.m, x.n, x.nnz, cnt[i]) for i, x in enumerate(mem))
+    ms_step = statistics.median(step_ms)
+    value = solved / (ms_step / 1e3)
+    # oracle-side check of a sample of members: KKT residuals of the returned points
+    from oracle import kkt
+    idx = np.linspace(0, len(mem) - 1, 16).astype(int)
+    worst_kkt = 0.0
+    for i in idx:
+        s_i, x, y, z, it_i, r_i = capi.acs_batch_get(h, int(i), mem[i].m, mem[i].n)
+        if s_i == capi.SOLVED:
+            rr = kkt.residuals(mem[i].to_scipy(), mem[i].b, mem[i].c, x, y, z, mem[i].n_orth, mem[i].soc_dims)
+            worst_kkt = max(worst_kkt, kkt.max_residual(rr))
+    capi.acs_batch_destroy(h)
+
+    # plain form: the single-problem API on a size-stratified sample, one
+    # solve after another, extrapolated to the whole batch
+    order = np.argsort([x.nnz for x in mem])
+    sample = order[np.linspace(0, len(mem) - 1, args.plain_sample).astype(int)]
+    plain_ms, plain_solved = [], 0
+    for i in sample:
+        x = mem[i]
+        hs = capi.acs_problem_create(x.m, x.n, x.row_ptr, x.col, x.val, x.b, x.c, x.n_orth, x.soc_dims,
+                                     capi.acs_settings_default(cuda_stream=stream.cuda_stream, device=local,
+                                                               **wl["settings"]))
+        capi.acs_solve(hs, tol, max_iter)                 # warm-up
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        capi.acs_solve_async(hs, tol, max_iter)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b2))
+        plain_solved += capi.acs_get_residuals(hs)[0] == capi.SOLVED
+        capi.acs_problem_destroy(hs)
+    plain_total_ms = float(np.mean(plain_ms)) * len(mem)
+    plain_value = (plain_solved / len(sample)) * len(mem) / (plain_total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: create (host preparation
+    # and upload), solve, read back every member's x, y, s
+    e2e = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        h2 = capi.acs_batch_create(mem, capi.acs_settings_default(device=local, **wl["settings"]),
+                                   (th, team), share)
+        capi.acs_batch_solve(h2, tol, max_iter)
+        for i, x in enumerate(mem):
+            capi.acs_batch_get(h2, i, x.m, x.n)
+        capi.acs_batch_destroy(h2)
+        t_e2e = time.perf_counter() - t0
+        h2d = 16 * info0["stored_nnz"] * 2 + 8 * (info0["sum_m"] + info0["sum_n"])
+        d2h = 8 * (2 * info0["sum_n"] + info0["sum_m"])
+        e2e = {"value": solved / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    it_s = iters[st == capi.SOLVED]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch", "desc": wl["desc"], "members": len(mem),
+                   "distinct_matrices": info0["matrices"], "sum_m": info0["sum_m"], "sum_n": info0["sum_n"],
+                   "stored_nnz_distinct": info0["stored_nnz"], "tol": tol, "max_iter": max_iter,
+                   "solved": solved, "iterations_median": float(np.median(it_s)) if it_s.size else None,
+                   "iterations_p90": float(np.percentile(it_s, 90)) if it_s.size else None,
+                   "mapping": {"threads_per_cta": th, "team_ctas": team, "teams": info["teams"],
+                               "ctas": info["ctas"]},
+                   "autotune_ms": tune_ms.tolist(), "cuda_graph": bool(info["graph"]),
+                   "sampled_oracle_kkt_max": worst_kkt, "generate_s": t_gen, "create_s": t_create,
+                   "l2": "inputs larger than L2 (distinct matrices ~2.6 GB)"},
+        "plain": {"value": plain_value, "unit": UNIT, "sample": int(len(sample)),
+                  "sample_solved": int(plain_solved), "mean_ms": float(np.mean(plain_ms)),
+                  "how": "single-problem API, one member after another, size-stratified sample "
+                         "extrapolated to all members"},
+        "batched_over_plain": value / plain_value if plain_value > 0 else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "batch_kernel",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms},
+        "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def reference_arm(args) -> None:
     rank, world, local = dist_info()
     if rank != 0:
@@ -396,6 +537,10 @@ def main():
                     help="KKT tolerance of a step (0 with --max-iter: a truncated solve, for profiling)")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-max-iter", type=int, default=BATCH_MAX_ITER)
+    ap.add_argument("--autotune-iters", type=int, default=20)
+    ap.add_argument("--plain-sample", type=int, default=24)
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.workload, args.cpu_iters)), flush=True)
@@ -404,6 +549,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch":
+        batch_arm(args)
     else:
         gpu_arm(args)
 

@@ -183,8 +183,9 @@ int acs_last_launch_ms(acs_problem* p, double* ms);
 /* Time of each phase of the persistent kernel in the last solve (ms, from
  * the device's global timer, barrier wait included) and how often it ran, in
  * the order: rescale-o, rescale-apply, b_tilde, q-refresh, abs_K, CG-rhs,
- * CG A' pass, CG A pass, CG vector step, update, KKT.  n >= 11.  Returns the
- * number of phases written or an error. */
+ * CG A' pass, CG A pass, CG vector step, update, KKT, cached-operator
+ * factorisation, cached-operator correction.  n >= 13.  Returns the number of
+ * phases written or an error. */
 int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t n);
 /* Mean time (ns) of one grid-wide reduce-and-barrier of the persistent
  * kernel's launch shape, over n back-to-back barriers. */
@@ -303,6 +304,12 @@ int acs_batch_last_ms(acs_batch* b, double* ms);
  * was replayed from a CUDA graph}.  counters6 (may be NULL): acs_debug_counters
  * summed over members. */
 int acs_batch_info(acs_batch* b, long long* out8, long long* counters6);
+
+/* Pass counters of every member's last solve: out[8 * count], per member
+ * {A passes, A' passes (FP32 or FP64 correction CG), FP64 A passes, FP64 A'
+ * passes, rescalings, KKT checks, cached-operator corrections, cached-operator
+ * factorisations}.  Waits for queued work. */
+int acs_batch_counters(acs_batch* b, long long* out);
 
 void acs_batch_destroy(acs_batch* b);
 

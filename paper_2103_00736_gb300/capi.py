@@ -108,6 +108,7 @@ def lib():
         L.acs_batch_set_mapping.argtypes = [P, C.POINTER(acs_batch_mapping)]
         L.acs_batch_last_ms.argtypes = [P, dp]
         L.acs_batch_info.argtypes = [P, llp, llp]
+        L.acs_batch_counters.argtypes = [P, llp]
         L.acs_batch_destroy.argtypes = [P]
         L.acs_batch_destroy.restype = None
         _lib = L
@@ -231,7 +232,7 @@ def acs_debug_counters(h) -> np.ndarray:
 
 
 PHASES = ("rescale_o", "rescale_apply", "b_tilde", "q_refresh", "abs_K", "cg_rhs", "cg_At",
-          "cg_A", "cg_vec", "update", "kkt")
+          "cg_A", "cg_vec", "update", "kkt", "dense_factor", "dense_solve")
 
 
 def acs_debug_phase_times(h) -> dict:
@@ -428,6 +429,15 @@ def acs_batch_info(h) -> dict:
     d = dict(zip(keys, out.tolist()))
     d["counters"] = cnt
     return d
+
+
+def acs_batch_counters(h, count: int) -> np.ndarray:
+    """int64 [count, 8]: see include/acs.h."""
+    out = np.zeros((count, 8), dtype=np.int64)
+    rc = lib().acs_batch_counters(C.c_void_p(h), out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_counters")
+    return out
 
 
 def acs_batch_destroy(h) -> None:

@@ -842,6 +842,20 @@ int acs_batch_info(acs_batch* h, long long* out8, long long* counters6) {
     return ACS_SOLVED;
 }
 
+int acs_batch_counters(acs_batch* h, long long* out) {
+    Batch* B = reinterpret_cast<Batch*>(h);
+    if (!B || !out) return ACS_ERR_ARG;
+    if (cudaSetDevice(B->device) != cudaSuccess) return ACS_ERR_CUDA;
+    if (acs::fetch_controls(B) != ACS_SOLVED) return ACS_ERR_CUDA;
+    for (int i = 0; i < B->count; ++i) {
+        const acs::Control& C = B->ctl_host[i];
+        long long* o = out + 8 * (size_t)i;
+        o[0] = C.n_cg_A; o[1] = C.n_cg_AT; o[2] = C.n_64_A; o[3] = C.n_64_AT;
+        o[4] = C.n_cond; o[5] = C.n_checks; o[6] = C.n_dense_solve; o[7] = C.n_dense_factor;
+    }
+    return ACS_SOLVED;
+}
+
 void acs_batch_destroy(acs_batch* h) {
     Batch* B = reinterpret_cast<Batch*>(h);
     if (!B) return;
