@@ -91,8 +91,13 @@ typedef struct {
                                 rescaling, with L^{-1} kept so that each iteration's solve is
                                 exact up to rounding (two dense products); a factorisation
                                 that fails (M singular) switches that solve to CG          */
-    int32_t dense_max_m;     /* largest m for the cached operator under ACS_PROJ_AUTO;
-                                default 256, at most 4096                                      */
+    int32_t dense_max_m;     /* largest m for the cached operator from the first iteration
+                                under ACS_PROJ_AUTO; default 512, at most 4096                 */
+    int32_t dense_switch_max_m; /* ACS_PROJ_AUTO, dense_max_m < m <= this: start with CG and
+                                switch to the cached operator when CG averages more than
+                                dense_switch_cg iterations per outer iteration over 8 outer
+                                iterations; default 1024, at most 4096                         */
+    int32_t dense_switch_cg; /* default 40; 0 disables the switch                               */
 } acs_settings;
 
 enum { ACS_PROJ_AUTO = 0, ACS_PROJ_CG = 1, ACS_PROJ_DENSE = 2 };
@@ -310,6 +315,11 @@ int acs_batch_info(acs_batch* b, long long* out8, long long* counters6);
  * passes, rescalings, KKT checks, cached-operator corrections, cached-operator
  * factorisations}.  Waits for queued work. */
 int acs_batch_counters(acs_batch* b, long long* out);
+
+/* Device time (ms, the team's global timer from its first to its last
+ * barrier on the member, barrier waits included) each member's last solve
+ * took: ms[count].  Waits for queued work. */
+int acs_batch_member_ms(acs_batch* b, double* ms);
 
 void acs_batch_destroy(acs_batch* b);
 

@@ -42,6 +42,8 @@ class acs_settings(C.Structure):
         ("device", C.c_int32),
         ("projection", C.c_int32),
         ("dense_max_m", C.c_int32),
+        ("dense_switch_max_m", C.c_int32),
+        ("dense_switch_cg", C.c_int32),
     ]
 
 
@@ -109,6 +111,7 @@ def lib():
         L.acs_batch_last_ms.argtypes = [P, dp]
         L.acs_batch_info.argtypes = [P, llp, llp]
         L.acs_batch_counters.argtypes = [P, llp]
+        L.acs_batch_member_ms.argtypes = [P, dp]
         L.acs_batch_destroy.argtypes = [P]
         L.acs_batch_destroy.restype = None
         _lib = L
@@ -438,6 +441,14 @@ def acs_batch_counters(h, count: int) -> np.ndarray:
     if rc != 0:
         raise AcsError(rc, "acs_batch_counters")
     return out
+
+
+def acs_batch_member_ms(h, count: int) -> np.ndarray:
+    ms = np.zeros(count)
+    rc = lib().acs_batch_member_ms(C.c_void_p(h), _ptr(ms, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_batch_member_ms")
+    return ms
 
 
 def acs_batch_destroy(h) -> None:

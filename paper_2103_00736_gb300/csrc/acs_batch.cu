@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B)
         Control* ctl = B.ctl + i;
         sync_init(sync_smem().gen);                      // clear a failure of the previous member
         int st;
-        if (B.fp64 || B.p64[i].dense) {                  // the cached operator runs in the FP64 loop
+        if (B.fp64 || B.p64[i].dense == 1) {             // the cached operator runs in the FP64 loop
             const IterParams<double>& P = B.p64[i];
             init_member(P);
             if (!grid_sync(&ctl->err)) return;
@@ -183,7 +183,7 @@ struct Matrix {       // one distinct A of the batch
 
 struct Member {
     int m = 0, n = 0, n_orth = 0, n_soc = 0, mat = 0;
-    bool dense = false;               // cached dense projection operator
+    int dense = 0;                    // cached dense operator: 0 never, 1 always, 2 when CG stalls
     long long nnz = 0;
     std::vector<double> b, c;
     std::vector<int> soc_off;
@@ -293,7 +293,8 @@ IterParams<T> member_params(const Batch* B, const Member& M, const Matrix& X, co
     Q.refresh = 0;
     Q.refine = B->set.cg_refine > 0 ? B->set.cg_refine : 1;
     Q.switch_ok = B->set.precision == ACS_PREC_MIXED ? 1 : 0;
-    Q.dense = (sizeof(T) == 8 && M.dense) ? 1 : 0;
+    Q.dense = M.dense;
+    Q.dense_switch_cg = B->set.dense_switch_cg;
     Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
     return Q;
 }
@@ -568,7 +569,7 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         }
         const Matrix& X = B->mats[mat_of[i]];
         M.m = I.m; M.n = I.n; M.n_orth = I.n_orthant; M.n_soc = I.n_soc; M.mat = mat_of[i];
-        M.dense = host::use_dense(set, I.m);
+        M.dense = host::dense_mode(set, I.m);
         if (M.dense) B->dense_m2 = std::max(B->dense_m2, (long long)I.m * I.m);
         M.nnz = X.stored;
         M.b.resize(I.m);
@@ -852,6 +853,19 @@ int acs_batch_counters(acs_batch* h, long long* out) {
         long long* o = out + 8 * (size_t)i;
         o[0] = C.n_cg_A; o[1] = C.n_cg_AT; o[2] = C.n_64_A; o[3] = C.n_64_AT;
         o[4] = C.n_cond; o[5] = C.n_checks; o[6] = C.n_dense_solve; o[7] = C.n_dense_factor;
+    }
+    return ACS_SOLVED;
+}
+
+int acs_batch_member_ms(acs_batch* h, double* ms) {
+    Batch* B = reinterpret_cast<Batch*>(h);
+    if (!B || !ms) return ACS_ERR_ARG;
+    if (cudaSetDevice(B->device) != cudaSuccess) return ACS_ERR_CUDA;
+    if (acs::fetch_controls(B) != ACS_SOLVED) return ACS_ERR_CUDA;
+    for (int i = 0; i < B->count; ++i) {
+        unsigned long long t = 0;
+        for (int k = 0; k < acs::PH_COUNT; ++k) t += B->ctl_host[i].phase_ns[k];
+        ms[i] = (double)t * 1e-6;
     }
     return ACS_SOLVED;
 }

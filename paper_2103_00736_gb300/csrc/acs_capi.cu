@@ -124,7 +124,9 @@ int acs_settings_default(acs_settings* s) {
     s->cuda_stream = nullptr;
     s->device = 0;
     s->projection = ACS_PROJ_AUTO;
-    s->dense_max_m = 256;
+    s->dense_max_m = 512;
+    s->dense_switch_max_m = 1024;
+    s->dense_switch_cg = 40;
     return ACS_SOLVED;
 }
 
@@ -201,7 +203,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (alloc_outer(P, P->X) || alloc_inner(P, P->V32) || alloc_inner(P, P->V64)) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }
-    P->dense = acs::host::use_dense(set, m);
+    P->dense = acs::host::dense_mode(set, m);
     if (P->dense && (dalloc(P, &P->dM, (size_t)m * m) || dalloc(P, &P->dX, (size_t)m * m))) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }

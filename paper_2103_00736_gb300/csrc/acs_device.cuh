@@ -784,17 +784,30 @@ __device__ __noinline__ void phase_dense_assemble(const IterParams<T>& P) {
 // triangle with column k: M_ij -= M_ik M_jk / M_kk for k < j <= i.  The two
 // touch disjoint columns.  The diagonal keeps the pivots d_k (L_kk = sqrt(d_k));
 // below it the columns hold L.  Row i belongs to the same warp at every
-// step; other rows are read past L1.  Returns false if a pivot is not
-// positive and finite.
-__device__ __forceinline__ bool dense_chol_step(double* M, int m, int k) {
+// step; other rows are read past L1.
+// A pivot below 1e-13 of the row's original diagonal (jinv = 1 / diag M)
+// marks row k of A as linearly dependent on the rows before it (rank-
+// deficient A): the direction is dropped -- the pivot becomes +inf, so the
+// column scales to zero, nothing is eliminated with it, and row k of L^{-1}
+// is zero.  For a consistent right-hand side (b in range(A)) this solves the
+// remaining independent equations, which imply the dropped one.  Returns
+// false only for a pivot that is negative beyond rounding or not a number.
+template <typename T>
+__device__ __forceinline__ bool dense_chol_step(double* M, int m, int k, const T* jinv) {
     const int lane = threadIdx.x & 31;
     const double s = (k > 0) ? 1.0 / sqrt(__ldcg(M + (size_t)(k - 1) * m + (k - 1))) : 0.0;
-    const double d = (k < m) ? __ldcg(M + (size_t)k * m + k) : 1.0;
-    if (!(d > 0.0) || !(d < INFINITY)) return false;
-    const double inv = 1.0 / d;
+    double inv = 0.0;
+    if (k < m) {
+        const double d = __ldcg(M + (size_t)k * m + k);
+        const double tau = 1e-13 / (double)__ldcg(jinv + k);
+        if (d != d || d < -1e3 * tau) return false;
+        const bool dep = !(d > tau) || d == INFINITY;
+        if (dep && team_rank() == 0 && threadIdx.x == 0) M[(size_t)k * m + k] = INFINITY;
+        inv = dep ? 0.0 : 1.0 / d;
+    }
     for (int i = global_warp(); i < m; i += global_warps()) {
         double* Mi = M + (size_t)i * m;
-        if (k < i && k < m) {
+        if (k < i && k < m && inv != 0.0) {
             const double f = __ldcg(Mi + k) * inv;
             for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, __ldcg(M + (size_t)j * m + k), Mi[j]);
         }
@@ -892,7 +905,17 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     bool ok = true;
     // cached projection operator (FP64 loops only); a factorisation that fails
     // (M singular: rank-deficient A) hands this solve to the CG projection
-    bool dense = sizeof(T) == 8 && P.dense != 0 && sync_smem().dM != nullptr;
+    // P.dense == 2: start with CG and switch to the cached operator once CG
+    // averages more than P.dense_switch_cg iterations per outer iteration over
+    // a window of 8 outer iterations (an M too ill-conditioned for Jacobi-CG).
+    // An FP32 loop hands over to the FP64 loop for that; an FP64 loop that
+    // takes over this way factors at once.
+    const bool have_scratch = sync_smem().dM != nullptr;
+    bool dense = sizeof(T) == 8 && have_scratch && (P.dense == 1 || (P.dense == 2 && status0 == ST_SWITCH));
+    const bool may_switch = P.dense == 2 && (sizeof(T) == 4 ? P.switch_ok != 0 : have_scratch);
+    bool dense_failed = false;
+    long long win_cg = 0;
+    int win_it = 0;
     long long ndense = 0, nfactor = 0;
 
 // grid barrier that ends phase `ph`; leaves the enclosing loop on error
@@ -911,6 +934,15 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         if (l >= P.max_iter) { status = ACS_MAX_ITER; break; }
         const int lnext = l + 1;
         const bool cond = (lnext == 1) || in_schedule(P, lnext);
+        if (may_switch && !dense && !dense_failed && win_it >= 8) {
+            if (win_cg > (long long)P.dense_switch_cg * win_it) {
+                if (sizeof(T) == 4) { status = ST_SWITCH; break; }
+                dense = true;
+                refresh = true;                                 // factor at this iteration
+            }
+            win_cg = 0;
+            win_it = 0;
+        }
         if (cond) {                                             // steps 5-14
             phase_cond_o(P);
             ACS_SYNC(PH_COND_O);
@@ -944,7 +976,10 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 phase_dense_assemble(P);
                 ACS_SYNC(PH_DENSE_FACTOR);
                 for (int k = 0; k <= P.m && dense; ++k) {
-                    if (!dense_chol_step(sync_smem().dM, P.m, k)) dense = false;
+                    if (!dense_chol_step(sync_smem().dM, P.m, k, P.V.jinv)) {
+                        dense = false;
+                        dense_failed = true;
+                    }
                     ACS_SYNC(PH_DENSE_FACTOR);
                 }
                 if (!ok) break;
@@ -1032,6 +1067,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             }
             if (!ok || status == ACS_ERR_NUMERICAL) break;
             cg_total += k;
+            win_cg += k;
             // an FP32 solve that stalls far above its target cannot refine this M
             if ((broke || k >= P.cg_max) && sqrt(fmax(gam, 0.0)) > 100.0 * thr) trouble = true;
         }
@@ -1064,6 +1100,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             ds = ds_new;
         }
         l = lnext;
+        ++win_it;
         if (sizeof(T) == 4 && trouble && P.switch_ok) { status = ST_SWITCH; break; }
 
         if (check) {

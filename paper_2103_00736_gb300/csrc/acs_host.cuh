@@ -35,14 +35,19 @@ inline bool valid_settings(const acs_settings& set) {
            set.n_cond_list >= 0 && !(set.n_cond_list > 0 && !set.cond_list) &&
            (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP64) &&
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
-           set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit;
+           set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit && set.dense_switch_max_m >= 0 &&
+           set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0;
 }
 
-// Does a problem with m constraints use the cached dense projection operator?
-inline bool use_dense(const acs_settings& set, int m) {
-    if (set.projection == ACS_PROJ_DENSE) return m <= kDenseLimit;
-    if (set.projection == ACS_PROJ_AUTO) return m <= set.dense_max_m;
-    return false;
+// How a problem with m constraints applies the projection: 0 = CG only,
+// 1 = the cached dense operator from the first iteration, 2 = CG, switching
+// to the cached operator if CG stalls.
+inline int dense_mode(const acs_settings& set, int m) {
+    if (set.projection == ACS_PROJ_DENSE) return m <= kDenseLimit ? 1 : 0;
+    if (set.projection != ACS_PROJ_AUTO) return 0;
+    if (m <= set.dense_max_m) return 1;
+    if (set.dense_switch_cg > 0 && m <= set.dense_switch_max_m) return 2;
+    return 0;
 }
 
 // Checks of the problem statement (Section II, Eq. (1)) as the ABI states

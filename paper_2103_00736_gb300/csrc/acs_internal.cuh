@@ -102,7 +102,9 @@ struct IterParams {
     int refresh;                                      // recompute c_hat, b_tilde, J, q first
     int refine;                                       // correction solves per iteration
     int switch_ok;                                    // FP32 launch may hand over to FP64
-    int dense;                                        // cached dense projection operator (FP64 loop)
+    int dense;                                        // cached dense projection operator (FP64 loop):
+                                                      // 0 = never, 1 = from the start, 2 = when CG stalls
+    int dense_switch_cg;                              // CG iterations per outer iteration that switch
     double* dM; double* dX;                           // its scratch in a single-problem launch
 };
 
@@ -139,7 +141,7 @@ struct Problem {
     int warm_l = 0;
     double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 1e-2;
     int last_status = ACS_MAX_ITER;
-    bool dense = false;                  // cached dense projection operator
+    int dense = 0;                       // cached dense operator: 0 never, 1 always, 2 when CG stalls
     double *dM = nullptr, *dX = nullptr; // its scratch, [m * m] each
     std::vector<void*> allocations;
     cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch

@@ -145,7 +145,8 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.refresh = P->warm ? 1 : 0;
     Q.refine = P->set.cg_refine > 0 ? P->set.cg_refine : 1;
     Q.switch_ok = P->set.precision == ACS_PREC_MIXED ? 1 : 0;
-    Q.dense = (sizeof(T) == 8 && P->dense) ? 1 : 0;
+    Q.dense = P->dense;
+    Q.dense_switch_cg = P->set.dense_switch_cg;
     Q.dM = P->dM;
     Q.dX = P->dX;
     return Q;
@@ -206,7 +207,7 @@ int launch_solve(Problem* P, double tol, int max_iter) {
     if (cudaGetLastError() != cudaSuccess) return ACS_ERR_CUDA;
     cudaError_t e;
     if (P->ev_launch[0]) cudaEventRecord(P->ev_launch[0], st);
-    if (P->set.precision == ACS_PREC_FP64 || P->dense) {
+    if (P->set.precision == ACS_PREC_FP64 || P->dense == 1) {
         // the cached operator runs in the FP64 loop (exact corrections)
         IterParams<double> Q = make_params<double>(P, tol, max_iter, P->V64);
         e = launch_iter<double>(P, Q, P->grid64);

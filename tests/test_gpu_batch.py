@@ -181,3 +181,22 @@ def test_batch_dense_and_cg_projection_agree(mixed):
             assert B.solve(tol=1e-7, max_iter=50000) == capi.SOLVED
             objs.append([_check_member(inst, *B.get(i)[1:4])["obj_p"] for i, inst in enumerate(sub)])
     np.testing.assert_allclose(objs[0], objs[1], rtol=2e-6, atol=1e-6)
+
+
+def test_batch_cg_stall_switches_to_cached_operator():
+    """Members with 256 < m <= 512 of the batch recipe under CG first
+    (dense_max_m = 0): where Jacobi-CG averages more than 40 iterations per
+    outer iteration after a rescaling, the member switches to the cached
+    operator; every member still reaches the planted optimum."""
+    rec = I.batch(count=96, m_shared=300, mmin=50, mmax=600)
+    sub = [r for r in rec[24:] if 256 < r.m <= 512][:10]
+    with capi.Batch(sub, dense_max_m=0, dense_switch_max_m=1024, dense_switch_cg=40, **LP) as B:
+        rc = B.solve(tol=1e-7, max_iter=20000)
+        worst, st, iters, res = B.results()
+        cnt = capi.acs_batch_counters(B.h, len(sub))
+        assert rc == capi.SOLVED, (st, iters)
+        for i, inst in enumerate(sub):
+            _check_member(inst, *B.get(i)[1:4])
+    assert np.all(cnt[:, 0] > 0)                 # every member started with CG
+    assert np.any(cnt[:, 7] > 0), cnt            # some switched and factorised
+    print("switched:", int(np.sum(cnt[:, 7] > 0)), "of", len(sub))

@@ -326,3 +326,27 @@ def test_rescaling_with_degenerate_o():
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
     assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+
+
+def test_cached_operator_drops_dependent_rows():
+    """Rank-deficient A (a row repeated, b consistent): the dense Cholesky
+    meets a zero pivot, drops that direction, and the solve stays on the
+    cached operator (no CG) and reaches the planted optimum."""
+    base = I.small_lp()
+    A = base.to_scipy().tolil()
+    import scipy.sparse as sp
+    A2 = sp.vstack([A, A[7] * 2.0]).tocsr()
+    A2.sort_indices()
+    inst = I.Instance(m=base.m + 1, n=base.n, row_ptr=A2.indptr.astype(np.int64),
+                      col=A2.indices.astype(np.int32), val=A2.data, b=A2 @ base.x_star,
+                      c=base.c, n_orth=base.n, soc_dims=base.soc_dims, x_star=base.x_star,
+                      y_star=np.zeros(base.m + 1), s_star=base.s_star)
+    with capi.Solver(inst, **LP_SCHED) as s:
+        st = s.solve(tol=1e-7, max_iter=20000)
+        rc, x, y, z, iters, res = s.get()
+        ph = capi.acs_debug_phase_times(s.h)
+    assert st == capi.SOLVED
+    assert ph["dense_factor"][1] > 0 and ph["dense_solve"][1] == 2 * iters and ph["cg_At"][1] == 0
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
