@@ -323,6 +323,77 @@ int acs_batch_member_ms(acs_batch* b, double* ms);
 
 void acs_batch_destroy(acs_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent solves.
+ *
+ * A worker thread owned by the server admits submitted requests into a
+ * device memory pool of a fixed budget (a request waits while it does not
+ * fit, or while every slot is taken), keeps each admitted request's data and
+ * iterates on the device, and runs rounds: one persistent team launch over
+ * every admitted request, time-sliced by a device-side deadline at which
+ * each request pauses at the end of an iteration.  A paused request resumes
+ * from its device state in the next round exactly where it stopped, so its
+ * result is the one it has when solved alone in a batched launch of the
+ * same mapping.  Finished requests leave between rounds, freeing their slot
+ * and memory for waiting ones, so requests that arrive while others are on
+ * the GPU join the next round.  Requests larger than large_nnz stored
+ * entries run alone, between rounds, on the whole GPU (the single-problem
+ * launch).  Each request is solved by Algorithm 2 like acs_solve, with the
+ * server's settings and its own tol / max_iter.
+ * ------------------------------------------------------------------------ */
+typedef struct acs_server acs_server;
+
+typedef struct {
+    int64_t budget_bytes;    /* device memory for admitted requests; default 4 GiB          */
+    int32_t max_active;      /* slots (requests admitted at once); default 2048             */
+    double round_ms;         /* time slice of one round; default 2 ms                       */
+    int64_t large_nnz;       /* requests whose A has more nonzeros run alone on the whole
+                                GPU; default 262144                                          */
+    int32_t threads_per_cta; /* mapping of the rounds (as acs_batch_mapping); default 256   */
+    int32_t team_ctas;       /* default 1                                                    */
+} acs_server_config;
+
+int acs_server_config_default(acs_server_config* cfg);
+
+/* settings: shared by all requests (NULL = defaults; cuda_stream is ignored,
+ * the server owns its stream).  Errors: ACS_ERR_ARG, ACS_ERR_OOM (the budget
+ * cannot be allocated), ACS_ERR_CUDA. */
+int acs_server_create(const acs_settings* settings, const acs_server_config* cfg, acs_server** out);
+
+/* Validate and prepare a request on the calling thread (host work only) and
+ * queue it; returns at once with *id.  The acs_instance's share_A_with must
+ * be -1.  per_request (may be NULL): this request's mu, t, cond_first,
+ * cond_period and check_every (e.g. the SOCP schedule t = 1.7, L = {200,
+ * 300, ...} for a request with Lorentz cones, the LP one for an LP); every
+ * other setting is the server's, and its cond_list must be empty.
+ * Errors: ACS_ERR_ARG, ACS_ERR_CSR, ACS_ERR_CONES, ACS_ERR_LIMIT (the request
+ * can never fit the budget).  Thread-safe. */
+int acs_server_submit(acs_server* s, const acs_instance* req, double tol, int32_t max_iter,
+                      const acs_settings* per_request, int64_t* id);
+
+/* *done = 1 once request id has finished.  Thread-safe. */
+int acs_server_poll(acs_server* s, int64_t id, int32_t* done);
+
+/* Block until request id has finished or timeout_s has passed (< 0: no
+ * limit).  Returns the request's status, or ACS_ERR_DEVICE_TIMEOUT if the
+ * wait timed out.  Thread-safe. */
+int acs_server_wait(acs_server* s, int64_t id, double timeout_s);
+
+/* Results of a finished request (as acs_get; any pointer may be NULL) and
+ * its latency from submission to completion (ms); then the server forgets
+ * the request.  Returns its status, or ACS_ERR_ARG for an unknown or
+ * unfinished id.  Thread-safe. */
+int acs_server_result(acs_server* s, int64_t id, double* x, double* y, double* sl, int32_t* iters,
+                      double* residuals, double* latency_ms);
+
+/* out[10] = {rounds, requests admitted, requests finished, requests active,
+ * pool bytes in use, peak pool bytes, requests run alone (large), requests
+ * waiting, mean ms per round, mean active requests per round}. */
+int acs_server_stats(acs_server* s, double* out);
+
+/* Finish every submitted request, stop the worker, release everything. */
+void acs_server_destroy(acs_server* s);
+
 /* Library version string. */
 const char* acs_version(void);
 

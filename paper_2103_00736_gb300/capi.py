@@ -61,6 +61,11 @@ class acs_batch_mapping(C.Structure):
     _fields_ = [("threads_per_cta", C.c_int32), ("team_ctas", C.c_int32)]
 
 
+class acs_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("max_active", C.c_int32), ("round_ms", C.c_double),
+                ("large_nnz", C.c_int64), ("threads_per_cta", C.c_int32), ("team_ctas", C.c_int32)]
+
+
 class AcsError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {acs_status_string(code)} ({code})")
@@ -113,6 +118,16 @@ def lib():
         L.acs_batch_counters.argtypes = [P, llp]
         L.acs_batch_member_ms.argtypes = [P, dp]
         L.acs_batch_destroy.argtypes = [P]
+        L.acs_server_config_default.argtypes = [C.POINTER(acs_server_config)]
+        L.acs_server_create.argtypes = [C.POINTER(acs_settings), C.POINTER(acs_server_config), C.POINTER(P)]
+        L.acs_server_submit.argtypes = [P, C.POINTER(acs_instance), C.c_double, C.c_int32,
+                                        C.POINTER(acs_settings), C.POINTER(C.c_int64)]
+        L.acs_server_poll.argtypes = [P, C.c_int64, ip]
+        L.acs_server_wait.argtypes = [P, C.c_int64, C.c_double]
+        L.acs_server_result.argtypes = [P, C.c_int64, dp, dp, dp, ip, dp, dp]
+        L.acs_server_stats.argtypes = [P, dp]
+        L.acs_server_destroy.argtypes = [P]
+        L.acs_server_destroy.restype = None
         L.acs_batch_destroy.restype = None
         _lib = L
     return _lib
@@ -501,6 +516,147 @@ class Batch:
 
     def close(self):
         acs_batch_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# serving loop
+# ---------------------------------------------------------------------------
+
+def acs_server_config_default(**overrides) -> acs_server_config:
+    c = acs_server_config()
+    rc = lib().acs_server_config_default(C.byref(c))
+    if rc != 0:
+        raise AcsError(rc, "acs_server_config_default")
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def acs_server_create(settings=None, config=None):
+    h = C.c_void_p()
+    rc = lib().acs_server_create(C.byref(settings) if settings is not None else None,
+                                 C.byref(config) if config is not None else None, C.byref(h))
+    if rc != 0:
+        raise AcsError(rc, "acs_server_create")
+    return h.value
+
+
+def acs_server_submit(h, inst, tol: float = 1e-6, max_iter: int = 10000, settings=None) -> int:
+    """Queue one request (host arrays are copied during the call); returns its id.
+    settings: per-request mu, t, schedule and check period (acs_settings), or None."""
+    rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(inst.col, dtype=np.int32)
+    vl = np.ascontiguousarray(inst.val, dtype=np.float64)
+    b = np.ascontiguousarray(inst.b, dtype=np.float64)
+    c = np.ascontiguousarray(inst.c, dtype=np.float64)
+    d = np.ascontiguousarray(inst.soc_dims, dtype=np.int32)
+    a = acs_instance()
+    a.m, a.n = int(inst.m), int(inst.n)
+    a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)
+    a.b, a.c = _ptr(b, C.c_double), _ptr(c, C.c_double)
+    a.n_orthant, a.n_soc, a.soc_dims = int(inst.n_orth), int(d.size), _ptr(d, C.c_int32)
+    a.share_A_with = -1
+    rid = C.c_int64()
+    rc = lib().acs_server_submit(C.c_void_p(h), C.byref(a), float(tol), int(max_iter),
+                                 C.byref(settings) if settings is not None else None, C.byref(rid))
+    if rc != 0:
+        raise AcsError(rc, "acs_server_submit")
+    return rid.value
+
+
+def acs_server_poll(h, rid: int) -> bool:
+    done = C.c_int32()
+    rc = lib().acs_server_poll(C.c_void_p(h), int(rid), C.byref(done))
+    if rc != 0:
+        raise AcsError(rc, "acs_server_poll")
+    return bool(done.value)
+
+
+def acs_server_wait(h, rid: int, timeout_s: float = -1.0) -> int:
+    return lib().acs_server_wait(C.c_void_p(h), int(rid), float(timeout_s))
+
+
+def acs_server_result(h, rid: int, m: int, n: int):
+    """(status, x, y, s, iters, residuals[8], latency_ms) of a finished request."""
+    x, y, s, res = np.empty(n), np.empty(m), np.empty(n), np.empty(8)
+    it = C.c_int32()
+    lat = C.c_double()
+    rc = lib().acs_server_result(C.c_void_p(h), int(rid), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                                 _ptr(s, C.c_double), C.byref(it), _ptr(res, C.c_double), C.byref(lat))
+    return rc, x, y, s, it.value, res, lat.value
+
+
+def acs_server_stats(h) -> dict:
+    out = np.zeros(10)
+    rc = lib().acs_server_stats(C.c_void_p(h), _ptr(out, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_server_stats")
+    keys = ("rounds", "admitted", "finished", "active", "pool_bytes", "pool_peak_bytes", "large",
+            "waiting", "round_ms_mean", "active_mean")
+    return dict(zip(keys, out.tolist()))
+
+
+def acs_server_destroy(h) -> None:
+    if h:
+        lib().acs_server_destroy(C.c_void_p(h))
+
+
+LP_SCHEDULE = dict(t=9.2, cond_first=300, cond_period=100)      # Section V-A experiments
+SOCP_SCHEDULE = dict(t=1.7, cond_first=200, cond_period=100)    # Section V-C experiments
+
+
+def schedule_for(inst) -> acs_settings:
+    """Per-request settings with the paper's schedule for the request's cone type."""
+    return acs_settings_default(**(SOCP_SCHEDULE if len(inst.soc_dims) else LP_SCHEDULE))
+
+
+class Server:
+    """Owner of one serving loop."""
+
+    def __init__(self, settings=None, config=None, **cfg):
+        if config is None:
+            config = acs_server_config_default(**cfg)
+        self.h = acs_server_create(settings, config)
+        self.shapes = {}
+
+    def submit(self, inst, tol=1e-6, max_iter=10000, settings="auto") -> int:
+        """settings="auto": the paper's LP schedule (t = 9.2, L = {300, 400, ...})
+        for an LP, its SOCP schedule (t = 1.7, L = {200, 300, ...}) for a
+        request with Lorentz cones."""
+        if isinstance(settings, str) and settings == "auto":
+            settings = schedule_for(inst)
+        rid = acs_server_submit(self.h, inst, tol, max_iter, settings)
+        self.shapes[rid] = (int(inst.m), int(inst.n))
+        return rid
+
+    def wait(self, rid, timeout_s=-1.0) -> int:
+        return acs_server_wait(self.h, rid, timeout_s)
+
+    def result(self, rid):
+        m, n = self.shapes.pop(rid)
+        return acs_server_result(self.h, rid, m, n)
+
+    def stats(self) -> dict:
+        return acs_server_stats(self.h)
+
+    def close(self):
+        acs_server_destroy(self.h)
         self.h = None
 
     def __enter__(self):

@@ -23,180 +23,13 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 #include <new>
 #include <numeric>
-#include <type_traits>
 #include <vector>
 
-#include "acs_device.cuh"
-#include "acs_host.cuh"
+#include "acs_team.cuh"
 
 namespace acs {
-
-// ---------------------------------------------------------------------------
-// device
-// ---------------------------------------------------------------------------
-
-struct BatchArgs {
-    int count;                        // members
-    const int* order;                 // [count] members in the order teams take them
-    const IterParams<float>* p32;     // [count] parameters of the FP32-correction loop
-    const IterParams<double>* p64;    // [count] parameters of the FP64-correction loop
-    Control* ctl;                     // [count]
-    int* head;                        // next position in order
-    int* mailbox;                     // [teams] member posted by the team's rank 0
-    unsigned long long* team_bar;     // [teams] barrier arrival counters
-    double* team_part;                // [CTAs * kMaxRed] partials
-    int* team_err;                    // [teams] barrier failures outside a member's solve
-    double* dense;                    // [teams * 2 * dense_m2] scratch of the cached operator
-    long long dense_m2;               // (largest m among members that use it)^2
-    int g;                            // CTAs per team
-    int fp64;                         // FP64 correction solve from the start
-};
-
-__global__ void batch_reset(BatchArgs B, double eta0) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = t; i < B.count; i += gridDim.x * blockDim.x) {
-        Control* c = B.ctl + i;
-        c->status = ST_RUNNING;
-        c->err = 0;
-        c->l = 0;
-        c->cg_iters = 0;
-        c->switched_at = 0;
-        for (int k = 0; k < 6; ++k) c->res[k] = NAN;
-        c->ds = INFINITY;
-        c->snorm = 0.0;
-        c->eta = eta0;
-        c->n_cg_A = c->n_cg_AT = c->n_64_A = c->n_64_AT = c->n_cond = c->n_checks = 0;
-        for (int k = 0; k < PH_COUNT; ++k) { c->phase_ns[k] = 0; c->phase_n[k] = 0; }
-        c->bar_count = 0;
-        c->bar_gen = 0;
-        c->bar_count64 = 0;
-    }
-    if (t == 0) *B.head = 0;
-}
-
-__global__ void batch_reset_teams(BatchArgs B, int teams) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < teams; t += gridDim.x * blockDim.x) {
-        B.team_bar[t] = 0ull;
-        B.team_err[t] = 0;
-        B.mailbox[t] = 0;
-    }
-}
-
-// Initial point of Algorithm 2 (x = z = e, the cone identity; w = q = 0),
-// written by the whole team.
-template <typename T>
-__device__ void init_member(const IterParams<T>& P) {
-    for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
-        P.x[j] = 1.0;
-        P.z[j] = 1.0;
-        P.X.q[j] = 0.0;
-    }
-    const int lane = threadIdx.x & 31;
-    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
-        const int a = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
-        for (int j = a + lane; j < e; j += 32) {
-            const double v = (j == a) ? 1.0 : 0.0;
-            P.x[j] = v;
-            P.z[j] = v;
-            P.X.q[j] = 0.0;
-        }
-    }
-    for (int i = global_tid(); i < P.m; i += global_threads()) P.X.w[i] = 0.0;
-}
-
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B) {
-    const int team = (int)blockIdx.x / B.g, rank = (int)blockIdx.x % B.g;
-    double* scratch = B.dense ? B.dense + (size_t)team * 2 * B.dense_m2 : nullptr;
-    team_set(rank, B.g, B.team_bar + team, B.team_part + (size_t)team * B.g * kMaxRed, scratch,
-             scratch ? scratch + B.dense_m2 : nullptr);
-    sync_init(0u);
-    __shared__ int s_k;
-    while (true) {
-        // the team's rank 0 takes the next member; the barrier publishes it
-        if (rank == 0 && threadIdx.x == 0) B.mailbox[team] = atomicAdd(B.head, 1);
-        if (!grid_sync(B.team_err + team)) return;
-        if (threadIdx.x == 0) s_k = __ldcg(B.mailbox + team);
-        __syncthreads();
-        const int k = s_k;
-        if (k >= B.count) return;
-        const int i = __ldg(B.order + k);
-        Control* ctl = B.ctl + i;
-        sync_init(sync_smem().gen);                      // clear a failure of the previous member
-        int st;
-        if (B.fp64 || B.p64[i].dense == 1) {             // the cached operator runs in the FP64 loop
-            const IterParams<double>& P = B.p64[i];
-            init_member(P);
-            if (!grid_sync(&ctl->err)) return;
-            st = solve_loop<double>(P, ST_RUNNING);
-        } else {
-            const IterParams<float>& P = B.p32[i];
-            init_member(P);
-            if (!grid_sync(&ctl->err)) return;
-            st = solve_loop<float>(P, ST_RUNNING);
-            if (st == ST_SWITCH) {
-                // the loop's state is in ctl (written by rank 0): publish it
-                if (!grid_sync(&ctl->err)) return;
-                solve_loop<double>(B.p64[i], ST_SWITCH);
-            }
-        }
-        // a barrier that timed out leaves the team out of step: stop it
-        if (ld_volatile_int(&ctl->err) == ACS_ERR_DEVICE_TIMEOUT) return;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// host
-// ---------------------------------------------------------------------------
-
-namespace {
-
-constexpr int kThreadChoices[3] = {256, 512, 1024};
-constexpr int kTeamChoices[3] = {1, 2, 4};
-
-// Bump allocator over one device allocation; a dry run (base = 0) measures.
-struct Pool {
-    char* base = nullptr;
-    size_t off = 0;
-    template <typename T>
-    T* take(size_t count) {
-        off = (off + 255) & ~(size_t)255;
-        T* p = reinterpret_cast<T*>(base + off);
-        off += (count ? count : 1) * sizeof(T);
-        return p;
-    }
-};
-
-struct DevSell {      // offsets of one sliced-ELLPACK matrix inside the pool
-    int* sptr; int* slen; int* col; float* v32; double* v64;
-};
-
-struct Matrix {       // one distinct A of the batch
-    host::HostProblem H;            // host image (released after upload)
-    SellMat A{}, AT{};
-    DevSell dA{}, dAT{};
-    long long stored = 0;
-};
-
-struct Member {
-    int m = 0, n = 0, n_orth = 0, n_soc = 0, mat = 0;
-    int dense = 0;                    // cached dense operator: 0 never, 1 always, 2 when CG stalls
-    long long nnz = 0;
-    std::vector<double> b, c;
-    std::vector<int> soc_off;
-    double bnorm = 0, cnorm = 0;
-    // device pointers inside the pool
-    double *db = nullptr, *dc = nullptr, *x = nullptr, *z = nullptr, *ocone = nullptr;
-    int* dsoc = nullptr;
-    Outer X{};
-    Inner<float> V32{};
-    Inner<double> V64{};
-};
-
-}  // namespace
 
 struct Batch {
     int count = 0, device = 0, nsm = 0;
@@ -236,26 +69,6 @@ struct Batch {
 
 namespace {
 
-int occupancy_for(int threads, int* blocks_per_sm) {
-    cudaError_t e = cudaErrorInvalidValue;
-    if (threads == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<256>, 256, 0);
-    if (threads == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<512>, 512, 0);
-    if (threads == 1024) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<1024>, 1024, 0);
-    return e == cudaSuccess && *blocks_per_sm >= 1 ? ACS_SOLVED : ACS_ERR_CUDA;
-}
-
-const void* kernel_for(int threads) {
-    if (threads == 256) return (const void*)batch_kernel<256>;
-    if (threads == 512) return (const void*)batch_kernel<512>;
-    return (const void*)batch_kernel<1024>;
-}
-
-bool valid_mapping(const acs_batch_mapping& m) {
-    const bool t = m.threads_per_cta == 256 || m.threads_per_cta == 512 || m.threads_per_cta == 1024;
-    const bool g = m.team_ctas == 1 || m.team_ctas == 2 || m.team_ctas == 4 || m.team_ctas == 8;
-    return t && g;
-}
-
 // CTAs of a launch under mapping m: every resident CTA, in whole teams.
 int grid_for(Batch* B, const acs_batch_mapping& m, int* grid) {
     int bps = 0;
@@ -267,46 +80,15 @@ int grid_for(Batch* B, const acs_batch_mapping& m, int* grid) {
     return ACS_SOLVED;
 }
 
-template <typename T>
-IterParams<T> member_params(const Batch* B, const Member& M, const Matrix& X, const Inner<T>& V, double tol,
-                            int max_iter) {
-    IterParams<T> Q{};
-    Q.m = M.m; Q.n = M.n; Q.n_orth = M.n_orth; Q.n_soc = M.n_soc;
-    Q.A = X.A; Q.AT = X.AT;
-    Q.soc_off = M.dsoc;
-    Q.b = M.db; Q.c = M.dc; Q.bnorm = M.bnorm; Q.cnorm = M.cnorm;
-    Q.X = M.X;
-    Q.V = V;
-    Q.x = M.x; Q.z = M.z; Q.ocone = M.ocone;
-    Q.partials = nullptr; Q.flags = nullptr; Q.release = nullptr; Q.bcast = nullptr;
-    Q.ctl = nullptr;
-    Q.mu = B->set.mu; Q.t_cond = B->set.t;
-    Q.cond_first = B->set.cond_first; Q.cond_period = B->set.cond_period;
-    Q.cond_list = B->d_cond_list; Q.n_cond_list = (int)B->cond_list_host.size();
-    Q.check_every = B->set.check_every > 0 ? B->set.check_every : 1;
-    Q.max_iter = max_iter;
-    Q.tol = tol;
-    Q.cg_eta = B->set.cg_eta;
-    Q.cg_tol = B->set.cg_tol;
-    Q.cg_relfloor = sizeof(T) == 4 ? 1e-6 : 1e-13;
-    Q.cg_max = B->set.cg_max_iter;
-    Q.refresh = 0;
-    Q.refine = B->set.cg_refine > 0 ? B->set.cg_refine : 1;
-    Q.switch_ok = B->set.precision == ACS_PREC_MIXED ? 1 : 0;
-    Q.dense = M.dense;
-    Q.dense_switch_cg = B->set.dense_switch_cg;
-    Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
-    return Q;
-}
-
 // Write the per-member parameter blocks for (tol, max_iter).
 int upload_params(Batch* B, double tol, int max_iter) {
     std::vector<IterParams<float>> p32(B->count);
     std::vector<IterParams<double>> p64(B->count);
     for (int i = 0; i < B->count; ++i) {
         const Member& M = B->mem[i];
-        p32[i] = member_params<float>(B, M, B->mats[M.mat], M.V32, tol, max_iter);
-        p64[i] = member_params<double>(B, M, B->mats[M.mat], M.V64, tol, max_iter);
+        const int ncl = (int)B->cond_list_host.size();
+        p32[i] = member_params<float>(B->set, B->d_cond_list, ncl, M, B->mats[M.mat], M.V32, tol, max_iter);
+        p64[i] = member_params<double>(B->set, B->d_cond_list, ncl, M, B->mats[M.mat], M.V64, tol, max_iter);
         p32[i].ctl = B->d_ctl + i;
         p64[i].ctl = B->d_ctl + i;
     }
@@ -420,12 +202,6 @@ int fetch_controls(Batch* B) {
     return ACS_SOLVED;
 }
 
-int member_status(const Control& C) {
-    int s = C.status;
-    if (s == ST_RUNNING || s == ST_SWITCH) s = ACS_ERR_CUDA;   // never finished
-    return s;
-}
-
 // Lay out (dry run with base = 0, then for real) every device buffer.
 void layout(Batch* B, Pool& P) {
     const int count = B->count;
@@ -479,11 +255,6 @@ void layout(Batch* B, Pool& P) {
     B->total_bytes = P.off;
 }
 
-template <typename T>
-void put_bytes(std::vector<char>& img, const void* dev_off, const T* src, size_t count) {
-    if (count) memcpy(img.data() + reinterpret_cast<size_t>(dev_off), src, count * sizeof(T));
-}
-
 void free_batch(Batch* B) {
     if (!B) return;
     drop_graph(B);
@@ -495,11 +266,6 @@ void free_batch(Batch* B) {
     }
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
     B->stream = nullptr;
-}
-
-template <typename T>
-T* rebase(T* off, char* base) {
-    return reinterpret_cast<T*>(base + reinterpret_cast<size_t>(off));
 }
 
 }  // namespace

@@ -53,6 +53,7 @@ struct SyncShared {
     double* tpart;            // the team's partials, [team_size * kMaxRed]
     double* dM;               // the team's dense scratch for the cached projection operator:
     double* dX;               //   M / its Cholesky factor and L^{-1}, [m * m] each
+    unsigned long long deadline;  // global-timer time at which a time-sliced solve pauses (0 = none)
     double blk[kMaxRed];      // this CTA's partials
     double out[kMaxRed];      // grid-reduced values of the last barrier
     double wsum[kWarps][kMaxRed];
@@ -81,6 +82,7 @@ __device__ __forceinline__ void team_set(int rank, int size, unsigned long long*
         S.tpart = partials;
         S.dM = dense_M;
         S.dX = dense_X;
+        S.deadline = 0ull;
     }
     __syncthreads();
 }
@@ -652,9 +654,13 @@ __device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, b
         }
     };
     sell_rows<double>(P.AT, gather, epi);
-    const double v[2] = {ds2, ss2};
-    const int op[2] = {0, 0};
-    block_partials<2>(v, op, P.partials);
+    // a time-sliced solve: has the deadline passed (one clock read per CTA,
+    // max-reduced, so every CTA of the team takes the same decision)?
+    const unsigned long long dl = sync_smem().deadline;
+    const double over = (update && dl != 0ull && threadIdx.x == 0 && gtimer() > dl) ? 1.0 : 0.0;
+    const double v[3] = {ds2, ss2, over};
+    const int op[3] = {0, 0, 1};
+    block_partials<3>(v, op, P.partials);
 }
 
 // FP64 residual partials: ||Ax - b||^2, ||A'y + z - c||^2 (y = w/mu), c'x, b'y,
@@ -911,11 +917,16 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     // An FP32 loop hands over to the FP64 loop for that; an FP64 loop that
     // takes over this way factors at once.
     const bool have_scratch = sync_smem().dM != nullptr;
-    bool dense = sizeof(T) == 8 && have_scratch && (P.dense == 1 || (P.dense == 2 && status0 == ST_SWITCH));
+    bool dense = sizeof(T) == 8 && have_scratch &&
+                 (P.dense == 1 || (P.dense == 2 && (status0 == ST_SWITCH || __ldcg(&ctl->dense_on) != 0)));
     const bool may_switch = P.dense == 2 && (sizeof(T) == 4 ? P.switch_ok != 0 : have_scratch);
-    bool dense_failed = false;
-    long long win_cg = 0;
-    int win_it = 0;
+    bool dense_failed = __ldcg(&ctl->dense_failed) != 0;
+    // a factor held in the problem's own scratch stays valid across a pause
+    // (O changes only at rescalings, which refactor)
+    bool factor_kept = P.own_scratch != 0 && __ldcg(&ctl->dense_on) != 0;
+    bool over = false;                                  // deadline of a time-sliced solve passed
+    long long win_cg = __ldcg(&ctl->win_cg);
+    int win_it = __ldcg(&ctl->win_it);
     long long ndense = 0, nfactor = 0;
 
 // grid barrier that ends phase `ph`; leaves the enclosing loop on error
@@ -972,7 +983,10 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             const int op[1] = {0};
             grid_combine<1>(P.partials, op, bb);
             if (bb[0] > 0.0) { atomicCAS(&ctl->err, 0, ACS_ERR_FACTOR); ok = false; break; }
-            if (dense) {
+            if (dense && factor_kept && !cond) {
+                factor_kept = false;                        // resumed: the cached factor is current
+            } else if (dense) {
+                factor_kept = false;
                 phase_dense_assemble(P);
                 ACS_SYNC(PH_DENSE_FACTOR);
                 for (int k = 0; k <= P.m && dense; ++k) {
@@ -1079,11 +1093,12 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ++nAT64;
         ACS_SYNC(PH_UPDATE);
         {
-            double d2[2];
-            const int op[2] = {0, 0};
-            grid_combine<2>(P.partials, op, d2);
+            double d2[3];
+            const int op[3] = {0, 0, 1};
+            grid_combine<3>(P.partials, op, d2);
             const double ds_new = sqrt(d2[0]);
             snorm = sqrt(d2[1]);
+            over = d2[2] > 0.0;
             if (!isfinite(ds_new) || !isfinite(snorm)) { status = ACS_ERR_NUMERICAL; l = lnext; break; }
             // With exact projections the step norm ||s_l - s_{l-1}|| never grows
             // between rescalings (the iteration map is firmly nonexpansive,
@@ -1122,6 +1137,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             if (!isfinite(mx)) { status = ACS_ERR_NUMERICAL; break; }
             if (mx <= P.tol) { status = ACS_SOLVED; break; }
         }
+        if (over && l < P.max_iter) { status = ST_PAUSED; break; }
     }
 #undef ACS_SYNC
 
@@ -1143,6 +1159,11 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ctl->n_checks += nchk;
         ctl->n_dense_solve += ndense;
         ctl->n_dense_factor += nfactor;
+        ctl->stage = (sizeof(T) == 8 || status == ST_SWITCH) ? 1 : 0;
+        ctl->dense_on = dense ? 1 : 0;
+        ctl->dense_failed = dense_failed ? 1 : 0;
+        ctl->win_cg = win_cg;
+        ctl->win_it = win_it;
         ctl->bar_gen = sync_smem().gen;
         for (int i = 0; i < PH_COUNT; ++i) {
             ctl->phase_ns[i] += s_ph_ns[i];

@@ -18,7 +18,11 @@ constexpr int kMaxRed = 8;              // doubles reduced per grid reduction
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s per barrier
 
 // device-side status value of a solve still in progress
-enum : int { ST_RUNNING = 100, ST_SWITCH = 101 /* FP32 correction solve handed over to FP64 */ };
+enum : int {
+    ST_RUNNING = 100,
+    ST_SWITCH = 101,   // FP32 correction solve handed over to FP64
+    ST_PAUSED = 102    // a time-sliced solve stopped at its deadline; resumable
+};
 
 // phases of the persistent kernel, for the per-phase time record
 enum Phase : int {
@@ -43,6 +47,11 @@ struct Control {
     // pass counters (for the algorithmic-byte model of the benchmark)
     long long n_cg_A, n_cg_AT, n_64_A, n_64_AT, n_cond, n_checks;
     long long n_dense_solve, n_dense_factor;   // cached-operator corrections and factorisations
+    int stage;            // loop that runs the solve: 0 = FP32 correction CG, 1 = FP64 loop
+    int dense_on;         // the cached dense operator is in use (kept across pauses)
+    int dense_failed;     // its factorisation failed for this solve
+    int win_it;           // outer iterations in the current CG-stall window
+    long long win_cg;     // CG iterations in that window
     unsigned bar_count, bar_gen;
     unsigned long long bar_count64;   // monotonic barrier arrival counter of the current solve
     // nanoseconds spent in each phase (from one barrier exit to the next, as
@@ -105,7 +114,9 @@ struct IterParams {
     int dense;                                        // cached dense projection operator (FP64 loop):
                                                       // 0 = never, 1 = from the start, 2 = when CG stalls
     int dense_switch_cg;                              // CG iterations per outer iteration that switch
-    double* dM; double* dX;                           // its scratch in a single-problem launch
+    double* dM; double* dX;                           // its scratch: single-problem launch, or a member
+                                                      // that keeps its own (NULL: the team's)
+    int own_scratch;                                  // dM/dX belong to this problem and outlive a launch
 };
 
 struct Problem {

@@ -113,6 +113,11 @@ __global__ void reset_control(Control* ctl, int l, double ds, double snorm, doub
     ctl->bar_count = 0;
     ctl->bar_gen = 0;
     ctl->bar_count64 = 0;
+    ctl->stage = 0;
+    ctl->dense_on = 0;
+    ctl->dense_failed = 0;
+    ctl->win_it = 0;
+    ctl->win_cg = 0;
 }
 
 // ---------------------------------------------------------------------------
