@@ -257,13 +257,13 @@ void admit(Server* S, Request* R) {
     cudaMemsetAsync(base + R->static_bytes, 0, R->bytes - R->static_bytes, S->stream);
     std::vector<char>().swap(R->image);
     // offsets -> device addresses
-    auto fin = [&](const host::HostSell& H, const DevSell& D, SellMat& Sm) {
-        Sm.nrows = H.nrows; Sm.nslices = H.nslices; Sm.g = H.g;
+    // (the shapes were recorded at submission, when the host image was built)
+    auto fin = [&](const DevSell& D, SellMat& Sm) {
         Sm.sptr = rebase(D.sptr, base); Sm.slen = rebase(D.slen, base); Sm.col = rebase(D.col, base);
         Sm.v32 = rebase(D.v32, base); Sm.v64 = rebase(D.v64, base);
     };
-    fin(R->X.H.A, R->X.dA, R->X.A);
-    fin(R->X.H.AT, R->X.dAT, R->X.AT);
+    fin(R->X.dA, R->X.A);
+    fin(R->X.dAT, R->X.AT);
     Member& M = R->M;
     M.db = rebase(M.db, base); M.dc = rebase(M.dc, base); M.dsoc = rebase(M.dsoc, base);
     M.x = rebase(M.x, base); M.z = rebase(M.z, base); M.ocone = rebase(M.ocone, base);
@@ -599,6 +599,11 @@ int acs_server_submit(acs_server* h, const acs_instance* I, double tol, int32_t 
             return ACS_ERR_LIMIT;
         }
         request_image(R);
+        auto shape = [](const host::HostSell& H, SellMat& Sm) {
+            Sm.nrows = H.nrows; Sm.nslices = H.nslices; Sm.g = H.g;
+        };
+        shape(R->X.H.A, R->X.A);
+        shape(R->X.H.AT, R->X.AT);
         // the host images are no longer needed (keep the row relabelling)
         std::vector<int> perm = std::move(R->X.H.perm);
         R->X.H = host::HostProblem();
