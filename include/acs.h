@@ -380,8 +380,9 @@ int acs_server_poll(acs_server* s, int64_t id, int32_t* done);
 int acs_server_wait(acs_server* s, int64_t id, double timeout_s);
 
 /* Results of a finished request (as acs_get; any pointer may be NULL) and
- * its latency from submission to completion (ms); then the server forgets
- * the request.  Returns its status, or ACS_ERR_ARG for an unknown or
+ * its latency (ms) from the entry of acs_server_submit (host preparation
+ * included) to the moment its results were in host memory; then the server
+ * forgets the request.  Returns its status, or ACS_ERR_ARG for an unknown or
  * unfinished id.  Thread-safe. */
 int acs_server_result(acs_server* s, int64_t id, double* x, double* y, double* sl, int32_t* iters,
                       double* residuals, double* latency_ms);

@@ -559,6 +559,7 @@ int acs_server_submit(acs_server* h, const acs_instance* I, double tol, int32_t 
     const int vrc = host::validate(I->m, I->n, I->row_ptr, I->col, I->val, I->b, I->c, I->n_orthant, I->n_soc,
                                    I->soc_dims);
     if (vrc != ACS_SOLVED) return vrc;
+    const Clock::time_point t_entry = Clock::now();   // latency includes the host preparation
     Request* R = new (std::nothrow) Request();
     if (!R) return ACS_ERR_OOM;
     R->tol = tol;
@@ -614,7 +615,7 @@ int acs_server_submit(acs_server* h, const acs_instance* I, double tol, int32_t 
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R->id = S->next_id++;
-        R->t_submit = Clock::now();
+        R->t_submit = t_entry;
         S->reqs[R->id] = R;
         S->pending.push_back(R);
         *id = R->id;
