@@ -334,12 +334,16 @@ void acs_batch_destroy(acs_batch* b);
  * each request pauses at the end of an iteration.  A paused request resumes
  * from its device state in the next round exactly where it stopped, so its
  * result is the one it has when solved alone in a batched launch of the
- * same mapping.  Finished requests leave between rounds, freeing their slot
- * and memory for waiting ones, so requests that arrive while others are on
- * the GPU join the next round.  Requests larger than large_nnz stored
- * entries run alone, between rounds, on the whole GPU (the single-problem
- * launch).  Each request is solved by Algorithm 2 like acs_solve, with the
- * server's settings and its own tol / max_iter.
+ * same mapping.  When fewer requests are admitted than the launch has
+ * CTAs, every request gets a team of its own sized by its work (so a few
+ * large requests spread over the whole GPU); otherwise teams of the
+ * configured size take requests from a queue.  Finished requests leave
+ * between rounds, freeing their slot and memory for waiting ones, so
+ * requests that arrive while others are on the GPU join the next round.
+ * Requests larger than large_nnz stored entries run alone, between rounds,
+ * on the whole GPU (the single-problem launch).  Each request is solved by
+ * Algorithm 2 like acs_solve, with the server's settings and its own tol /
+ * max_iter.
  * ------------------------------------------------------------------------ */
 typedef struct acs_server acs_server;
 
@@ -348,9 +352,15 @@ typedef struct {
     int32_t max_active;      /* slots (requests admitted at once); default 2048             */
     double round_ms;         /* time slice of one round; default 2 ms                       */
     int64_t large_nnz;       /* requests whose A has more nonzeros run alone on the whole
-                                GPU; default 262144                                          */
+                                GPU; default 8388608                                         */
     int32_t threads_per_cta; /* mapping of the rounds (as acs_batch_mapping); default 256   */
     int32_t team_ctas;       /* default 1                                                    */
+    int32_t adaptive_teams;  /* 1 (default): work-sized teams while fewer requests than CTAs
+                                are admitted; 0: always queued teams of team_ctas CTAs, so
+                                that every request's arithmetic (reduction order included) is
+                                the same in every round and a served result equals, bit for
+                                bit, the request solved alone by acs_batch_solve with the same
+                                mapping                                                        */
 } acs_server_config;
 
 int acs_server_config_default(acs_server_config* cfg);

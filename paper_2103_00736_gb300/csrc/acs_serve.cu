@@ -134,6 +134,7 @@ struct Server {
     unsigned long long* d_team_bar = nullptr;
     double* d_team_part = nullptr;
     int* d_team_err = nullptr;
+    int* d_cta = nullptr;                         // [3 * max_ctas] assigned teams: k, rank, size
     unsigned long long* d_t0 = nullptr;
     int* d_cond_list = nullptr;
     std::vector<int> cond_list_host;
@@ -349,6 +350,58 @@ void run_large(Server* S, Request* R) {
     finish(S, R);
 }
 
+int pow2_floor(long long v) {
+    int p = 1;
+    while ((long long)p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Teams of their own for the requests of a round with fewer requests than
+// CTAs: every request gets a power-of-two team sized by its share of the
+// round's work (stored entries, vectors, and m^2 for a cached dense factor),
+// capped where more CTAs would only add barrier cost (one CTA per 16384
+// units of work); spare CTAs go to the requests with the most work per CTA.
+// Fills cta[3 * grid] = (position in order or -1, rank, team size).
+void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& cta) {
+    const int n = (int)act.size();
+    std::vector<double> w(n);
+    std::vector<int> g(n), cap(n);
+    double total = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const Member& M = act[k]->M;
+        w[k] = (double)M.nnz * 2 + M.m + M.n + (M.dense ? 0.25 * (double)M.m * M.m : 0.0);
+        total += w[k];
+        cap[k] = std::min(pow2_floor(std::max(1LL, (long long)(w[k] / 16384.0))), std::min(grid, kMaxGrid));
+    }
+    long long used = 0;
+    for (int k = 0; k < n; ++k) {
+        g[k] = std::min(cap[k], pow2_floor(std::max(1LL, (long long)(grid * w[k] / total))));
+        used += g[k];
+    }
+    while (used > grid) {                          // halve the largest team
+        int j = (int)(std::max_element(g.begin(), g.end()) - g.begin());
+        used -= g[j] / 2;
+        g[j] /= 2;
+    }
+    while (true) {                                 // double where work per CTA is largest
+        int best = -1;
+        for (int k = 0; k < n; ++k)
+            if (g[k] < cap[k] && used + g[k] <= grid && (best < 0 || w[k] / g[k] > w[best] / g[best])) best = k;
+        if (best < 0) break;
+        used += g[best];
+        g[best] *= 2;
+    }
+    cta.assign(3 * (size_t)grid, 0);
+    for (int b = 0; b < grid; ++b) cta[b] = -1;
+    int b = 0;
+    for (int k = 0; k < n; ++k)
+        for (int r = 0; r < g[k]; ++r, ++b) {
+            cta[b] = k;
+            cta[grid + b] = r;
+            cta[2 * grid + b] = g[k];
+        }
+}
+
 // One time-sliced launch over every active request; retire the finished.
 void run_round(Server* S) {
     std::vector<Request*> act = S->active;
@@ -357,11 +410,17 @@ void run_round(Server* S) {
     for (size_t k = 0; k < act.size(); ++k) order[k] = act[k]->slot;
     cudaStream_t st = S->stream;
     cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st);
-    const int teams = S->grid / S->map.team_ctas;
+    // fewer requests than CTAs: teams of their own, sized by work
+    const bool assigned = S->cfg.adaptive_teams != 0 && (int)act.size() <= S->grid;
+    std::vector<int> cta;
+    if (assigned) {
+        assign_teams(act, S->grid, cta);
+        cudaMemcpyAsync(S->d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice, st);
+    }
     cudaMemsetAsync(S->d_head, 0, sizeof(int), st);
     cudaMemsetAsync(S->d_t0, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(S->d_team_bar, 0, sizeof(unsigned long long) * teams, st);
-    cudaMemsetAsync(S->d_team_err, 0, sizeof(int) * teams, st);
+    cudaMemsetAsync(S->d_team_bar, 0, sizeof(unsigned long long) * S->max_ctas, st);
+    cudaMemsetAsync(S->d_team_err, 0, sizeof(int) * S->max_ctas, st);
     BatchArgs a{};
     a.count = (int)order.size();
     a.order = S->d_order;
@@ -379,6 +438,11 @@ void run_round(Server* S) {
     a.round_ns = (unsigned long long)(S->cfg.round_ms * 1e6);
     a.g = S->map.team_ctas;
     a.fp64 = S->set.precision == ACS_PREC_FP64 ? 1 : 0;
+    if (assigned) {
+        a.cta_k = S->d_cta;
+        a.cta_rank = S->d_cta + S->grid;
+        a.cta_g = S->d_cta + 2 * S->grid;
+    }
     void* args[] = {(void*)&a};
     const auto t0 = Clock::now();
     cudaError_t e = cudaLaunchCooperativeKernel(kernel_for(S->map.threads_per_cta), dim3(S->grid),
@@ -467,9 +531,10 @@ int acs_server_config_default(acs_server_config* c) {
     c->budget_bytes = (int64_t)4 << 30;
     c->max_active = 2048;
     c->round_ms = 2.0;
-    c->large_nnz = 262144;
+    c->large_nnz = (int64_t)1 << 23;
     c->threads_per_cta = 256;
     c->team_ctas = 1;
+    c->adaptive_teams = 1;
     return ACS_SOLVED;
 }
 
@@ -527,6 +592,7 @@ int acs_server_create(const acs_settings* settings, const acs_server_config* cfg
     rc |= salloc(S, &S->d_team_bar, S->max_ctas);
     rc |= salloc(S, &S->d_team_part, (size_t)S->max_ctas * kMaxRed);
     rc |= salloc(S, &S->d_team_err, S->max_ctas);
+    rc |= salloc(S, &S->d_cta, 3 * (size_t)S->max_ctas);
     rc |= salloc(S, &S->d_t0, 1);
     rc |= salloc(S, &S->d_cond_list, S->cond_list_host.size());
     if (rc) return fail(ACS_ERR_OOM);

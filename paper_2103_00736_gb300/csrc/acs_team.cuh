@@ -38,6 +38,9 @@ struct BatchArgs {
     long long dense_m2;               // (largest m among members that use it)^2
     unsigned long long* round_t0;     // time-sliced launch: global-timer start of the launch
     unsigned long long round_ns;      //   and its length (0 = run every member to its end)
+    const int* cta_k;                 // assigned teams: per CTA, position in order (-1 = idle),
+    const int* cta_rank;              //   rank in its team,
+    const int* cta_g;                 //   and team size; NULL = queued teams of g CTAs
     int g;                            // CTAs per team
     int fp64;                         // FP64 correction solve from the start
 };
@@ -99,14 +102,42 @@ __device__ void init_member(const IterParams<T>& P) {
     for (int i = global_tid(); i < P.m; i += global_threads()) P.X.w[i] = 0.0;
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B) {
-    const int team = (int)blockIdx.x / B.g, rank = (int)blockIdx.x % B.g;
-    double* scratch = B.dense ? B.dense + (size_t)team * 2 * B.dense_m2 : nullptr;
-    team_set(rank, B.g, B.team_bar + team, B.team_part + (size_t)team * B.g * kMaxRed, scratch,
-             scratch ? scratch + B.dense_m2 : nullptr);
-    sync_init(0u);
-    __shared__ int s_k;
+// One member's solve (or its time slice) by the calling team.  Returns false
+// if the team must stop (a barrier failed or timed out).
+__device__ __noinline__ bool run_member(const BatchArgs& B, int i, double* scratch, unsigned long long deadline) {
+    Control* ctl = B.ctl + i;
+    sync_init(sync_smem().gen);                          // clear a failure of the previous member
+    if (threadIdx.x == 0) {
+        SyncShared& S = sync_smem();
+        // a member with scratch of its own keeps its cached factor across launches
+        S.dM = B.p64[i].dM ? B.p64[i].dM : scratch;
+        S.dX = B.p64[i].dX ? B.p64[i].dX : (scratch ? scratch + B.dense_m2 : nullptr);
+        S.deadline = deadline;
+    }
+    __syncthreads();
+    // a resumed member (refresh) continues in the loop it paused in
+    const bool fresh = B.p64[i].refresh == 0;
+    const int stage = fresh ? 0 : __ldcg(&ctl->stage);
+    if (B.fp64 || B.p64[i].dense == 1 || stage == 1) {   // the cached operator runs in the FP64 loop
+        const IterParams<double>& P = B.p64[i];
+        if (fresh) init_member(P);
+        if (!grid_sync(&ctl->err)) return false;
+        solve_loop<double>(P, ST_RUNNING);
+    } else {
+        const IterParams<float>& P = B.p32[i];
+        if (fresh) init_member(P);
+        if (!grid_sync(&ctl->err)) return false;
+        if (solve_loop<float>(P, ST_RUNNING) == ST_SWITCH) {
+            // the loop's state is in ctl (written by rank 0): publish it
+            if (!grid_sync(&ctl->err)) return false;
+            solve_loop<double>(B.p64[i], ST_SWITCH);
+        }
+    }
+    // a barrier that timed out leaves the team out of step: stop it
+    return ld_volatile_int(&ctl->err) != ACS_ERR_DEVICE_TIMEOUT;
+}
+
+__device__ __forceinline__ unsigned long long launch_deadline(const BatchArgs& B) {
     __shared__ unsigned long long s_deadline;
     if (threadIdx.x == 0) {
         s_deadline = 0ull;
@@ -118,7 +149,35 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B)
         }
     }
     __syncthreads();
-    const unsigned long long deadline = s_deadline;
+    return s_deadline;
+}
+
+// Two ways to map CTAs to members.  Queued teams (cta_k == NULL): fixed teams
+// of g consecutive CTAs take members from a global counter until none is
+// left (or the time slice is over).  Assigned teams (cta_k != NULL): the host
+// has given every member a team of its own, cta_g[b] consecutive CTAs sized
+// by its work (a launch with fewer members than CTAs), and CTA b works as
+// rank cta_rank[b] on member order[cta_k[b]] (or idles if cta_k[b] < 0).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B) {
+    if (B.cta_k) {
+        const int k = __ldg(B.cta_k + blockIdx.x);
+        if (k < 0) return;
+        const int rank = __ldg(B.cta_rank + blockIdx.x), g = __ldg(B.cta_g + blockIdx.x);
+        const int base = (int)blockIdx.x - rank;
+        team_set(rank, g, B.team_bar + base, B.team_part + (size_t)base * kMaxRed, nullptr, nullptr);
+        sync_init(0u);
+        const unsigned long long deadline = launch_deadline(B);
+        run_member(B, __ldg(B.order + k), nullptr, deadline);
+        return;
+    }
+    const int team = (int)blockIdx.x / B.g, rank = (int)blockIdx.x % B.g;
+    double* scratch = B.dense ? B.dense + (size_t)team * 2 * B.dense_m2 : nullptr;
+    team_set(rank, B.g, B.team_bar + team, B.team_part + (size_t)team * B.g * kMaxRed, scratch,
+             scratch ? scratch + B.dense_m2 : nullptr);
+    sync_init(0u);
+    __shared__ int s_k;
+    const unsigned long long deadline = launch_deadline(B);
     while (true) {
         // the team's rank 0 takes the next member (none once the time slice
         // is over); the barrier publishes it
@@ -129,39 +188,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_kernel(BatchArgs B)
         __syncthreads();
         const int k = s_k;
         if (k >= B.count) return;
-        const int i = __ldg(B.order + k);
-        Control* ctl = B.ctl + i;
-        sync_init(sync_smem().gen);                      // clear a failure of the previous member
-        if (threadIdx.x == 0) {
-            SyncShared& S = sync_smem();
-            // a member with scratch of its own keeps its cached factor across launches
-            S.dM = B.p64[i].dM ? B.p64[i].dM : scratch;
-            S.dX = B.p64[i].dX ? B.p64[i].dX : (scratch ? scratch + B.dense_m2 : nullptr);
-            S.deadline = deadline;
-        }
-        __syncthreads();
-        // a resumed member (refresh) continues in the loop it paused in
-        const bool fresh = B.p64[i].refresh == 0;
-        const int stage = fresh ? 0 : __ldcg(&ctl->stage);
-        int st;
-        if (B.fp64 || B.p64[i].dense == 1 || stage == 1) {   // the cached operator runs in the FP64 loop
-            const IterParams<double>& P = B.p64[i];
-            if (fresh) init_member(P);
-            if (!grid_sync(&ctl->err)) return;
-            st = solve_loop<double>(P, ST_RUNNING);
-        } else {
-            const IterParams<float>& P = B.p32[i];
-            if (fresh) init_member(P);
-            if (!grid_sync(&ctl->err)) return;
-            st = solve_loop<float>(P, ST_RUNNING);
-            if (st == ST_SWITCH) {
-                // the loop's state is in ctl (written by rank 0): publish it
-                if (!grid_sync(&ctl->err)) return;
-                solve_loop<double>(B.p64[i], ST_SWITCH);
-            }
-        }
-        // a barrier that timed out leaves the team out of step: stop it
-        if (ld_volatile_int(&ctl->err) == ACS_ERR_DEVICE_TIMEOUT) return;
+        if (!run_member(B, __ldg(B.order + k), scratch, deadline)) return;
     }
 }
 
