@@ -70,7 +70,7 @@ TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "08b7d34618b7e1fe", "b
 def kernel_source_sha16() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("acs_iter.cu", "acs_internal.cuh"):
+    for f in ("acs_device.cuh", "acs_iter.cu", "acs_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2103_00736_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
