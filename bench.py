@@ -63,8 +63,9 @@ BATCH_MAX_ITER = 5000       # per member; members not solved by then count as un
 
 # DRAM bytes of one launch of the persistent kernel, from one ncu capture
 # (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
-# taken from: reported as null once acs_iter.cu or acs_internal.cuh change.
-TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "08b7d34618b7e1fe", "bytes": 569.34e9}
+# taken from: reported as null once acs_device.cuh, acs_iter.cu or
+# acs_internal.cuh change.
+TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "c1551fb624e445f2", "bytes": 573.44e9}
 
 
 def kernel_source_sha16() -> str:
