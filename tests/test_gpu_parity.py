@@ -350,3 +350,27 @@ def test_cached_operator_drops_dependent_rows():
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
     assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+
+
+@pytest.mark.slow
+def test_socp_full_size():
+    """The SOCP at full size (100000-dim orthant + 20000 Lorentz cones of
+    sizes 3..64, m = 150000, 8 nonzeros per column), SOCP schedule: end
+    result re-evaluated by the oracle's residuals, objective against the
+    planted optimum, and the first iteration's iterate against the oracle's
+    (CG to 1e-13 in FP64) on the whole vector and on sampled coordinates."""
+    inst = I.socp()
+    kw = dict(t=1.7, cond_first=200, cond_period=100)
+    st, x, y, z, iters, res = _solve(inst, tol=5e-7, max_iter=5000, **kw)
+    assert st == capi.SOLVED, (capi.acs_status_string(st), res)
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * (1 + abs(inst.obj_star))
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n_orth, inst.soc_dims, t=1.7,
+                         L=alg.SOCP_SCHEDULE, max_iter=1, tol=0.0, keep_x=1, solver="cg")
+    st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=1, precision=capi.PREC_FP64,
+                                     cg_eta=1e-12, cg_tol=0.0, **kw)
+    xr = ref.x_history[0]
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+    idx = np.random.default_rng(1).choice(inst.n, 1000, replace=False)
+    np.testing.assert_allclose(x[idx], xr[idx], atol=1e-7 * np.abs(xr).max())
