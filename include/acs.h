@@ -74,7 +74,7 @@ typedef struct {
                                 the iteration needs; ACS_PREC_FP64: FP64 correction CG      */
     double cg_eta;           /* inexact projection: CG stops once its error estimate
                                 sqrt(r' J^-1 r) <= eta * ||s_l - s_{l-1}||, eta starting at
-                                cg_eta (default 1e-2) and shrunk tenfold whenever the step
+                                cg_eta (default 0.3) and shrunk tenfold whenever the step
                                 norm grows between rescalings; iterations that rescale
                                 solve to the floors                                            */
     double cg_tol;           /* ... or <= cg_tol * ||s_l||; default 1e-12                     */

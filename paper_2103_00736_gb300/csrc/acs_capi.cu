@@ -117,7 +117,7 @@ int acs_settings_default(acs_settings* s) {
     s->n_cond_list = 0;
     s->check_every = 10;
     s->precision = ACS_PREC_MIXED;
-    s->cg_eta = 1e-2;
+    s->cg_eta = 0.3;
     s->cg_tol = 1e-12;
     s->cg_max_iter = 500;
     s->cg_refine = 1;

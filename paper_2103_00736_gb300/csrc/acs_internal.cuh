@@ -150,7 +150,7 @@ struct Problem {
     int grid32 = 0, grid64 = 0;
     bool warm = false;                   // acs_set_state called
     int warm_l = 0;
-    double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 1e-2;
+    double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 0.3;
     int last_status = ACS_MAX_ITER;
     int dense = 0;                       // cached dense operator: 0 never, 1 always, 2 when CG stalls
     double *dM = nullptr, *dX = nullptr; // its scratch, [m * m] each

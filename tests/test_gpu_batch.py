@@ -4,7 +4,9 @@ launch) through the C ABI, against the FP64 CPU oracle.
 Bars (the same as for a single solve):
   * end results: every member SOLVED; every relative KKT residual <= 1e-6
     when re-evaluated by the oracle's residual function on the returned
-    (x, y, z); objective within 1e-6 relative of the planted optimum;
+    (x, y, z); objective within 1e-6 relative of the planted optimum (solves
+    that check the objective stop at a KKT residual of 2e-7: a residual of
+    1e-6 alone does not bound the objective error by 1e-6);
   * FP64 iterates of members equal the oracle's to 1e-7 relative over the
     first iterations (no rescaling before l = 300 under the LP schedule);
   * a member gives the same answer alone (single-problem launch) and in the
@@ -77,7 +79,7 @@ def _check_member(inst, x, y, z, tol=1e-6):
 @pytest.mark.parametrize("mapping", [(1024, 1), (256, 1), (512, 2), (256, 4)])
 def test_batch_end_results(mixed, mapping):
     with capi.Batch(mixed, mapping=mapping, **LP) as B:
-        rc = B.solve(tol=1e-6, max_iter=20000)
+        rc = B.solve(tol=2e-7, max_iter=20000)
         worst, st, iters, res = B.results()
         assert rc == capi.SOLVED and np.all(st == capi.SOLVED), (st, iters)
         info = capi.acs_batch_info(B.h)
@@ -118,11 +120,11 @@ def test_batch_member_alone_and_in_batch(mixed):
     """The same member solved by the single-problem launch and inside the
     batch: both converge, objectives agree to 1e-6 relative."""
     with capi.Batch(mixed, **LP) as B:
-        assert B.solve(tol=1e-6, max_iter=20000) == capi.SOLVED
+        assert B.solve(tol=2e-7, max_iter=20000) == capi.SOLVED
         for i in (0, 5, 14):
             inst = mixed[i]
             with capi.Solver(inst, **LP) as s:
-                assert s.solve(tol=1e-6, max_iter=20000) == capi.SOLVED
+                assert s.solve(tol=2e-7, max_iter=20000) == capi.SOLVED
                 _, xa, ya, za, _, _ = s.get()
             _, xb, yb, zb, _, _ = B.get(i)
             oa, ob = inst.c @ xa, inst.c @ xb
@@ -149,7 +151,7 @@ def test_batch_socp_members():
     mem = [I.socp(scale=0.002), I.socp(seed=I.seed_for(I.K_SOCP, 7), scale=0.001)]
     mem += [r for r in (I.serve_request(i, mmax=400) for i in range(12)) if r.meta["with_soc"]][:3]
     with capi.Batch(mem, t=1.7, cond_first=200, cond_period=100) as B:
-        rc = B.solve(tol=1e-6, max_iter=20000)
+        rc = B.solve(tol=2e-7, max_iter=20000)
         worst, st, iters, res = B.results()
         assert rc == capi.SOLVED, (st, iters)
         for i, inst in enumerate(mem):
@@ -162,7 +164,7 @@ def test_batch_autotune_picks_a_valid_mapping(mixed):
         (th, g), ms = capi.acs_batch_autotune(B.h, max_iter=20)
         assert th in (256, 512, 1024) and g in (1, 2, 4)
         assert (ms > 0).any() and np.all(ms[ms >= 0] > 0)
-        rc = B.solve(tol=1e-6, max_iter=20000)
+        rc = B.solve(tol=2e-7, max_iter=20000)
         assert rc == capi.SOLVED
         for i in (0, 9, len(mixed) - 1):
             _check_member(mixed[i], *B.get(i)[1:4])

@@ -3,7 +3,10 @@
 Tolerances (stated requirement of the method's hot path):
   * end results: every relative KKT residual <= 1e-6 when re-evaluated by the
     oracle's FP64 residual function on the returned (x, y, z); objective
-    within 1e-6 relative of the oracle's and of the planted optimum;
+    within 1e-6 relative of the oracle's and of the planted optimum.  Where
+    the objective is checked, the solve stops at a KKT residual of 2e-7: a
+    residual of 1e-6 alone does not bound the objective error by 1e-6 (the
+    inexact projections end some solves 1.6e-6 away at 1e-6 residuals);
   * FP32 iterates: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-4 over the first
     50 iterations under the paper's LP schedule (no rescaling before l = 300);
   * FP64 iterates: same comparison <= 1e-7 (the projection solve stops at a
@@ -42,7 +45,7 @@ def _solve(inst, tol=1e-6, max_iter=20000, **kw):
 def test_small_lp_end_result(precision, projection):
     """m = 200: the cached dense operator by default, CG when forced."""
     inst = I.small_lp()
-    st, x, y, z, iters, res = _solve(inst, precision=precision, projection=projection, **LP_SCHED)
+    st, x, y, z, iters, res = _solve(inst, tol=2e-7, precision=precision, projection=projection, **LP_SCHED)
     assert st == capi.SOLVED, capi.acs_status_string(st)
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
@@ -50,7 +53,7 @@ def test_small_lp_end_result(precision, projection):
     for k, key in enumerate(("r_p", "r_d", "r_gap", "r_cone")):
         assert abs(res[k] - ours[key]) <= 1e-9 + 1e-6 * ours[key], (key, res[k], ours[key])
     ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
-                         max_iter=20000, tol=1e-6, check_every=10)
+                         max_iter=20000, tol=2e-7, check_every=10)
     assert abs(ours["obj_p"] - ref.res["obj_p"]) <= 1e-6 * abs(ref.res["obj_p"])
     assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
     # x* is unique here (|supp x*| = 150 < m)
@@ -104,7 +107,7 @@ def test_worked_example(sched, precision, projection):
 @pytest.mark.parametrize("precision", [capi.PREC_MIXED, capi.PREC_FP64])
 def test_small_socp(precision):
     inst = I.socp(scale=0.002)
-    st, x, y, z, iters, res = _solve(inst, precision=precision, t=1.7, cond_first=200,
+    st, x, y, z, iters, res = _solve(inst, tol=2e-7, precision=precision, t=1.7, cond_first=200,
                                      cond_period=100, max_iter=20000)
     assert st == capi.SOLVED, capi.acs_status_string(st)
     ours = _kkt_of(inst, x, y, z)
@@ -321,7 +324,7 @@ def test_rescaling_with_degenerate_o():
         _, O, _, l, _ = capi.acs_get_state(s.h, inst.m, inst.n)
     np.testing.assert_allclose(O, ref.O_history[1][1], rtol=1e-7)
     assert abs(math.log(O.max() / O.min()) - 9.2) <= 1e-9
-    st, x, y, z, iters, res = _solve(inst, tol=1e-6, cond_list=[3], **LP_SCHED)
+    st, x, y, z, iters, res = _solve(inst, tol=2e-7, cond_list=[3], **LP_SCHED)
     assert st == capi.SOLVED
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours

@@ -5,9 +5,10 @@ Bars:
     across rounds, in a changing mix) as solved alone in a batched launch of
     the same mapping: same status and iteration count, iterates equal to
     1e-12 relative (the pause/resume is exact);
-  * against the single-problem launch (another launch shape): both solved,
-    objectives within 1e-6 relative, and every relative KKT residual of the
-    served result <= 1e-6 when re-evaluated by the oracle;
+  * against the single-problem launch (another launch shape): both solved
+    (to a KKT residual of 2e-7, which the objective bar needs), objectives
+    within 1e-6 relative, and every relative KKT residual of the served
+    result <= 1e-6 when re-evaluated by the oracle;
   * admission waits for memory: with a budget that holds a few requests at a
     time every request still finishes; a request that can never fit is
     refused at submission.
@@ -38,12 +39,12 @@ def requests():
     return reqs
 
 
-def _serve(reqs, stagger_s=0.002, **cfg):
+def _serve(reqs, stagger_s=0.002, tol=2e-7, **cfg):
     out = {}
     with capi.Server(**cfg) as S:
         ids = []
         for k, r in enumerate(reqs):
-            ids.append(S.submit(r, tol=1e-6, max_iter=20000))
+            ids.append(S.submit(r, tol=tol, max_iter=20000))
             if stagger_s and k % 3 == 2:
                 time.sleep(stagger_s)           # later ones arrive while earlier ones run
         for k, rid in enumerate(ids):
@@ -53,7 +54,7 @@ def _serve(reqs, stagger_s=0.002, **cfg):
     return out, stats
 
 
-def _alone_in_batches(reqs):
+def _alone_in_batches(reqs, tol=2e-7):
     """Each request solved alone in a batched launch of the serving mapping
     (one launch per cone type, each with that type's schedule)."""
     out = {}
@@ -63,7 +64,7 @@ def _alone_in_batches(reqs):
             continue
         sched = capi.SOCP_SCHEDULE if socp else capi.LP_SCHEDULE
         with capi.Batch([reqs[k] for k in ks], mapping=(256, 1), share=[-1] * len(ks), **sched) as B:
-            B.solve(tol=1e-6, max_iter=20000)
+            B.solve(tol=tol, max_iter=20000)
             for j, k in enumerate(ks):
                 out[k] = B.get(j)
     return out
@@ -111,7 +112,7 @@ def test_served_matches_single_problem_launch(requests):
         assert kkt.max_residual(r) <= 1e-6, (k, r)
         sched = capi.SOCP_SCHEDULE if len(inst.soc_dims) else capi.LP_SCHEDULE
         with capi.Solver(inst, **sched) as s:
-            assert s.solve(tol=1e-6, max_iter=20000) == capi.SOLVED
+            assert s.solve(tol=2e-7, max_iter=20000) == capi.SOLVED
             _, xa, _, _, _, _ = s.get()
         oa = inst.c @ xa
         assert abs(r["obj_p"] - oa) <= 1e-6 * (1 + abs(oa)), (k, r["obj_p"], oa)
