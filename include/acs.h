@@ -98,7 +98,14 @@ typedef struct {
                                 dense_switch_cg iterations per outer iteration over 8 outer
                                 iterations; default 1024, at most 4096                         */
     int32_t dense_switch_cg; /* default 40; 0 disables the switch                               */
+    int32_t a_storage;       /* values of A read by the FP32 correction CG: ACS_STORE_FP32
+                                (default) or ACS_STORE_BF16 (2 bytes a nonzero, rounded to
+                                nearest even; the FP64 passes -- residual of the projection
+                                system, update, KKT -- still read the FP64 values, so the
+                                refinement converges to the same FP64 iterate)                 */
 } acs_settings;
+
+enum { ACS_STORE_FP32 = 0, ACS_STORE_BF16 = 1 };
 
 enum { ACS_PROJ_AUTO = 0, ACS_PROJ_CG = 1, ACS_PROJ_DENSE = 2 };
 

@@ -20,6 +20,7 @@ ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
 ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
 PREC_MIXED, PREC_FP64 = 0, 2
 PROJ_AUTO, PROJ_CG, PROJ_DENSE = 0, 1, 2
+STORE_FP32, STORE_BF16 = 0, 1
 
 _lib = None
 
@@ -44,6 +45,7 @@ class acs_settings(C.Structure):
         ("dense_max_m", C.c_int32),
         ("dense_switch_max_m", C.c_int32),
         ("dense_switch_cg", C.c_int32),
+        ("a_storage", C.c_int32),
     ]
 
 

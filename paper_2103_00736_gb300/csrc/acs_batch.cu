@@ -207,15 +207,9 @@ void layout(Batch* B, Pool& P) {
     const int count = B->count;
     // static region: matrices, then per-member b, c, cone offsets, cond list
     for (Matrix& X : B->mats) {
-        auto put = [&](const host::HostSell& H, DevSell& D) {
-            D.sptr = P.take<int>(H.sptr.size());
-            D.slen = P.take<int>(H.slen.size());
-            D.col = P.take<int>(H.col.size());
-            D.v32 = P.take<float>(H.col.size());
-            D.v64 = P.take<double>(H.col.size());
-        };
-        put(X.H.A, X.dA);
-        put(X.H.AT, X.dAT);
+        const bool bf16 = B->set.a_storage == ACS_STORE_BF16;
+        layout_sell(P, X.H.A, X.dA, bf16);
+        layout_sell(P, X.H.AT, X.dAT, bf16);
     }
     for (Member& M : B->mem) {
         M.db = P.take<double>(M.m);
@@ -391,17 +385,8 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
             return fail(ACS_ERR_OOM, -1);
         }
         for (Matrix& X : B->mats) {
-            auto put = [&](const host::HostSell& H, const DevSell& D) {
-                put_bytes(img, D.sptr, H.sptr.data(), H.sptr.size());
-                put_bytes(img, D.slen, H.slen.data(), H.slen.size());
-                put_bytes(img, D.col, H.col.data(), H.col.size());
-                std::vector<float> f(H.val.size());
-                for (size_t k = 0; k < f.size(); ++k) f[k] = (float)H.val[k];
-                put_bytes(img, D.v32, f.data(), f.size());
-                put_bytes(img, D.v64, H.val.data(), H.val.size());
-            };
-            put(X.H.A, X.dA);
-            put(X.H.AT, X.dAT);
+            image_sell(img, X.H.A, X.dA);
+            image_sell(img, X.H.AT, X.dAT);
         }
         for (Member& M : B->mem) {
             put_bytes(img, M.db, M.b.data(), M.b.size());
@@ -421,8 +406,7 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
     for (Matrix& X : B->mats) {
         auto fin = [&](const host::HostSell& H, const DevSell& D, SellMat& S) {
             S.nrows = H.nrows; S.nslices = H.nslices; S.g = H.g;
-            S.sptr = rebase(D.sptr, base); S.slen = rebase(D.slen, base); S.col = rebase(D.col, base);
-            S.v32 = rebase(D.v32, base); S.v64 = rebase(D.v64, base);
+            rebase_sell(D, base, S);
         };
         fin(X.H.A, X.dA, X.A);
         fin(X.H.AT, X.dAT, X.AT);

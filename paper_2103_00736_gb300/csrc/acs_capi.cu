@@ -43,25 +43,34 @@ int upload(Problem* P, T* dst, const T* src, size_t count) {
     return ACS_SOLVED;
 }
 
+// FP64 values always; for the FP32 correction CG either FP32 values or,
+// with BF16 storage of A, BF16 bit patterns (v32 is then NULL).
 int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     int* sptr = nullptr; int* slen = nullptr; int* col = nullptr;
-    float* v32 = nullptr; double* v64 = nullptr;
+    float* v32 = nullptr; double* v64 = nullptr; unsigned short* v16 = nullptr;
     const size_t tot = H.col.size();
+    const bool bf16 = P->set.a_storage == ACS_STORE_BF16;
     if (dalloc(P, &sptr, H.sptr.size()) || dalloc(P, &slen, H.slen.size()) || dalloc(P, &col, tot) ||
-        dalloc(P, &v32, tot) || dalloc(P, &v64, tot))
+        (bf16 ? dalloc(P, &v16, tot) : dalloc(P, &v32, tot)) || dalloc(P, &v64, tot))
         return ACS_ERR_OOM;
-    std::vector<float> f(tot);
-    for (size_t k = 0; k < tot; ++k) f[k] = (float)H.val[k];
     int rc = 0;
     rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
     rc |= upload(P, slen, H.slen.data(), H.slen.size());
     rc |= upload(P, col, H.col.data(), tot);
-    rc |= upload(P, v32, f.data(), tot);
+    if (bf16) {
+        std::vector<unsigned short> h(tot);
+        for (size_t k = 0; k < tot; ++k) h[k] = acs::host::to_bf16(H.val[k]);
+        rc |= upload(P, v16, h.data(), tot);
+    } else {
+        std::vector<float> f(tot);
+        for (size_t k = 0; k < tot; ++k) f[k] = (float)H.val[k];
+        rc |= upload(P, v32, f.data(), tot);
+    }
     rc |= upload(P, v64, H.val.data(), tot);
     // the pageable source buffers are released when this function returns
     if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
     M.nrows = H.nrows; M.nslices = H.nslices; M.g = H.g;
-    M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64;
+    M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64; M.v16 = v16;
     return ACS_SOLVED;
 }
 
@@ -127,6 +136,7 @@ int acs_settings_default(acs_settings* s) {
     s->dense_max_m = 512;
     s->dense_switch_max_m = 1024;
     s->dense_switch_cg = 40;
+    s->a_storage = ACS_STORE_FP32;
     return ACS_SOLVED;
 }
 

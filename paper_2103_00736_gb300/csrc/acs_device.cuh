@@ -255,6 +255,15 @@ template <typename T> __device__ __forceinline__ const T* sell_vals(const SellMa
 template <> __device__ __forceinline__ const float* sell_vals<float>(const SellMat& M) { return M.v32; }
 template <> __device__ __forceinline__ const double* sell_vals<double>(const SellMat& M) { return M.v64; }
 
+// Stored value -> arithmetic type.  A BF16 value is the upper half of the
+// FP32 value with the same bits, so the conversion is exact.
+__device__ __forceinline__ unsigned short ld_stream(const unsigned short* p) { return __ldcs(p); }
+template <typename T> __device__ __forceinline__ T val_to(T v) { return v; }
+template <typename T> __device__ __forceinline__ T val_to(unsigned short b);
+template <> __device__ __forceinline__ float val_to<float>(unsigned short b) {
+    return __uint_as_float((unsigned)b << 16);
+}
+
 // Layout (see SellMat): a slice holds 32/G rows; chunk c of the slice is 32
 // consecutive entries, entry k of local row r at chunk k/G, lane r*G + k%G.
 // Warp w handles slices w, w + nwarps, ..., in batches of U chunks; each lane
@@ -266,14 +275,14 @@ template <> __device__ __forceinline__ const double* sell_vals<double>(const Sel
 // table entries of the next slice) are issued before the gathers of the
 // current batch, so a warp keeps one matrix round trip and one gather round
 // trip in flight at the same time instead of one after the other.
-template <int U, typename T>
-__device__ __forceinline__ void sell_load_batch(const int* __restrict__ col, const T* __restrict__ val,
+template <int U, typename T, typename V>
+__device__ __forceinline__ void sell_load_batch(const int* __restrict__ col, const V* __restrict__ val,
                                                 int base, int k, int len, int (&c)[U], T (&a)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (k + u < len) {
             c[u] = ld_stream(col + base + 32 * (k + u));
-            a[u] = ld_stream(val + base + 32 * (k + u));
+            a[u] = val_to<T>(ld_stream(val + base + 32 * (k + u)));
         } else {
             c[u] = 0;
             a[u] = T(0);
@@ -281,9 +290,9 @@ __device__ __forceinline__ void sell_load_batch(const int* __restrict__ col, con
     }
 }
 
-template <int G, int U, typename T, typename Gather, typename Epi>
-__device__ __forceinline__ void sell_rows_g(const SellMat& M, Gather gather, Epi epi) {
-    const T* __restrict__ val = sell_vals<T>(M);
+// V: the stored value type (T itself, or BF16 bits for T = float).
+template <int G, int U, typename T, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void sell_rows_g(const SellMat& M, const V* __restrict__ val, Gather gather, Epi epi) {
     const int* __restrict__ col = M.col;
     const int lane = threadIdx.x & 31;
     const int nw = global_warps();
@@ -343,17 +352,33 @@ __device__ __forceinline__ void sell_rows_g(const SellMat& M, Gather gather, Epi
     }
 }
 
+// Chunks per software-pipeline batch: each lane keeps U column/value loads
+// and U gathers in flight.  Measured on the large LP (1e7 nonzeros): U = 4,
+// 8, 12 give 58.9, 57.9, 70.1 us for the CG A pass and 44.8, 46.2, 51.2 us
+// for the A' pass -- the passes are bound by the L2 gather rate, not by the
+// depth of the chain -- so 4 stays; FP64 passes at 8 would spill registers.
+#ifndef ACS_CG_U
+#define ACS_CG_U 4
+#endif
+
+template <typename T, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void sell_rows_v(const SellMat& M, const V* val, Gather gather, Epi epi) {
+    constexpr int U = (sizeof(T) == 4) ? ACS_CG_U : 4;
+    switch (M.g) {
+        case 1: sell_rows_g<1, U, T>(M, val, gather, epi); break;
+        case 2: sell_rows_g<2, U, T>(M, val, gather, epi); break;
+        case 4: sell_rows_g<4, U, T>(M, val, gather, epi); break;
+        case 8: sell_rows_g<8, U, T>(M, val, gather, epi); break;
+        case 16: sell_rows_g<16, U, T>(M, val, gather, epi); break;
+        default: sell_rows_g<32, U, T>(M, val, gather, epi); break;
+    }
+}
+
+// FP32 products read the BF16 copy of the values when A is stored in BF16.
 template <typename T, typename Gather, typename Epi>
 __device__ __forceinline__ void sell_rows(const SellMat& M, Gather gather, Epi epi) {
-    constexpr int U = 4;
-    switch (M.g) {
-        case 1: sell_rows_g<1, U, T>(M, gather, epi); break;
-        case 2: sell_rows_g<2, U, T>(M, gather, epi); break;
-        case 4: sell_rows_g<4, U, T>(M, gather, epi); break;
-        case 8: sell_rows_g<8, U, T>(M, gather, epi); break;
-        case 16: sell_rows_g<16, U, T>(M, gather, epi); break;
-        default: sell_rows_g<32, U, T>(M, gather, epi); break;
-    }
+    if (sizeof(T) == 4 && M.v16 != nullptr) sell_rows_v<T>(M, M.v16, gather, epi);
+    else sell_rows_v<T>(M, sell_vals<T>(M), gather, epi);
 }
 
 // Two sums per row: sum a*g1(j) and sum a*a*g2(j) (FP64 values).

@@ -7,6 +7,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <climits>
@@ -36,7 +37,18 @@ inline bool valid_settings(const acs_settings& set) {
            (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP64) &&
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
            set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit && set.dense_switch_max_m >= 0 &&
-           set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0;
+           set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0 &&
+           (set.a_storage == ACS_STORE_FP32 || set.a_storage == ACS_STORE_BF16);
+}
+
+// BF16 bit pattern of a finite value: the upper 16 bits of its FP32 value,
+// rounded to nearest with ties to even.
+inline unsigned short to_bf16(double v) {
+    const float f = (float)v;
+    unsigned u;
+    memcpy(&u, &f, sizeof(u));
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
 }
 
 // How a problem with m constraints applies the projection: 0 = CG only,

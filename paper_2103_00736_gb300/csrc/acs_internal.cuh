@@ -82,6 +82,7 @@ struct SellMat {
     const int* col;        // [sptr[nslices]]
     const float* v32;
     const double* v64;
+    const unsigned short* v16;   // BF16 bit patterns of the values (BF16 storage of A), else NULL
 };
 
 // Everything one launch of the iteration kernel needs (passed by value).

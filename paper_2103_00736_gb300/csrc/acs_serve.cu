@@ -173,15 +173,9 @@ int salloc(Server* S, T** p, size_t count) {
 void request_layout(Request* R, Pool& P) {
     Matrix& X = R->X;
     Member& M = R->M;
-    auto put = [&](const host::HostSell& H, DevSell& D) {
-        D.sptr = P.take<int>(H.sptr.size());
-        D.slen = P.take<int>(H.slen.size());
-        D.col = P.take<int>(H.col.size());
-        D.v32 = P.take<float>(H.col.size());
-        D.v64 = P.take<double>(H.col.size());
-    };
-    put(X.H.A, X.dA);
-    put(X.H.AT, X.dAT);
+    const bool bf16 = R->set.a_storage == ACS_STORE_BF16;
+    layout_sell(P, X.H.A, X.dA, bf16);
+    layout_sell(P, X.H.AT, X.dAT, bf16);
     M.db = P.take<double>(M.m);
     M.dc = P.take<double>(M.n);
     M.dsoc = P.take<int>(M.n_soc + 1);
@@ -211,17 +205,8 @@ void request_layout(Request* R, Pool& P) {
 // Host image of the static part of the block.
 void request_image(Request* R) {
     R->image.assign(R->static_bytes, 0);
-    auto put = [&](const host::HostSell& H, const DevSell& D) {
-        put_bytes(R->image, D.sptr, H.sptr.data(), H.sptr.size());
-        put_bytes(R->image, D.slen, H.slen.data(), H.slen.size());
-        put_bytes(R->image, D.col, H.col.data(), H.col.size());
-        std::vector<float> f(H.val.size());
-        for (size_t k = 0; k < f.size(); ++k) f[k] = (float)H.val[k];
-        put_bytes(R->image, D.v32, f.data(), f.size());
-        put_bytes(R->image, D.v64, H.val.data(), H.val.size());
-    };
-    put(R->X.H.A, R->X.dA);
-    put(R->X.H.AT, R->X.dAT);
+    image_sell(R->image, R->X.H.A, R->X.dA);
+    image_sell(R->image, R->X.H.AT, R->X.dAT);
     put_bytes(R->image, R->M.db, R->M.b.data(), R->M.b.size());
     put_bytes(R->image, R->M.dc, R->M.c.data(), R->M.c.size());
     put_bytes(R->image, R->M.dsoc, R->M.soc_off.data(), R->M.soc_off.size());
@@ -259,12 +244,8 @@ void admit(Server* S, Request* R) {
     std::vector<char>().swap(R->image);
     // offsets -> device addresses
     // (the shapes were recorded at submission, when the host image was built)
-    auto fin = [&](const DevSell& D, SellMat& Sm) {
-        Sm.sptr = rebase(D.sptr, base); Sm.slen = rebase(D.slen, base); Sm.col = rebase(D.col, base);
-        Sm.v32 = rebase(D.v32, base); Sm.v64 = rebase(D.v64, base);
-    };
-    fin(R->X.dA, R->X.A);
-    fin(R->X.dAT, R->X.AT);
+    rebase_sell(R->X.dA, base, R->X.A);
+    rebase_sell(R->X.dAT, base, R->X.AT);
     Member& M = R->M;
     M.db = rebase(M.db, base); M.dc = rebase(M.dc, base); M.dsoc = rebase(M.dsoc, base);
     M.x = rebase(M.x, base); M.z = rebase(M.z, base); M.ocone = rebase(M.ocone, base);

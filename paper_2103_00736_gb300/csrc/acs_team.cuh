@@ -213,8 +213,48 @@ struct Pool {
 };
 
 struct DevSell {      // offsets of one sliced-ELLPACK matrix inside the pool
-    int* sptr; int* slen; int* col; float* v32; double* v64;
+    int* sptr; int* slen; int* col; float* v32; double* v64; unsigned short* v16;
 };
+
+// Device layout of one matrix: FP64 values, and FP32 values or BF16 bits.
+inline void layout_sell(Pool& P, const host::HostSell& H, DevSell& D, bool bf16) {
+    D.sptr = P.take<int>(H.sptr.size());
+    D.slen = P.take<int>(H.slen.size());
+    D.col = P.take<int>(H.col.size());
+    D.v32 = bf16 ? nullptr : P.take<float>(H.col.size());
+    D.v16 = bf16 ? P.take<unsigned short>(H.col.size()) : nullptr;
+    D.v64 = P.take<double>(H.col.size());
+}
+
+template <typename T>
+void put_bytes(std::vector<char>& img, const void* dev_off, const T* src, size_t count);
+
+// Host image of one matrix at the offsets of layout_sell.
+inline void image_sell(std::vector<char>& img, const host::HostSell& H, const DevSell& D) {
+    put_bytes(img, D.sptr, H.sptr.data(), H.sptr.size());
+    put_bytes(img, D.slen, H.slen.data(), H.slen.size());
+    put_bytes(img, D.col, H.col.data(), H.col.size());
+    if (D.v16) {
+        std::vector<unsigned short> h(H.val.size());
+        for (size_t k = 0; k < h.size(); ++k) h[k] = host::to_bf16(H.val[k]);
+        put_bytes(img, D.v16, h.data(), h.size());
+    } else {
+        std::vector<float> f(H.val.size());
+        for (size_t k = 0; k < f.size(); ++k) f[k] = (float)H.val[k];
+        put_bytes(img, D.v32, f.data(), f.size());
+    }
+    put_bytes(img, D.v64, H.val.data(), H.val.size());
+}
+
+// Device addresses of a matrix laid out at offsets from base.
+template <typename T>
+T* rebase(T* off, char* base);
+inline void rebase_sell(const DevSell& D, char* base, SellMat& S) {
+    S.sptr = rebase(D.sptr, base); S.slen = rebase(D.slen, base); S.col = rebase(D.col, base);
+    S.v32 = D.v32 ? rebase(D.v32, base) : nullptr;
+    S.v16 = D.v16 ? rebase(D.v16, base) : nullptr;
+    S.v64 = rebase(D.v64, base);
+}
 
 struct Matrix {       // one distinct A of the batch
     host::HostProblem H;            // host image (released after upload)

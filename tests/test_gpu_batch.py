@@ -202,3 +202,12 @@ def test_batch_cg_stall_switches_to_cached_operator():
     assert np.all(cnt[:, 0] > 0)                 # every member started with CG
     assert np.any(cnt[:, 7] > 0), cnt            # some switched and factorised
     print("switched:", int(np.sum(cnt[:, 7] > 0)), "of", len(sub))
+
+
+def test_batch_bf16_storage(mixed):
+    """The batched launch with BF16 storage of A (CG projections): same bars."""
+    sub = mixed[:10]
+    with capi.Batch(sub, projection=capi.PROJ_CG, a_storage=capi.STORE_BF16, **LP) as B:
+        assert B.solve(tol=2e-7, max_iter=20000) == capi.SOLVED
+        for i, inst in enumerate(sub):
+            _check_member(inst, *B.get(i)[1:4])

@@ -377,3 +377,37 @@ def test_socp_full_size():
     assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
     idx = np.random.default_rng(1).choice(inst.n, 1000, replace=False)
     np.testing.assert_allclose(x[idx], xr[idx], atol=1e-7 * np.abs(xr).max())
+
+
+def test_bf16_storage_of_A():
+    """BF16 storage of A (the FP32 correction CG reads 2-byte values): the
+    FP64 residual of every refinement round still uses the FP64 values, so
+    the end result meets the same bars.  The first iterates differ from the
+    oracle's by the BF16 model error that one correction leaves (measured
+    below; bound 1e-3 relative against 1e-4 for FP32 storage)."""
+    inst = I.small_lp()
+    kw = dict(projection=capi.PROJ_CG, a_storage=capi.STORE_BF16, **LP_SCHED)
+    st, x, y, z, iters, res = _solve(inst, tol=2e-7, **kw)
+    assert st == capi.SOLVED
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
+                         max_iter=50, tol=0.0, keep_x=50)
+    worst = 0.0
+    for k in (1, 5, 20, 50):
+        st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, cg_eta=1e-9, cg_tol=0.0, **kw)
+        xr = ref.x_history[k - 1]
+        worst = max(worst, np.linalg.norm(x - xr) / np.linalg.norm(xr))
+    print("BF16 storage: worst relative iterate error over 50 iterations", worst)
+    assert worst <= 1e-3
+
+
+@pytest.mark.slow
+def test_bf16_storage_large_lp():
+    inst = I.large_lp()
+    st, x, y, z, iters, res = _solve(inst, tol=4e-7, max_iter=5000, a_storage=capi.STORE_BF16, **LP_SCHED)
+    assert st == capi.SOLVED, (capi.acs_status_string(st), res)
+    ours = _kkt_of(inst, x, y, z)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
