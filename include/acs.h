@@ -98,6 +98,10 @@ typedef struct {
                                 dense_switch_cg iterations per outer iteration over 8 outer
                                 iterations; default 1024, at most 4096                         */
     int32_t dense_switch_cg; /* default 40; 0 disables the switch                               */
+    double extrapolation;    /* start of each projection solve: w + theta (w - w_prev) with
+                                theta = extrapolation (the matching A_hat' w follows without a
+                                matrix pass while O is fixed); 0 starts from the previous w;
+                                default 1                                                      */
     int32_t a_storage;       /* values of A read by the FP32 correction CG: ACS_STORE_FP32
                                 (default) or ACS_STORE_BF16 (2 bytes a nonzero, rounded to
                                 nearest even; the FP64 passes -- residual of the projection

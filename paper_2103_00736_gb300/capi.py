@@ -45,6 +45,7 @@ class acs_settings(C.Structure):
         ("dense_max_m", C.c_int32),
         ("dense_switch_max_m", C.c_int32),
         ("dense_switch_cg", C.c_int32),
+        ("extrapolation", C.c_double),
         ("a_storage", C.c_int32),
     ]
 

@@ -229,6 +229,7 @@ void layout(Batch* B, Pool& P) {
         X.s = P.take<double>(n); X.p = P.take<double>(n); X.g = P.take<double>(n);
         X.q = P.take<double>(n); X.chat = P.take<double>(n); X.O = P.take<double>(n);
         X.w = P.take<double>(m); X.btil = P.take<double>(m);
+        X.wp = P.take<double>(m); X.qp = P.take<double>(n);
         auto inner = [&](auto& V) {
             using T = std::remove_pointer_t<decltype(V.r)>;
             V.r = P.take<T>(m); V.u = P.take<T>(m); V.p = P.take<T>(m); V.sv = P.take<T>(m);
@@ -418,6 +419,8 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         X.s = rebase(X.s, base); X.p = rebase(X.p, base); X.g = rebase(X.g, base); X.q = rebase(X.q, base);
         X.chat = rebase(X.chat, base); X.O = rebase(X.O, base); X.w = rebase(X.w, base);
         X.btil = rebase(X.btil, base);
+        X.wp = rebase(X.wp, base);
+        X.qp = rebase(X.qp, base);
         auto inner = [&](auto& V) {
             V.r = rebase(V.r, base); V.u = rebase(V.u, base); V.p = rebase(V.p, base); V.sv = rebase(V.sv, base);
             V.au = rebase(V.au, base); V.jinv = rebase(V.jinv, base); V.t = rebase(V.t, base);

@@ -94,6 +94,7 @@ int alloc_outer(Problem* P, acs::Outer& X) {
     rc |= dalloc(P, &X.s, n); rc |= dalloc(P, &X.p, n); rc |= dalloc(P, &X.g, n);
     rc |= dalloc(P, &X.q, n); rc |= dalloc(P, &X.w, m); rc |= dalloc(P, &X.chat, n);
     rc |= dalloc(P, &X.btil, m); rc |= dalloc(P, &X.O, n);
+    rc |= dalloc(P, &X.wp, m); rc |= dalloc(P, &X.qp, n);
     return rc ? ACS_ERR_OOM : ACS_SOLVED;
 }
 
@@ -137,6 +138,7 @@ int acs_settings_default(acs_settings* s) {
     s->dense_switch_max_m = 1024;
     s->dense_switch_cg = 40;
     s->a_storage = ACS_STORE_FP32;
+    s->extrapolation = 1.0;
     return ACS_SOLVED;
 }
 

@@ -549,17 +549,41 @@ __device__ __noinline__ void phase_btilde(const IterParams<T>& P) {
     block_partials<1>(v, op, P.partials);
 }
 
-// Step 17: p = abs_K(s); g = O (p + q) for the warm-started right-hand side.
+// Start of the projection solve: w <- w + theta (w - w_prev) and, since
+// q = A_hat' w is linear in w while O is fixed, q <- q + theta (q - q_prev)
+// exactly, with no matrix pass (theta = 0: the previous w, a plain warm
+// start).  The outer iteration converges linearly, so consecutive w follow a
+// near-geometric sequence and the extrapolated start leaves the correction
+// solve a smaller residual.  Returns the q to use; saves the current pair.
+__device__ __forceinline__ double extrap_q(const Outer& X, int j, double theta) {
+    const double q = X.q[j];
+    if (theta == 0.0) {
+        X.qp[j] = q;
+        return q;
+    }
+    const double qn = fma(theta, q - X.qp[j], q);
+    X.qp[j] = q;
+    X.q[j] = qn;
+    return qn;
+}
+
+// Step 17: p = abs_K(s); g = O (p + q) for the warm-started right-hand side
+// (theta: see extrap_q).
 // Lorentz cone (v1, vbar), t = ||vbar||: inside (t <= v1) abs = v; polar
 // (t <= -v1) abs = -v; otherwise abs = (t, (v1/t) vbar), which is 2 proj - v
 // for proj = ((v1 + t)/2)(1, vbar/t).
 template <typename T>
-__device__ __noinline__ void phase_abs(const IterParams<T>& P) {
+__device__ __noinline__ void phase_abs(const IterParams<T>& P, double theta) {
     const Outer& X = P.X;
+    for (int i = global_tid(); i < P.m; i += global_threads()) {
+        const double w = X.w[i];
+        if (theta != 0.0) X.w[i] = fma(theta, w - X.wp[i], w);
+        X.wp[i] = w;
+    }
     for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
         const double pj = fabs(X.s[j]);
         X.p[j] = pj;
-        X.g[j] = X.O[j] * (pj + X.q[j]);
+        X.g[j] = X.O[j] * (pj + extrap_q(X, j, theta));
     }
     const int lane = threadIdx.x & 31;
     for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
@@ -577,7 +601,7 @@ __device__ __noinline__ void phase_abs(const IterParams<T>& P) {
         for (int j = a + lane; j < e; j += 32) {
             const double pj = (j == a) ? head : ftail * X.s[j];
             X.p[j] = pj;
-            X.g[j] = Oc * (pj + X.q[j]);
+            X.g[j] = Oc * (pj + extrap_q(X, j, theta));
         }
     }
 }
@@ -950,6 +974,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     // (O changes only at rescalings, which refactor)
     bool factor_kept = P.own_scratch != 0 && __ldcg(&ctl->dense_on) != 0;
     bool over = false;                                  // deadline of a time-sliced solve passed
+    bool extrap_ok = __ldcg(&ctl->extrap_ok) != 0;
     long long win_cg = __ldcg(&ctl->win_cg);
     int win_it = __ldcg(&ctl->win_it);
     long long ndense = 0, nfactor = 0;
@@ -1034,8 +1059,11 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             refresh = false;
         }
 
-        phase_abs(P);                                           // step 17
+        // extrapolated start, valid once the previous iteration ran in the
+        // same scaling (not on an iteration that rescales)
+        phase_abs(P, (extrap_ok && !cond) ? P.extrap : 0.0);   // step 17
         ACS_SYNC(PH_ABS);
+        extrap_ok = true;
         // Projection solve: `refine` rounds of (FP64 residual, correction CG in
         // precision T); a round after the first refreshes q = A_hat' w first.
         bool trouble = false;                                   // FP32 solve cannot keep up
@@ -1189,6 +1217,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ctl->dense_failed = dense_failed ? 1 : 0;
         ctl->win_cg = win_cg;
         ctl->win_it = win_it;
+        ctl->extrap_ok = extrap_ok ? 1 : 0;
         ctl->bar_gen = sync_smem().gen;
         for (int i = 0; i < PH_COUNT; ++i) {
             ctl->phase_ns[i] += s_ph_ns[i];

@@ -38,7 +38,8 @@ inline bool valid_settings(const acs_settings& set) {
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
            set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit && set.dense_switch_max_m >= 0 &&
            set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0 &&
-           (set.a_storage == ACS_STORE_FP32 || set.a_storage == ACS_STORE_BF16);
+           (set.a_storage == ACS_STORE_FP32 || set.a_storage == ACS_STORE_BF16) &&
+           set.extrapolation >= 0 && set.extrapolation <= 2;
 }
 
 // BF16 bit pattern of a finite value: the upper 16 bits of its FP32 value,

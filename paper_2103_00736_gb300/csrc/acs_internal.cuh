@@ -52,6 +52,8 @@ struct Control {
     int dense_failed;     // its factorisation failed for this solve
     int win_it;           // outer iterations in the current CG-stall window
     long long win_cg;     // CG iterations in that window
+    int extrap_ok;        // wp, qp hold the previous iteration's w, q in the current scaling
+    int pad3;
     unsigned bar_count, bar_gen;
     unsigned long long bar_count64;   // monotonic barrier arrival counter of the current solve
     // nanoseconds spent in each phase (from one barrier exit to the next, as
@@ -63,6 +65,7 @@ struct Control {
 // Outer iteration state, always FP64 (Algorithm 2 in the scaled space).
 struct Outer {
     double *s, *p, *g, *q, *w, *chat, *btil, *O;
+    double *wp, *qp;      // w and q = A_hat' w of the previous iteration (extrapolated start)
 };
 // Inner projection-solve (CG) state in precision T (Chronopoulos-Gear CG:
 // r residual, u = J^{-1} r, p direction, sv = M p, au = M u, t = O^2 A' u).
@@ -118,6 +121,8 @@ struct IterParams {
     double* dM; double* dX;                           // its scratch: single-problem launch, or a member
                                                       // that keeps its own (NULL: the team's)
     int own_scratch;                                  // dM/dX belong to this problem and outlive a launch
+    double extrap;                                    // factor of the extrapolated start of the projection
+                                                      // solve (0 = start from the previous w)
 };
 
 struct Problem {

@@ -118,6 +118,7 @@ __global__ void reset_control(Control* ctl, int l, double ds, double snorm, doub
     ctl->dense_failed = 0;
     ctl->win_it = 0;
     ctl->win_cg = 0;
+    ctl->extrap_ok = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -152,6 +153,7 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.switch_ok = P->set.precision == ACS_PREC_MIXED ? 1 : 0;
     Q.dense = P->dense;
     Q.dense_switch_cg = P->set.dense_switch_cg;
+    Q.extrap = P->set.extrapolation;
     Q.dM = P->dM;
     Q.dX = P->dX;
     return Q;

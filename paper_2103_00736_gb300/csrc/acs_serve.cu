@@ -188,6 +188,7 @@ void request_layout(Request* R, Pool& P) {
     O.s = P.take<double>(n); O.p = P.take<double>(n); O.g = P.take<double>(n);
     O.q = P.take<double>(n); O.chat = P.take<double>(n); O.O = P.take<double>(n);
     O.w = P.take<double>(m); O.btil = P.take<double>(m);
+    O.wp = P.take<double>(m); O.qp = P.take<double>(n);
     auto inner = [&](auto& V) {
         using T = std::remove_pointer_t<decltype(V.r)>;
         V.r = P.take<T>(m); V.u = P.take<T>(m); V.p = P.take<T>(m); V.sv = P.take<T>(m);
@@ -252,6 +253,7 @@ void admit(Server* S, Request* R) {
     Outer& O = M.X;
     O.s = rebase(O.s, base); O.p = rebase(O.p, base); O.g = rebase(O.g, base); O.q = rebase(O.q, base);
     O.chat = rebase(O.chat, base); O.O = rebase(O.O, base); O.w = rebase(O.w, base); O.btil = rebase(O.btil, base);
+    O.wp = rebase(O.wp, base); O.qp = rebase(O.qp, base);
     auto inner = [&](auto& V) {
         V.r = rebase(V.r, base); V.u = rebase(V.u, base); V.p = rebase(V.p, base); V.sv = rebase(V.sv, base);
         V.au = rebase(V.au, base); V.jinv = rebase(V.jinv, base); V.t = rebase(V.t, base); V.O2 = rebase(V.O2, base);

@@ -68,6 +68,7 @@ __global__ void batch_reset(BatchArgs B, double eta0) {
         c->dense_failed = 0;
         c->win_it = 0;
         c->win_cg = 0;
+        c->extrap_ok = 0;
     }
     if (t == 0) *B.head = 0;
 }
@@ -335,6 +336,7 @@ IterParams<T> member_params(const acs_settings& set, const int* d_cond_list, int
     Q.switch_ok = set.precision == ACS_PREC_MIXED ? 1 : 0;
     Q.dense = M.dense;
     Q.dense_switch_cg = set.dense_switch_cg;
+    Q.extrap = set.extrapolation;
     Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
     return Q;
 }
