@@ -138,7 +138,7 @@ int acs_settings_default(acs_settings* s) {
     s->dense_switch_max_m = 1024;
     s->dense_switch_cg = 40;
     s->a_storage = ACS_STORE_FP32;
-    s->extrapolation = 1.0;
+    s->extrapolation = 0.0;
     return ACS_SOLVED;
 }
 
