@@ -225,6 +225,24 @@ def oracle_solves_per_s(sample: dict, workload: str) -> tuple[float, str]:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(x: float, pg=None, device: str = "cpu") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's);
+    x itself without a process group.  device: "cuda" under NCCL, "cpu"
+    under gloo."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -293,11 +311,8 @@ def gpu_arm(args) -> None:
     st, iters, res = capi.acs_get_residuals(h)
     if st != expect:
         raise RuntimeError(f"timed solve did not converge: {capi.acs_status_string(st)}")
-    if pg:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, pg, "cuda")
+    value = replica_throughput(world, args.steps, elapsed_ms / 1e3)
 
     # roofline of the persistent iteration kernel (the only kernel of a solve
     # besides three tiny initialisation launches)
@@ -330,11 +345,8 @@ def gpu_arm(args) -> None:
         h2d = 16 * (pa + pat) + 8 * (inst.m + inst.n) + 4 * (len(inst.soc_dims) + 1)
         h2d += 4 * ((inst.m + inst.n) // 8 + 4)          # slice tables (upper bound)
         d2h = 8 * (2 * inst.n + inst.m) + 256
-        if pg:
-            t = torch.tensor([t_e2e], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(t_e2e, pg, "cuda")
+        e2e = {"value": replica_throughput(world, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     capi.acs_problem_destroy(h)
 

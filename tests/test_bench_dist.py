@@ -1,0 +1,61 @@
+"""The multi-GPU path of the benchmark on CPU: replicas under a process
+group of two gloo ranks (127.0.0.1).  The only collective is the maximum of
+the timed region over ranks; the whole-job throughput is the units of all
+ranks over that maximum."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, l = bench.dist_info()
+    local_ms = 100.0 + 50.0 * rank                      # rank 1 is the slow one
+    m = bench.max_over_ranks(local_ms, dist, "cpu")
+    v = bench.replica_throughput(w, 3, m / 1e3)
+    dist.barrier()
+    out.put((r, w, l, m, v))
+    dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank():
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, (r, w, l, m, v) in enumerate(res):
+        assert (r, w, l) == (rank, world, rank)
+        assert m == 150.0                               # both ranks see the maximum
+        assert abs(v - world * 3 / 0.150) < 1e-9        # 40 solves/s for the job
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5) == 12.5
+    assert bench.replica_throughput(1, 5, 2.0) == 2.5
