@@ -414,7 +414,12 @@ def batch_arm(args) -> None:
     t_create = time.perf_counter() - t0
     info0 = capi.acs_batch_info(h)
     tol, max_iter = args.tol, args.batch_max_iter
-    (th, team), tune_ms = capi.acs_batch_autotune(h, max_iter=args.autotune_iters)
+    if args.autotune_iters > 0:
+        (th, team), tune_ms = capi.acs_batch_autotune(h, max_iter=args.autotune_iters)
+    else:                                        # a fixed mapping (profiling runs)
+        th, team = (int(v) for v in args.mapping.split("x"))
+        capi.acs_batch_set_mapping(h, th, team)
+        tune_ms = np.zeros((3, 3))
     for _ in range(args.warmup):
         capi.acs_batch_solve_async(h, tol, max_iter)
     capi.acs_batch_results(h, len(mem))
@@ -452,7 +457,7 @@ def batch_arm(args) -> None:
     # plain form: the single-problem API on a size-stratified sample, one
     # solve after another, extrapolated to the whole batch
     order = np.argsort([x.nnz for x in mem])
-    sample = order[np.linspace(0, len(mem) - 1, args.plain_sample).astype(int)]
+    sample = order[np.linspace(0, len(mem) - 1, args.plain_sample).astype(int)] if args.plain_sample > 0 else []
     plain_ms, plain_solved = [], 0
     for i in sample:
         x = mem[i]
@@ -468,8 +473,11 @@ def batch_arm(args) -> None:
         plain_ms.append(a.elapsed_time(b2))
         plain_solved += capi.acs_get_residuals(hs)[0] == capi.SOLVED
         capi.acs_problem_destroy(hs)
-    plain_total_ms = float(np.mean(plain_ms)) * len(mem)
-    plain_value = (plain_solved / len(sample)) * len(mem) / (plain_total_ms / 1e3)
+    if len(sample):
+        plain_total_ms = float(np.mean(plain_ms)) * len(mem)
+        plain_value = (plain_solved / len(sample)) * len(mem) / (plain_total_ms / 1e3)
+    else:
+        plain_ms, plain_value = [0.0], 0.0
 
     # end to end through the C ABI with host buffers: create (host preparation
     # and upload), solve, read back every member's x, y, s
@@ -663,7 +671,9 @@ def main():
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-max-iter", type=int, default=BATCH_MAX_ITER)
-    ap.add_argument("--autotune-iters", type=int, default=20)
+    ap.add_argument("--autotune-iters", type=int, default=20,
+                    help="truncated-solve length of each autotuner trial; 0 = use --mapping")
+    ap.add_argument("--mapping", default="512x1", help="threads per CTA x CTAs per team (no autotuning)")
     ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--serve-distinct", type=int, default=48)
     ap.add_argument("--serve-requests", type=int, default=96)
