@@ -847,13 +847,23 @@ __device__ __noinline__ void phase_dense_assemble(const IterParams<T>& P) {
 // is zero.  For a consistent right-hand side (b in range(A)) this solves the
 // remaining independent equations, which imply the dropped one.  Returns
 // false only for a pivot that is negative beyond rounding or not a number.
+constexpr int kColStage = 2048;   // column entries of a Cholesky step staged in shared memory
+
 template <typename T>
 __device__ __forceinline__ bool dense_chol_step(double* M, int m, int k, const T* jinv) {
+    // column k (rows k..m-1), read once per CTA into shared memory: every
+    // row's update needs it, and in row-major storage it is strided
+    __shared__ double colk[kColStage];
+    const bool staged = m <= kColStage;
     const int lane = threadIdx.x & 31;
     const double s = (k > 0) ? 1.0 / sqrt(__ldcg(M + (size_t)(k - 1) * m + (k - 1))) : 0.0;
+    if (staged && k < m) {
+        for (int j = k + (int)threadIdx.x; j < m; j += (int)blockDim.x) colk[j] = __ldcg(M + (size_t)j * m + k);
+        __syncthreads();
+    }
     double inv = 0.0;
     if (k < m) {
-        const double d = __ldcg(M + (size_t)k * m + k);
+        const double d = staged ? colk[k] : __ldcg(M + (size_t)k * m + k);
         const double tau = 1e-13 / (double)__ldcg(jinv + k);
         if (d != d || d < -1e3 * tau) return false;
         const bool dep = !(d > tau) || d == INFINITY;
@@ -863,11 +873,15 @@ __device__ __forceinline__ bool dense_chol_step(double* M, int m, int k, const T
     for (int i = global_warp(); i < m; i += global_warps()) {
         double* Mi = M + (size_t)i * m;
         if (k < i && k < m && inv != 0.0) {
-            const double f = __ldcg(Mi + k) * inv;
-            for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, __ldcg(M + (size_t)j * m + k), Mi[j]);
+            const double f = (staged ? colk[i] : __ldcg(Mi + k)) * inv;
+            if (staged)
+                for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, colk[j], Mi[j]);
+            else
+                for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, __ldcg(M + (size_t)j * m + k), Mi[j]);
         }
         if (k > 0 && i >= k && lane == 0) Mi[k - 1] *= s;
     }
+    if (staged) __syncthreads();      // colk is rewritten at the next step
     return true;
 }
 
@@ -902,9 +916,17 @@ __device__ __noinline__ void phase_dense_y(const IterParams<T>& P) {
     const int m = P.m;
     const T* r = P.V.r;
     for (int i = global_tid(); i < m; i += global_threads()) {
-        double acc = 0.0;
-        for (int c = 0; c <= i; ++c) acc = fma(__ldcg(X + (size_t)c * m + i), (double)__ldcg(r + c), acc);
-        P.V.p[i] = (T)acc;
+        // four independent partial sums keep four loads of X in flight
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 3 <= i; c += 4) {
+            a0 = fma(__ldcg(X + (size_t)c * m + i), (double)__ldcg(r + c), a0);
+            a1 = fma(__ldcg(X + (size_t)(c + 1) * m + i), (double)__ldcg(r + c + 1), a1);
+            a2 = fma(__ldcg(X + (size_t)(c + 2) * m + i), (double)__ldcg(r + c + 2), a2);
+            a3 = fma(__ldcg(X + (size_t)(c + 3) * m + i), (double)__ldcg(r + c + 3), a3);
+        }
+        for (; c <= i; ++c) a0 = fma(__ldcg(X + (size_t)c * m + i), (double)__ldcg(r + c), a0);
+        P.V.p[i] = (T)((a0 + a1) + (a2 + a3));
     }
 }
 
@@ -917,9 +939,14 @@ __device__ __noinline__ void phase_dense_x(const IterParams<T>& P) {
     const T* y = P.V.p;
     for (int c = global_warp(); c < m; c += global_warps()) {
         const double* Xc = X + (size_t)c * m;
-        double acc = 0.0;
-        for (int i = c + lane; i < m; i += 32) acc = fma(__ldcg(Xc + i), (double)__ldcg(y + i), acc);
-        acc = warp_sum(acc);
+        double a0 = 0.0, a1 = 0.0;
+        int i = c + lane;
+        for (; i + 32 < m; i += 64) {
+            a0 = fma(__ldcg(Xc + i), (double)__ldcg(y + i), a0);
+            a1 = fma(__ldcg(Xc + i + 32), (double)__ldcg(y + i + 32), a1);
+        }
+        if (i < m) a0 = fma(__ldcg(Xc + i), (double)__ldcg(y + i), a0);
+        const double acc = warp_sum(a0 + a1);
         if (lane == 0) P.X.w[c] += acc;
     }
 }
