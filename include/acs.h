@@ -334,6 +334,11 @@ int acs_batch_counters(acs_batch* b, long long* out);
  * took: ms[count].  Waits for queued work. */
 int acs_batch_member_ms(acs_batch* b, double* ms);
 
+/* Per-phase device times (ms) and counts of member i's last solve, or summed
+ * over all members for i = -1, in the order of acs_debug_phase_times; n >= 13.
+ * Returns the number of phases written or an error. */
+int acs_batch_phase_ms(acs_batch* b, int32_t i, double* ms, long long* count, int32_t n);
+
 void acs_batch_destroy(acs_batch* b);
 
 /* ------------------------------------------------------------------------

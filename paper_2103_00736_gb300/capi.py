@@ -121,6 +121,7 @@ def lib():
         L.acs_batch_info.argtypes = [P, llp, llp]
         L.acs_batch_counters.argtypes = [P, llp]
         L.acs_batch_member_ms.argtypes = [P, dp]
+        L.acs_batch_phase_ms.argtypes = [P, C.c_int32, dp, C.POINTER(C.c_longlong), C.c_int32]
         L.acs_batch_destroy.argtypes = [P]
         L.acs_server_config_default.argtypes = [C.POINTER(acs_server_config)]
         L.acs_server_create.argtypes = [C.POINTER(acs_settings), C.POINTER(acs_server_config), C.POINTER(P)]
@@ -468,6 +469,17 @@ def acs_batch_member_ms(h, count: int) -> np.ndarray:
     if rc != 0:
         raise AcsError(rc, "acs_batch_member_ms")
     return ms
+
+
+def acs_batch_phase_ms(h, i: int = -1) -> dict:
+    """{phase: (ms, count)} of member i's last solve, or summed over members (i = -1)."""
+    ms = np.zeros(16)
+    cnt = np.zeros(16, dtype=np.int64)
+    rc = lib().acs_batch_phase_ms(C.c_void_p(h), int(i), _ptr(ms, C.c_double),
+                                  cnt.ctypes.data_as(C.POINTER(C.c_longlong)), 16)
+    if rc < 0:
+        raise AcsError(rc, "acs_batch_phase_ms")
+    return {k: (float(ms[j]), int(cnt[j])) for j, k in enumerate(PHASES)}
 
 
 def acs_batch_destroy(h) -> None:

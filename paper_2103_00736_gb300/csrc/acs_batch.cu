@@ -623,6 +623,23 @@ int acs_batch_member_ms(acs_batch* h, double* ms) {
     return ACS_SOLVED;
 }
 
+int acs_batch_phase_ms(acs_batch* h, int32_t i, double* ms, long long* count, int32_t n) {
+    Batch* B = reinterpret_cast<Batch*>(h);
+    if (!B || !ms || !count || n < acs::PH_COUNT || i < -1 || i >= B->count) return ACS_ERR_ARG;
+    if (cudaSetDevice(B->device) != cudaSuccess) return ACS_ERR_CUDA;
+    if (acs::fetch_controls(B) != ACS_SOLVED) return ACS_ERR_CUDA;
+    for (int k = 0; k < acs::PH_COUNT; ++k) {
+        ms[k] = 0.0;
+        count[k] = 0;
+    }
+    for (int j = (i < 0 ? 0 : i); j < (i < 0 ? B->count : i + 1); ++j)
+        for (int k = 0; k < acs::PH_COUNT; ++k) {
+            ms[k] += (double)B->ctl_host[j].phase_ns[k] * 1e-6;
+            count[k] += (long long)B->ctl_host[j].phase_n[k];
+        }
+    return acs::PH_COUNT;
+}
+
 void acs_batch_destroy(acs_batch* h) {
     Batch* B = reinterpret_cast<Batch*>(h);
     if (!B) return;
