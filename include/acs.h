@@ -94,9 +94,10 @@ typedef struct {
     int32_t dense_max_m;     /* largest m for the cached operator from the first iteration
                                 under ACS_PROJ_AUTO; default 512, at most 4096                 */
     int32_t dense_switch_max_m; /* ACS_PROJ_AUTO, dense_max_m < m <= this: start with CG and
-                                switch to the cached operator when CG averages more than
-                                dense_switch_cg iterations per outer iteration over 8 outer
-                                iterations; default 1024, at most 4096                         */
+                                switch to the cached operator once the CG iterations since the
+                                last rescaling exceed the cost of one factorisation counted in
+                                CG iterations (0.3 m^3 / nonzeros, measured on the GB300), and
+                                at least 8 * dense_switch_cg; default 1024, at most 4096      */
     int32_t dense_switch_cg; /* default 40; 0 disables the switch                               */
     double extrapolation;    /* start of each projection solve: w + theta (w - w_prev) with
                                 theta = extrapolation (the matching A_hat' w follows without a

@@ -987,11 +987,14 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     bool ok = true;
     // cached projection operator (FP64 loops only); a factorisation that fails
     // (M singular: rank-deficient A) hands this solve to the CG projection
-    // P.dense == 2: start with CG and switch to the cached operator once CG
-    // averages more than P.dense_switch_cg iterations per outer iteration over
-    // a window of 8 outer iterations (an M too ill-conditioned for Jacobi-CG).
-    // An FP32 loop hands over to the FP64 loop for that; an FP64 loop that
-    // takes over this way factors at once.
+    // P.dense == 2: start with CG and switch to the cached operator once the
+    // CG iterations since the last rescaling exceed P.switch_budget, the cost
+    // of one factorisation counted in CG iterations (rent until the price of
+    // buying is spent): a member that finishes soon after a rescaling never
+    // pays for a factorisation, one whose M is too ill-conditioned for
+    // Jacobi-CG pays at most twice the better of the two.  An FP32 loop hands
+    // over to the FP64 loop for that; an FP64 loop that takes over this way
+    // factors at once.
     const bool have_scratch = sync_smem().dM != nullptr;
     bool dense = sizeof(T) == 8 && have_scratch &&
                  (P.dense == 1 || (P.dense == 2 && (status0 == ST_SWITCH || __ldcg(&ctl->dense_on) != 0)));
@@ -1022,14 +1025,14 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         if (l >= P.max_iter) { status = ACS_MAX_ITER; break; }
         const int lnext = l + 1;
         const bool cond = (lnext == 1) || in_schedule(P, lnext);
-        if (may_switch && !dense && !dense_failed && win_it >= 8) {
-            if (win_cg > (long long)P.dense_switch_cg * win_it) {
-                if (sizeof(T) == 4) { status = ST_SWITCH; break; }
-                dense = true;
-                refresh = true;                                 // factor at this iteration
-            }
+        if (cond) {                                     // a new scaling: a new rental
             win_cg = 0;
             win_it = 0;
+        }
+        if (may_switch && !dense && !dense_failed && win_cg > P.switch_budget) {
+            if (sizeof(T) == 4) { status = ST_SWITCH; break; }
+            dense = true;
+            refresh = true;                                     // factor at this iteration
         }
         if (cond) {                                             // steps 5-14
             phase_cond_o(P);

@@ -52,6 +52,16 @@ inline unsigned short to_bf16(double v) {
     return (unsigned short)(u >> 16);
 }
 
+// CG iterations after a rescaling that cost about one factorisation of the
+// cached operator ((2/3) m^3 FP64 flops against 2 sparse passes over nnz
+// stored entries per CG iteration; the factor 0.3 is measured on this GPU:
+// one factorisation of an m = 1000, 5e4-nonzero M costs ~5700 CG iterations),
+// and at least 8 * dense_switch_cg.
+inline long long switch_budget(const acs_settings& set, int m, long long nnz) {
+    const double f = 0.3 * (double)m * (double)m * (double)m / (double)(nnz > 0 ? nnz : 1);
+    return std::max((long long)8 * set.dense_switch_cg, (long long)f);
+}
+
 // How a problem with m constraints applies the projection: 0 = CG only,
 // 1 = the cached dense operator from the first iteration, 2 = CG, switching
 // to the cached operator if CG stalls.

@@ -50,8 +50,8 @@ struct Control {
     int stage;            // loop that runs the solve: 0 = FP32 correction CG, 1 = FP64 loop
     int dense_on;         // the cached dense operator is in use (kept across pauses)
     int dense_failed;     // its factorisation failed for this solve
-    int win_it;           // outer iterations in the current CG-stall window
-    long long win_cg;     // CG iterations in that window
+    int win_it;           // outer iterations since the last rescaling
+    long long win_cg;     // CG iterations since the last rescaling (switch to the cached operator)
     int extrap_ok;        // wp, qp hold the previous iteration's w, q in the current scaling
     int pad3;
     unsigned bar_count, bar_gen;
@@ -117,7 +117,7 @@ struct IterParams {
     int switch_ok;                                    // FP32 launch may hand over to FP64
     int dense;                                        // cached dense projection operator (FP64 loop):
                                                       // 0 = never, 1 = from the start, 2 = when CG stalls
-    int dense_switch_cg;                              // CG iterations per outer iteration that switch
+    long long switch_budget;                          // CG iterations since the last rescaling that switch
     double* dM; double* dX;                           // its scratch: single-problem launch, or a member
                                                       // that keeps its own (NULL: the team's)
     int own_scratch;                                  // dM/dX belong to this problem and outlive a launch

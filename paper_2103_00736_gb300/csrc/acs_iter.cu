@@ -35,6 +35,7 @@
 // vanishes as the iteration converges (a relative inexactness rule).
 
 #include "acs_device.cuh"
+#include "acs_host.cuh"
 
 namespace acs {
 
@@ -152,7 +153,7 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.refine = P->set.cg_refine > 0 ? P->set.cg_refine : 1;
     Q.switch_ok = P->set.precision == ACS_PREC_MIXED ? 1 : 0;
     Q.dense = P->dense;
-    Q.dense_switch_cg = P->set.dense_switch_cg;
+    Q.switch_budget = acs::host::switch_budget(P->set, P->m, P->padded_A);
     Q.extrap = P->set.extrapolation;
     Q.dM = P->dM;
     Q.dX = P->dX;

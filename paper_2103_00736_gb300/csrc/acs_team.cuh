@@ -335,7 +335,7 @@ IterParams<T> member_params(const acs_settings& set, const int* d_cond_list, int
     Q.refine = set.cg_refine > 0 ? set.cg_refine : 1;
     Q.switch_ok = set.precision == ACS_PREC_MIXED ? 1 : 0;
     Q.dense = M.dense;
-    Q.dense_switch_cg = set.dense_switch_cg;
+    Q.switch_budget = host::switch_budget(set, M.m, M.nnz);
     Q.extrap = set.extrapolation;
     Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
     return Q;
