@@ -993,16 +993,19 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     // buying is spent): a member that finishes soon after a rescaling never
     // pays for a factorisation, one whose M is too ill-conditioned for
     // Jacobi-CG pays at most twice the better of the two.  An FP32 loop hands
-    // over to the FP64 loop for that; an FP64 loop that takes over this way
-    // factors at once.
+    // over to the FP64 loop for that, marking the switch in ctl->dense_on; a
+    // hand-over for FP32 precision alone continues with FP64 CG under the
+    // same rule.
     const bool have_scratch = sync_smem().dM != nullptr;
     bool dense = sizeof(T) == 8 && have_scratch &&
-                 (P.dense == 1 || (P.dense == 2 && (status0 == ST_SWITCH || __ldcg(&ctl->dense_on) != 0)));
+                 (P.dense == 1 || (P.dense == 2 && __ldcg(&ctl->dense_on) != 0));
+    bool want_dense = false;                            // FP32 loop: hand over for the switch
     const bool may_switch = P.dense == 2 && (sizeof(T) == 4 ? P.switch_ok != 0 : have_scratch);
     bool dense_failed = __ldcg(&ctl->dense_failed) != 0;
     // a factor held in the problem's own scratch stays valid across a pause
     // (O changes only at rescalings, which refactor)
-    bool factor_kept = P.own_scratch != 0 && __ldcg(&ctl->dense_on) != 0;
+    bool factor_ok = __ldcg(&ctl->factor_ok) != 0;
+    bool factor_kept = P.own_scratch != 0 && factor_ok;
     bool over = false;                                  // deadline of a time-sliced solve passed
     bool extrap_ok = __ldcg(&ctl->extrap_ok) != 0;
     long long win_cg = __ldcg(&ctl->win_cg);
@@ -1030,7 +1033,11 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             win_it = 0;
         }
         if (may_switch && !dense && !dense_failed && win_cg > P.switch_budget) {
-            if (sizeof(T) == 4) { status = ST_SWITCH; break; }
+            if (sizeof(T) == 4) {
+                want_dense = true;
+                status = ST_SWITCH;
+                break;
+            }
             dense = true;
             refresh = true;                                     // factor at this iteration
         }
@@ -1063,10 +1070,12 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             const int op[1] = {0};
             grid_combine<1>(P.partials, op, bb);
             if (bb[0] > 0.0) { atomicCAS(&ctl->err, 0, ACS_ERR_FACTOR); ok = false; break; }
+            if (cond) factor_ok = false;                    // O changed: the factor is stale
             if (dense && factor_kept && !cond) {
                 factor_kept = false;                        // resumed: the cached factor is current
             } else if (dense) {
                 factor_kept = false;
+                factor_ok = false;
                 phase_dense_assemble(P);
                 ACS_SYNC(PH_DENSE_FACTOR);
                 for (int k = 0; k <= P.m && dense; ++k) {
@@ -1081,6 +1090,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                     phase_dense_inverse(P);
                     ACS_SYNC(PH_DENSE_FACTOR);
                     ++nfactor;
+                    factor_ok = true;
                 }
             }
             phase_update(P, false, false);                      // q = A_hat' w for the warm start
@@ -1243,7 +1253,8 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ctl->n_dense_solve += ndense;
         ctl->n_dense_factor += nfactor;
         ctl->stage = (sizeof(T) == 8 || status == ST_SWITCH) ? 1 : 0;
-        ctl->dense_on = dense ? 1 : 0;
+        ctl->dense_on = (dense || want_dense) ? 1 : 0;
+        ctl->factor_ok = factor_ok ? 1 : 0;
         ctl->dense_failed = dense_failed ? 1 : 0;
         ctl->win_cg = win_cg;
         ctl->win_it = win_it;

@@ -53,7 +53,7 @@ struct Control {
     int win_it;           // outer iterations since the last rescaling
     long long win_cg;     // CG iterations since the last rescaling (switch to the cached operator)
     int extrap_ok;        // wp, qp hold the previous iteration's w, q in the current scaling
-    int pad3;
+    int factor_ok;        // the problem's own cached factor is that of the current O
     unsigned bar_count, bar_gen;
     unsigned long long bar_count64;   // monotonic barrier arrival counter of the current solve
     // nanoseconds spent in each phase (from one barrier exit to the next, as

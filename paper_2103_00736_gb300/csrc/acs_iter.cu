@@ -120,6 +120,7 @@ __global__ void reset_control(Control* ctl, int l, double ds, double snorm, doub
     ctl->win_it = 0;
     ctl->win_cg = 0;
     ctl->extrap_ok = 0;
+    ctl->factor_ok = 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -69,6 +69,7 @@ __global__ void batch_reset(BatchArgs B, double eta0) {
         c->win_it = 0;
         c->win_cg = 0;
         c->extrap_ok = 0;
+        c->factor_ok = 0;
     }
     if (t == 0) *B.head = 0;
 }
