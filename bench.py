@@ -65,7 +65,7 @@ BATCH_MAX_ITER = 5000       # per member; members not solved by then count as un
 # (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
 # taken from: reported as null once acs_device.cuh, acs_iter.cu or
 # acs_internal.cuh change.
-TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "2f5b55074bad7e03", "bytes": 365.39e9}
+TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "1b1671daf2fd175f", "bytes": 366.12e9}
 
 
 def kernel_source_sha16() -> str:
