@@ -59,6 +59,9 @@ WORKLOADS = {
                   settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
 }
 BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
+# Random 4-byte gathers from an L2-resident 4 MB vector on this GB300 (152 SMs),
+# every load path (.ca, .cg, .nc), measured by a standalone probe: 275e9/s.
+GATHER_PROBE_G_PER_S = 275.0
 
 
 # DRAM bytes of one launch of the persistent kernel, from one ncu capture
@@ -317,6 +320,10 @@ def gpu_arm(args) -> None:
     # roofline of the persistent iteration kernel (the only kernel of a solve
     # besides three tiny initialisation launches)
     alg_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
+    # every stored entry of every matrix pass costs one random gather from an
+    # L2-resident vector: the rate that actually bounds these passes
+    n_cg_A, n_cg_AT, n64_A, n64_AT = (int(v) for v in counters[:4])
+    gathers = float(n_cg_A + n64_A) * info["padded_A"] + float(n_cg_AT + n64_AT) * info["padded_AT"]
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = args.traffic
@@ -366,6 +373,11 @@ def gpu_arm(args) -> None:
                        "nnz": inst.nnz, "tol": tol, "iterations": iters, "cg_iterations": int(res[6]),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (A and A' in FP32+FP64 ~0.6 GB)"},
+            "gather": {"achieved_g_per_s": gathers / (launch_ms / 1e3) / 1e9,
+                       "probe_g_per_s": GATHER_PROBE_G_PER_S,
+                       "frac": gathers / (launch_ms / 1e3) / 1e9 / GATHER_PROBE_G_PER_S,
+                       "note": "matrix passes x stored entries / launch time, against random 4-byte "
+                               "gathers from an L2-resident vector measured by a standalone probe"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "iter_kernel<float>",
