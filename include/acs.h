@@ -210,6 +210,13 @@ int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t 
  * kernel's launch shape, over n back-to-back barriers. */
 int acs_debug_barrier_ns(acs_problem* p, int32_t n, double* ns);
 int acs_problem_info(acs_problem* p, int32_t* out8);
+/* Test of the failure path of the persistent kernel's grid barrier: one
+ * grid-wide barrier of the solve's launch shape at which one CTA never
+ * arrives.  The others' bounded waits (2 s) run out; they record
+ * ACS_ERR_DEVICE_TIMEOUT and leave the kernel, which returns normally (no
+ * trap; the context and the handle stay usable).  Returns the recorded
+ * status and the time CTA 0 waited (ms). */
+int acs_debug_barrier_timeout(acs_problem* p, double* waited_ms);
 
 /*
  * KKT residuals of a caller-supplied point, for callers that cannot allocate

@@ -105,6 +105,7 @@ def lib():
         L.acs_problem_info.argtypes = [P, ip]
         L.acs_last_launch_ms.argtypes = [P, dp]
         L.acs_debug_barrier_ns.argtypes = [P, C.c_int32, dp]
+        L.acs_debug_barrier_timeout.argtypes = [P, dp]
         L.acs_kkt_residuals_noalloc.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, P, P,
                                                 C.c_int32, C.c_int32, P, P, P]
         L.acs_debug_phase_times.argtypes = [P, dp, C.POINTER(C.c_longlong), C.c_int32]
@@ -274,6 +275,13 @@ def acs_debug_barrier_ns(h, n: int = 1000) -> float:
     if rc != 0:
         raise AcsError(rc, "acs_debug_barrier_ns")
     return ns.value
+
+
+def acs_debug_barrier_timeout(h):
+    """(status recorded by the device, ms waited) of a barrier one CTA never reaches."""
+    ms = C.c_double()
+    rc = lib().acs_debug_barrier_timeout(C.c_void_p(h), C.byref(ms))
+    return rc, ms.value
 
 
 def acs_last_launch_ms(h) -> float:

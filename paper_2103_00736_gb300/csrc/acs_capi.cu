@@ -322,6 +322,16 @@ int acs_debug_barrier_ns(acs_problem* h, int32_t n, double* ns) {
     return acs::barrier_probe(P, n, ns);
 }
 
+int acs_debug_barrier_timeout(acs_problem* h, double* waited_ms) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !waited_ms) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    double ns = 0.0;
+    const int rc = acs::barrier_probe(P, 1, &ns, P->grid32 - 1);
+    *waited_ms = ns * 1e-6;
+    return rc;
+}
+
 int acs_last_launch_ms(acs_problem* h, double* ms) {
     Problem* P = reinterpret_cast<Problem*>(h);
     if (!P || !ms) return ACS_ERR_ARG;

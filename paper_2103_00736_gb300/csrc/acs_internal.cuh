@@ -167,6 +167,6 @@ struct Problem {
 // launches (acs_iter.cu)
 int launch_solve(Problem* P, double tol, int max_iter);
 int occupancy_grid(Problem* P);
-int barrier_probe(Problem* P, int n, double* ns_per_barrier);
+int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent = -1);
 
 }  // namespace acs

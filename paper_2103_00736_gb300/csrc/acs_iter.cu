@@ -39,9 +39,12 @@
 
 namespace acs {
 
-// Barrier latency probe: n grid_syncs with one reduced value each.
+// Barrier latency probe: n grid_syncs with one reduced value each.  With
+// absent >= 0 that CTA never arrives (the failure-path test): the others'
+// bounded waits run out, record ACS_ERR_DEVICE_TIMEOUT and leave; no trap.
 __global__ void __launch_bounds__(kThreads, 1)
-barrier_probe_kernel(Control* ctl, unsigned* flags, double* partials, int n, double* out) {
+barrier_probe_kernel(Control* ctl, unsigned* flags, double* partials, int n, double* out, int absent) {
+    if ((int)blockIdx.x == absent) return;
     team_set(blockIdx.x, gridDim.x, &ctl->bar_count64, partials);
     sync_init(ctl->bar_gen);
     const unsigned long long t0 = gtimer();
@@ -182,21 +185,25 @@ static cudaError_t launch_iter(Problem* P, const IterParams<T>& Q, int grid) {
                                        P->stream);
 }
 
-int barrier_probe(Problem* P, int n, double* ns_per_barrier) {
+int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent) {
     cudaStream_t st = P->stream;
     reset_flags<<<1, 256, 0, st>>>(P->flags, P->release, P->max_ctas);
     reset_control<<<1, 1, 0, st>>>(P->ctl, 0, INFINITY, 0.0, P->set.cg_eta);
     double* d_out = P->bcast;
-    void* args[] = {(void*)&P->ctl, (void*)&P->flags, (void*)&P->partials, (void*)&n, (void*)&d_out};
+    void* args[] = {(void*)&P->ctl, (void*)&P->flags, (void*)&P->partials, (void*)&n, (void*)&d_out,
+                    (void*)&absent};
     if (cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(P->grid32), dim3(kThreads), args, 0,
                                     st) != cudaSuccess)
         return ACS_ERR_CUDA;
     double h[2];
+    int err = 0;
     if (cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &P->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return ACS_ERR_CUDA;
-    if (h[1] != (double)n * P->grid32 * kThreads) return ACS_ERR_DEVICE_TIMEOUT;
     *ns_per_barrier = h[0];
+    if (err != 0) return err;
+    if (h[1] != (double)n * P->grid32 * kThreads) return ACS_ERR_DEVICE_TIMEOUT;
     return ACS_SOLVED;
 }
 
