@@ -184,3 +184,18 @@ def test_poisson_stream_from_several_threads(requests):
             assert kkt.max_residual(_kkt(requests[k], x, y, z)) <= 1e-6
     v = np.array(list(lat.values()))
     print("latency p50 %.2f ms p99 %.2f ms" % (np.percentile(v, 50), np.percentile(v, 99)))
+
+
+@pytest.mark.slow
+def test_served_full_recipe_sampled():
+    """Requests of the served recipe at full size (m up to 1e5, half with
+    cones) through the server with its defaults: every request solved, and
+    every result re-evaluated by the oracle's residual function."""
+    reqs = [I.serve_request(i) for i in range(16)]
+    with capi.Server(budget_bytes=8 << 30) as S:
+        ids = [S.submit(r, tol=1e-6, max_iter=5000) for r in reqs]
+        for k, rid in enumerate(ids):
+            assert S.wait(rid, 600.0) == capi.SOLVED
+            st, x, y, z, it, res, lat = S.result(rid)
+            r = _kkt(reqs[k], x, y, z)
+            assert kkt.max_residual(r) <= 1e-6, (k, reqs[k].m, r)
