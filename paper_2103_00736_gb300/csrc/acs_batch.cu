@@ -446,6 +446,11 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         X.H = host::HostProblem();
         X.H.perm = std::move(perm);
     }
+    for (Member& M : B->mem) {
+        std::vector<double>().swap(M.b);
+        std::vector<double>().swap(M.c);
+        std::vector<int>().swap(M.soc_off);
+    }
     const int rc = set_mapping(B, map0);
     if (rc != ACS_SOLVED) return fail(rc, -1);
     *out = reinterpret_cast<acs_batch*>(B);

@@ -223,7 +223,7 @@ Control fresh_control(double eta0) {
     return c;
 }
 
-void write_params(Server* S, Request* R) {
+cudaError_t write_params(Server* S, Request* R) {
     const int ncl = (int)S->cond_list_host.size();
     const Member& M = R->M;
     IterParams<float> p32 = member_params<float>(R->set, S->d_cond_list, ncl, M, R->X, M.V32, R->tol, R->max_iter);
@@ -233,15 +233,19 @@ void write_params(Server* S, Request* R) {
     p64.dM = R->dM;
     p64.dX = R->dX;
     p64.own_scratch = R->dM ? 1 : 0;
-    cudaMemcpyAsync(S->d_p32 + R->slot, &p32, sizeof(p32), cudaMemcpyHostToDevice, S->stream);
-    cudaMemcpyAsync(S->d_p64 + R->slot, &p64, sizeof(p64), cudaMemcpyHostToDevice, S->stream);
+    cudaError_t e = cudaMemcpyAsync(S->d_p32 + R->slot, &p32, sizeof(p32), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_p64 + R->slot, &p64, sizeof(p64), cudaMemcpyHostToDevice, S->stream);
+    return e;
 }
 
 // Upload an admitted request into its block and slot (worker thread).
-void admit(Server* S, Request* R) {
+// Returns the first CUDA error of the uploads (the caller then retires the
+// request with ACS_ERR_CUDA instead of running it).
+cudaError_t admit(Server* S, Request* R) {
     char* base = S->arena_base + R->off;
-    cudaMemcpyAsync(base, R->image.data(), R->static_bytes, cudaMemcpyHostToDevice, S->stream);
-    cudaMemsetAsync(base + R->static_bytes, 0, R->bytes - R->static_bytes, S->stream);
+    cudaError_t e = cudaMemcpyAsync(base, R->image.data(), R->static_bytes, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + R->static_bytes, 0, R->bytes - R->static_bytes, S->stream);
     std::vector<char>().swap(R->image);
     // offsets -> device addresses
     // (the shapes were recorded at submission, when the host image was built)
@@ -265,9 +269,10 @@ void admit(Server* S, Request* R) {
         R->dX = rebase(R->dX, base);
     }
     const Control c = fresh_control(S->set.cg_eta);
-    cudaMemcpyAsync(S->d_ctl + R->slot, &c, sizeof(c), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_ctl + R->slot, &c, sizeof(c), cudaMemcpyHostToDevice, S->stream);
     R->started = false;
-    write_params(S, R);
+    if (e == cudaSuccess) e = write_params(S, R);
+    return e;
 }
 
 void finish(Server* S, Request* R) {
@@ -494,8 +499,14 @@ void worker_main(Server* S) {
             }
         }
         for (Request* R : admitted) {
-            admit(S, R);
-            S->active.push_back(R);
+            if (admit(S, R) == cudaSuccess) {
+                S->active.push_back(R);
+            } else {
+                cudaGetLastError();
+                Control bad = fresh_control(0.0);
+                bad.status = ACS_ERR_CUDA;
+                retire(S, R, bad);
+            }
         }
         if (large) run_large(S, large);
         if (!S->active.empty()) run_round(S);
