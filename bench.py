@@ -68,7 +68,7 @@ GATHER_PROBE_G_PER_S = 275.0
 # (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
 # taken from: reported as null once acs_device.cuh, acs_iter.cu or
 # acs_internal.cuh change.
-TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "1b1671daf2fd175f", "bytes": 366.12e9}
+TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "ab96d071604e55d4", "bytes": 366.13e9}
 
 
 def kernel_source_sha16() -> str:
