@@ -381,6 +381,12 @@ typedef struct {
                                 GPU; default 8388608                                         */
     int32_t threads_per_cta; /* mapping of the rounds (as acs_batch_mapping); default 256   */
     int32_t team_ctas;       /* default 1                                                    */
+    int64_t long_nnz;        /* requests whose A has more nonzeros are "long": while long and
+                                short requests are both admitted, rounds alternate between the
+                                two classes with equal time for each, so that short requests do
+                                not wait idle for a long request's iteration (the deadline is
+                                checked at the end of an iteration); 0 = one class; default
+                                262144                                                         */
     int32_t adaptive_teams;  /* 1 (default): work-sized teams while fewer requests than CTAs
                                 are admitted; 0: always queued teams of team_ctas CTAs, so
                                 that every request's arithmetic (reduction order included) is

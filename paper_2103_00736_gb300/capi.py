@@ -67,7 +67,7 @@ class acs_batch_mapping(C.Structure):
 class acs_server_config(C.Structure):
     _fields_ = [("budget_bytes", C.c_int64), ("max_active", C.c_int32), ("round_ms", C.c_double),
                 ("large_nnz", C.c_int64), ("threads_per_cta", C.c_int32), ("team_ctas", C.c_int32),
-                ("adaptive_teams", C.c_int32)]
+                ("long_nnz", C.c_int64), ("adaptive_teams", C.c_int32)]
 
 
 class AcsError(RuntimeError):

@@ -153,6 +153,7 @@ struct Server {
     // statistics
     long long n_rounds = 0, n_admitted = 0, n_done = 0, n_large = 0;
     double round_ms_sum = 0.0, active_sum = 0.0;
+    double short_credit_ms = 0.0;                 // round time the short class is owed
 };
 
 namespace {
@@ -390,9 +391,18 @@ void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& 
         }
 }
 
-// One time-sliced launch over every active request; retire the finished.
-void run_round(Server* S) {
-    std::vector<Request*> act = S->active;
+bool is_long(const Server* S, const Request* R) {
+    return S->cfg.long_nnz > 0 && R->M.nnz > S->cfg.long_nnz;
+}
+
+// One time-sliced launch over the active requests of a class (-1: all, 0:
+// short, 1: long); retire the finished.  Returns the round's wall time (ms).
+double run_round(Server* S, int cls) {
+    std::vector<Request*> act, others;
+    for (Request* R : S->active) {
+        if (cls < 0 || (int)is_long(S, R) == cls) act.push_back(R);
+        else others.push_back(R);
+    }
     std::sort(act.begin(), act.end(), [](const Request* a, const Request* b) { return a->id < b->id; });
     std::vector<int> order(act.size());
     for (size_t k = 0; k < act.size(); ++k) order[k] = act[k]->slot;
@@ -467,8 +477,10 @@ void run_round(Server* S) {
             retire(S, R, C);
         }
     }
-    S->active.swap(keep);
+    others.insert(others.end(), keep.begin(), keep.end());
+    S->active.swap(others);
     if (e != cudaSuccess) fprintf(stderr, "acs: serving round failed: %s\n", cudaGetErrorString(e));
+    return ms;
 }
 
 void worker_main(Server* S) {
@@ -509,7 +521,22 @@ void worker_main(Server* S) {
             }
         }
         if (large) run_large(S, large);
-        if (!S->active.empty()) run_round(S);
+        if (!S->active.empty()) {
+            // with both classes admitted, alternate with equal time for each:
+            // a long request's iteration can outlast the deadline by far, and
+            // short requests would wait idle for it in a shared round
+            int n_long = 0;
+            for (const Request* R : S->active) n_long += is_long(S, R) ? 1 : 0;
+            const int n_short = (int)S->active.size() - n_long;
+            if (n_long == 0 || n_short == 0) {
+                run_round(S, -1);
+                S->short_credit_ms = 0.0;
+            } else if (S->short_credit_ms > 0.0) {
+                S->short_credit_ms -= run_round(S, 0);
+            } else {
+                S->short_credit_ms += run_round(S, 1);
+            }
+        }
     }
 }
 
@@ -528,6 +555,7 @@ int acs_server_config_default(acs_server_config* c) {
     c->large_nnz = (int64_t)1 << 23;
     c->threads_per_cta = 256;
     c->team_ctas = 1;
+    c->long_nnz = 262144;
     c->adaptive_teams = 1;
     return ACS_SOLVED;
 }
@@ -542,7 +570,7 @@ int acs_server_create(const acs_settings* settings, const acs_server_config* cfg
     acs_server_config c;
     if (cfg) c = *cfg; else acs_server_config_default(&c);
     const acs_batch_mapping map{c.threads_per_cta, c.team_ctas};
-    if (c.budget_bytes < (1 << 20) || c.max_active <= 0 || !(c.round_ms > 0) || c.large_nnz < 0 ||
+    if (c.budget_bytes < (1 << 20) || c.max_active <= 0 || !(c.round_ms > 0) || c.large_nnz < 0 || c.long_nnz < 0 ||
         !valid_mapping(map))
         return ACS_ERR_ARG;
     Server* S = new (std::nothrow) Server();
