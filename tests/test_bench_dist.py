@@ -59,3 +59,17 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.replica_throughput(1, 5, 2.0) == 2.5
+
+
+def test_affine_residuals_of_the_bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    from paper_2103_00736_gb300 import instances as I
+    inst = I.socp(scale=0.001)
+    r = bench.affine_residuals(inst, inst.x_star, inst.y_star, inst.s_star)
+    assert max(r.values()) < 1e-12, r
+    x = inst.x_star + 1e-3 * np.random.default_rng(0).standard_normal(inst.n)
+    r = bench.affine_residuals(inst, x, inst.y_star, inst.s_star)
+    assert r["r_p"] > 1e-6 and r["obj_rel_err"] > 0
+    assert bench.worst_of([{"a": 1.0}, {"a": 3.0, "b": 2.0}]) == {"a": 3.0, "b": 2.0}
