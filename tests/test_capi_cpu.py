@@ -115,3 +115,29 @@ def test_shared_A_detection(capi):
     mem = I.batch(count=8, m_shared=60, mmin=20, mmax=80)
     share = capi.shared_A_index(mem)
     assert share[:2] == [-1, 0] and all(s == -1 for s in share[2:])
+
+
+def test_server_rejects_bad_configurations_before_the_device(capi):
+    bad = [dict(budget_bytes=1000), dict(max_active=0), dict(round_ms=0.0), dict(large_nnz=-1),
+           dict(long_nnz=-1), dict(threads_per_cta=384), dict(team_ctas=3)]
+    for kw in bad:
+        with pytest.raises(capi.AcsError) as e:
+            capi.acs_server_create(None, capi.acs_server_config_default(**kw))
+        assert e.value.code == capi.ERR_ARG, kw
+    s = capi.acs_settings_default(mu=-1.0)
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_server_create(s, capi.acs_server_config_default())
+    assert e.value.code == capi.ERR_ARG
+    c = capi.acs_server_config_default()
+    assert (c.round_ms, c.max_active, c.threads_per_cta, c.team_ctas, c.adaptive_teams) == (2.0, 2048, 256, 1, 1)
+
+
+def test_settings_of_the_projection_are_validated(capi):
+    from paper_2103_00736_gb300 import instances as I
+    inst = I.bernoulli_lp(21, 6, 15, density=0.3)
+    for kw in (dict(projection=7), dict(dense_max_m=5000), dict(a_storage=3), dict(extrapolation=-0.5),
+               dict(dense_switch_cg=-1)):
+        with pytest.raises(capi.AcsError) as e:
+            capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
+                                    inst.n_orth, inst.soc_dims, capi.acs_settings_default(**kw))
+        assert e.value.code == capi.ERR_ARG, kw
