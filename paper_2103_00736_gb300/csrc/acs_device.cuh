@@ -554,11 +554,12 @@ __device__ __noinline__ void phase_btilde(const IterParams<T>& P) {
 // exactly, with no matrix pass (theta = 0: the previous w, a plain warm
 // start).  The outer iteration converges linearly, so consecutive w follow a
 // near-geometric sequence and the extrapolated start leaves the correction
-// solve a smaller residual.  Returns the q to use; saves the current pair.
-__device__ __forceinline__ double extrap_q(const Outer& X, int j, double theta) {
+// solve a smaller residual.  Returns the q to use; saves the current pair
+// when the setting is on (save).
+__device__ __forceinline__ double extrap_q(const Outer& X, int j, double theta, bool save) {
     const double q = X.q[j];
     if (theta == 0.0) {
-        X.qp[j] = q;
+        if (save) X.qp[j] = q;
         return q;
     }
     const double qn = fma(theta, q - X.qp[j], q);
@@ -575,15 +576,17 @@ __device__ __forceinline__ double extrap_q(const Outer& X, int j, double theta) 
 template <typename T>
 __device__ __noinline__ void phase_abs(const IterParams<T>& P, double theta) {
     const Outer& X = P.X;
-    for (int i = global_tid(); i < P.m; i += global_threads()) {
-        const double w = X.w[i];
-        if (theta != 0.0) X.w[i] = fma(theta, w - X.wp[i], w);
-        X.wp[i] = w;
-    }
+    const bool save = P.extrap != 0.0;                  // the setting is on: keep the pairs
+    if (save)
+        for (int i = global_tid(); i < P.m; i += global_threads()) {
+            const double w = X.w[i];
+            if (theta != 0.0) X.w[i] = fma(theta, w - X.wp[i], w);
+            X.wp[i] = w;
+        }
     for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
         const double pj = fabs(X.s[j]);
         X.p[j] = pj;
-        X.g[j] = X.O[j] * (pj + extrap_q(X, j, theta));
+        X.g[j] = X.O[j] * (pj + extrap_q(X, j, theta, save));
     }
     const int lane = threadIdx.x & 31;
     for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
@@ -601,7 +604,7 @@ __device__ __noinline__ void phase_abs(const IterParams<T>& P, double theta) {
         for (int j = a + lane; j < e; j += 32) {
             const double pj = (j == a) ? head : ftail * X.s[j];
             X.p[j] = pj;
-            X.g[j] = Oc * (pj + extrap_q(X, j, theta));
+            X.g[j] = Oc * (pj + extrap_q(X, j, theta, save));
         }
     }
 }
