@@ -68,7 +68,7 @@ GATHER_PROBE_G_PER_S = 275.0
 # (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
 # taken from: reported as null once acs_device.cuh, acs_iter.cu or
 # acs_internal.cuh change.
-TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "ab96d071604e55d4", "bytes": 366.13e9}
+TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "85288478835299f6", "bytes": 357.23e9}
 
 
 def kernel_source_sha16() -> str:
