@@ -437,6 +437,17 @@ int acs_server_stats(acs_server* s, double* out);
 /* Finish every submitted request, stop the worker, release everything. */
 void acs_server_destroy(acs_server* s);
 
+/* Host-only checks of the serving loop's bookkeeping (no device involved).
+ * acs_debug_assign_teams: the work-sized teams of a round with n <= grid
+ * requests of the given work (> 0): cta[3 * grid] = per CTA the request's
+ * position (-1 = idle), its rank in the team and the team size.
+ * acs_debug_arena: runs ops on a first-fit pool of cap bytes: ops[k] > 0
+ * allocates ops[k] bytes (offsets[k] = its offset, or -1 if it did not fit),
+ * ops[k] < 0 frees the block of op -ops[k]-1; used_peak[2] = bytes in use at
+ * the end and the peak (blocks are rounded up to 256 bytes). */
+int acs_debug_assign_teams(int32_t n, const double* work, int32_t grid, int32_t* cta);
+int acs_debug_arena(int64_t cap, int32_t nops, const int64_t* ops, int64_t* offsets, int64_t* used_peak);
+
 /* Library version string. */
 const char* acs_version(void);
 

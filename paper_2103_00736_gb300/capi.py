@@ -133,6 +133,9 @@ def lib():
         L.acs_server_result.argtypes = [P, C.c_int64, dp, dp, dp, ip, dp, dp]
         L.acs_server_stats.argtypes = [P, dp]
         L.acs_server_destroy.argtypes = [P]
+        L.acs_debug_assign_teams.argtypes = [C.c_int32, dp, C.c_int32, ip]
+        L.acs_debug_arena.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64)]
         L.acs_server_destroy.restype = None
         L.acs_batch_destroy.restype = None
         _lib = L
@@ -695,3 +698,25 @@ class Server:
                 self.close()
         except Exception:
             pass
+
+
+def acs_debug_assign_teams(work, grid: int) -> np.ndarray:
+    """int32 [3, grid]: position, rank, team size per CTA (host-only check)."""
+    w = np.ascontiguousarray(work, dtype=np.float64)
+    out = np.zeros(3 * grid, dtype=np.int32)
+    rc = lib().acs_debug_assign_teams(int(w.size), _ptr(w, C.c_double), int(grid), _ptr(out, C.c_int32))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_assign_teams")
+    return out.reshape(3, grid)
+
+
+def acs_debug_arena(cap: int, ops):
+    """(offsets, used, peak) of a first-fit pool run (host-only check)."""
+    o = np.ascontiguousarray(ops, dtype=np.int64)
+    off = np.zeros(max(1, o.size), dtype=np.int64)
+    up = np.zeros(2, dtype=np.int64)
+    rc = lib().acs_debug_arena(int(cap), int(o.size), _ptr(o, C.c_int64), _ptr(off, C.c_int64),
+                               _ptr(up, C.c_int64))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_arena")
+    return off[:o.size], int(up[0]), int(up[1])

@@ -351,14 +351,16 @@ int pow2_floor(long long v) {
 // capped where more CTAs would only add barrier cost (one CTA per 16384
 // units of work); spare CTAs go to the requests with the most work per CTA.
 // Fills cta[3 * grid] = (position in order or -1, rank, team size).
-void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& cta) {
-    const int n = (int)act.size();
-    std::vector<double> w(n);
+double team_work(const Member& M) {
+    return (double)M.nnz * 2 + M.m + M.n + (M.dense ? 0.25 * (double)M.m * M.m : 0.0);
+}
+
+// w[k]: work of request k; requires 1 <= w.size() <= grid.
+void assign_teams_w(const std::vector<double>& w, int grid, std::vector<int>& cta) {
+    const int n = (int)w.size();
     std::vector<int> g(n), cap(n);
     double total = 0.0;
     for (int k = 0; k < n; ++k) {
-        const Member& M = act[k]->M;
-        w[k] = (double)M.nnz * 2 + M.m + M.n + (M.dense ? 0.25 * (double)M.m * M.m : 0.0);
         total += w[k];
         cap[k] = std::min(pow2_floor(std::max(1LL, (long long)(w[k] / 16384.0))), std::min(grid, kMaxGrid));
     }
@@ -369,6 +371,7 @@ void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& 
     }
     while (used > grid) {                          // halve the largest team
         int j = (int)(std::max_element(g.begin(), g.end()) - g.begin());
+        if (g[j] == 1) break;                      // (cannot happen while n <= grid)
         used -= g[j] / 2;
         g[j] /= 2;
     }
@@ -389,6 +392,12 @@ void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& 
             cta[grid + b] = r;
             cta[2 * grid + b] = g[k];
         }
+}
+
+void assign_teams(const std::vector<Request*>& act, int grid, std::vector<int>& cta) {
+    std::vector<double> w(act.size());
+    for (size_t k = 0; k < act.size(); ++k) w[k] = team_work(act[k]->M);
+    assign_teams_w(w, grid, cta);
 }
 
 bool is_long(const Server* S, const Request* R) {
@@ -774,6 +783,40 @@ int acs_server_stats(acs_server* h, double* out) {
     out[7] = (double)S->pending.size();
     out[8] = S->n_rounds ? S->round_ms_sum / S->n_rounds : 0.0;
     out[9] = S->n_rounds ? S->active_sum / S->n_rounds : 0.0;
+    return ACS_SOLVED;
+}
+
+int acs_debug_assign_teams(int32_t n, const double* work, int32_t grid, int32_t* cta) {
+    if (n <= 0 || grid <= 0 || n > grid || !work || !cta) return ACS_ERR_ARG;
+    std::vector<double> w(work, work + n);
+    for (double v : w)
+        if (!(v > 0)) return ACS_ERR_ARG;
+    std::vector<int> c;
+    acs::assign_teams_w(w, grid, c);
+    std::copy(c.begin(), c.end(), cta);
+    return ACS_SOLVED;
+}
+
+int acs_debug_arena(int64_t cap, int32_t nops, const int64_t* ops, int64_t* offsets, int64_t* used_peak) {
+    if (cap <= 0 || nops < 0 || (nops > 0 && (!ops || !offsets)) || !used_peak) return ACS_ERR_ARG;
+    acs::Arena A;
+    A.init((size_t)cap);
+    std::vector<int64_t> size_of(nops, 0);
+    for (int k = 0; k < nops; ++k) {
+        if (ops[k] > 0) {
+            size_t off = 0;
+            offsets[k] = A.alloc((size_t)ops[k], &off) ? (int64_t)off : -1;
+            size_of[k] = offsets[k] >= 0 ? ops[k] : 0;
+        } else {
+            const int64_t j = -ops[k] - 1;              // free the block of op j
+            if (j < 0 || j >= k || ops[j] <= 0 || offsets[j] < 0 || size_of[j] == 0) return ACS_ERR_ARG;
+            A.release((size_t)offsets[j], (size_t)size_of[j]);
+            size_of[j] = 0;
+            offsets[k] = -1;
+        }
+    }
+    used_peak[0] = (int64_t)A.used;
+    used_peak[1] = (int64_t)A.peak;
     return ACS_SOLVED;
 }
 
