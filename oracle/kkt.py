@@ -13,7 +13,9 @@ All norms are Euclidean.  The y-free gap of Eq. (15b),
 |(A^dagger b)'(c - z) - c'x|, is available separately.
 
 Pinned by: all residuals vanish (to rounding) at a planted optimum and are
-positive at perturbed points (tests/test_oracle_kkt.py).
+positive at perturbed points; the y-free gap equals |b'y - c'x| for every
+dual pair z = c - A'y and sees only the row-space part of z
+(tests/test_oracle_kkt.py).
 """
 from __future__ import annotations
 

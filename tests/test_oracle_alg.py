@@ -305,3 +305,17 @@ def test_iterate_history_and_y():
     assert len(r.x_history) == 5
     # y = w / mu is the multiplier: dual residual vanishes at convergence
     assert np.linalg.norm(A.T @ r.y + r.z - inst.c) <= 1e-6 * (1 + np.linalg.norm(inst.c))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vertex_enumeration_matches_highs(seed):
+    """The brute-force ground truth itself agrees with a simplex/IPM code."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(500 + seed)
+    m, n = int(rng.integers(2, 6)), int(rng.integers(6, 11))
+    A, b, c = _tiny_lp(rng, m, n)
+    x_ref, obj_ref, bases = vertex.solve_lp(A, b, c)
+    hi = linprog(c, A_eq=A, b_eq=b, bounds=(0, None), method="highs")
+    assert hi.status == 0
+    assert abs(hi.fun - obj_ref) <= 1e-9 * (1 + abs(obj_ref))
+    assert np.abs(A @ x_ref - b).max() <= 1e-9 * (1 + np.abs(b).max()) and x_ref.min() >= 0

@@ -43,3 +43,27 @@ def test_perturbations_are_detected():
     res = kkt.residuals(A, inst.b, inst.c, 1.1 * inst.x_star, inst.y_star, inst.s_star,
                         inst.n_orth, inst.soc_dims)
     assert res["r_gap"] > 1e-3 and res["r_cone"] < 1e-14
+
+
+def test_yfree_gap_is_the_duality_gap_of_any_dual_pair():
+    """Eq. (15b) without y: for z = c - A'y and Ax = b, (A^dagger b)'(c - z)
+    = b'(AA')^{-1} A A' y = b'y, so the y-free gap is |b'y - c'x| for every
+    y, and zero at the planted optimum."""
+    rng = np.random.default_rng(3)
+    for inst in (I.small_lp(), I.socp(scale=0.002)):
+        A = inst.to_scipy()
+        assert kkt.yfree_gap(A, inst.b, inst.c, inst.x_star, inst.s_star) <= \
+            1e-9 * (1 + abs(inst.obj_star))
+        for _ in range(3):
+            y = inst.y_star + rng.standard_normal(inst.m)
+            z = inst.c - A.T @ y
+            g = kkt.yfree_gap(A, inst.b, inst.c, inst.x_star, z)
+            assert abs(g - abs(inst.b @ y - inst.c @ inst.x_star)) <= 1e-8 * (1 + abs(g))
+    # with a z that is not of the form c - A'y only the row-space part counts
+    inst = I.small_lp()
+    A = inst.to_scipy()
+    u = rng.standard_normal(inst.n)
+    P = A.T @ np.linalg.lstsq(A.toarray().T, u, rcond=None)[0]     # row-space part of u
+    g1 = kkt.yfree_gap(A, inst.b, inst.c, inst.x_star, inst.s_star + u)
+    g2 = kkt.yfree_gap(A, inst.b, inst.c, inst.x_star, inst.s_star + P)
+    assert abs(g1 - g2) <= 1e-9 * (1 + g1) and g1 > 1e-3
