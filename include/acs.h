@@ -417,8 +417,9 @@ int acs_server_submit(acs_server* s, const acs_instance* req, double tol, int32_
 int acs_server_poll(acs_server* s, int64_t id, int32_t* done);
 
 /* Block until request id has finished or timeout_s has passed (< 0: no
- * limit).  Returns the request's status, or ACS_ERR_DEVICE_TIMEOUT if the
- * wait timed out.  Thread-safe. */
+ * limit).  Returns the request's status, ACS_ERR_DEVICE_TIMEOUT if the wait
+ * timed out, or ACS_ERR_ARG for an unknown id (also when another thread's
+ * acs_server_result took the request during the wait).  Thread-safe. */
 int acs_server_wait(acs_server* s, int64_t id, double timeout_s);
 
 /* Results of a finished request (as acs_get; any pointer may be NULL) and

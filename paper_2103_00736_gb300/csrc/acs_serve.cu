@@ -735,15 +735,20 @@ int acs_server_wait(acs_server* h, int64_t id, double timeout_s) {
     Server* S = reinterpret_cast<Server*>(h);
     if (!S) return ACS_ERR_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(id);
-    if (it == S->reqs.end()) return ACS_ERR_ARG;
-    acs::Request* R = it->second;
+    if (S->reqs.find(id) == S->reqs.end()) return ACS_ERR_ARG;
+    // look the request up again on every wake-up: another thread's
+    // acs_server_result may have taken (and freed) it meanwhile
+    auto ready = [&] {
+        auto it = S->reqs.find(id);
+        return it == S->reqs.end() || it->second->done;
+    };
     if (timeout_s < 0) {
-        S->cv_done.wait(lk, [&] { return R->done; });
-    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return R->done; })) {
+        S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
         return ACS_ERR_DEVICE_TIMEOUT;
     }
-    return R->status;
+    auto it = S->reqs.find(id);
+    return it == S->reqs.end() ? ACS_ERR_ARG : it->second->status;
 }
 
 int acs_server_result(acs_server* h, int64_t id, double* x, double* y, double* sl, int32_t* iters, double* residuals,

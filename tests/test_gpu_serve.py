@@ -199,3 +199,27 @@ def test_served_full_recipe_sampled():
             st, x, y, z, it, res, lat = S.result(rid)
             r = _kkt(reqs[k], x, y, z)
             assert kkt.max_residual(r) <= 1e-6, (k, reqs[k].m, r)
+
+
+def test_wait_while_another_thread_takes_the_result(requests):
+    """Several threads wait on one request while another takes its result:
+    every waiter returns the status or ACS_ERR_ARG (the request is gone),
+    never touches a freed request."""
+    with capi.Server(round_ms=0.5) as S:
+        for k in range(3):
+            rid = S.submit(requests[k], tol=1e-6, max_iter=20000)
+            got = []
+            th = [threading.Thread(target=lambda: got.append(S.wait(rid, 60.0))) for _ in range(6)]
+            for t in th:
+                t.start()
+            m, n = int(requests[k].m), int(requests[k].n)
+            while True:                                  # take the result as soon as it exists
+                st = capi.acs_server_result(S.h, rid, m, n)[0]
+                if st != capi.ERR_ARG:                   # ERR_ARG: not finished yet
+                    break
+                time.sleep(0.0005)
+            for t in th:
+                t.join()
+            assert st == capi.SOLVED
+            assert len(got) == 6 and all(g in (capi.SOLVED, capi.ERR_ARG) for g in got), got
+            assert S.wait(rid, 1.0) == capi.ERR_ARG
