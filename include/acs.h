@@ -131,9 +131,12 @@ int acs_settings_default(acs_settings* s);
  *                 n_orthant + sum(soc_dims) must equal n.
  *   settings    : may be NULL for the defaults.
  *   out         : receives the handle (NULL on failure).
- * Every row of A must be nonempty (A of full row rank is required by the
- * pseudoinverse of Algorithm 1 step 2; rank deficiency surfaces as
- * ACS_ERR_FACTOR in acs_solve).
+ * Every row of A must be nonempty.  The pseudoinverse of Algorithm 1 step 2
+ * asks for A of full row rank; linearly dependent rows with a consistent b
+ * are still solved (the cached operator drops the dependent direction, CG
+ * stays in the range of M).  With an inconsistent b the problem is
+ * infeasible and acs_solve ends with ACS_ERR_FACTOR, ACS_ERR_NUMERICAL or
+ * ACS_MAX_ITER, never ACS_SOLVED.
  * Errors: ACS_ERR_ARG, ACS_ERR_CSR, ACS_ERR_CONES, ACS_ERR_OOM, ACS_ERR_CUDA.
  */
 int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col,
@@ -445,7 +448,9 @@ void acs_server_destroy(acs_server* s);
  * acs_debug_arena: runs ops on a first-fit pool of cap bytes: ops[k] > 0
  * allocates ops[k] bytes (offsets[k] = its offset, or -1 if it did not fit),
  * ops[k] < 0 frees the block of op -ops[k]-1; used_peak[2] = bytes in use at
- * the end and the peak (blocks are rounded up to 256 bytes). */
+ * the end and the peak (blocks are rounded up to 256 bytes).
+ * Both return ACS_SOLVED, or ACS_ERR_ARG for n outside [1, grid], a work
+ * <= 0, a NULL pointer, or a free of a later, failed or already freed block. */
 int acs_debug_assign_teams(int32_t n, const double* work, int32_t grid, int32_t* cta);
 int acs_debug_arena(int64_t cap, int32_t nops, const int64_t* ops, int64_t* offsets, int64_t* used_peak);
 

@@ -190,10 +190,10 @@ def test_edge_shapes():
 
 def test_rank_deficient_rows():
     """Duplicate rows: M = AA' is singular.  The cached dense factorisation
-    fails and the solve continues with CG; with a consistent b the right-hand
-    sides stay in range(M), CG converges and the LP is solved (min x1 + x2,
-    x1 + 2 x2 = 1, x >= 0 -> x = (0, 1/2)); with an inconsistent b the
-    problem is infeasible and no solve may report success."""
+    drops the dependent direction; with a consistent b the remaining equation
+    implies the dropped one and the LP is solved (min x1 + x2, x1 + 2 x2 = 1,
+    x >= 0 -> x = (0, 1/2)); with an inconsistent b the problem is
+    infeasible and no solve may report success."""
     row_ptr = np.array([0, 2, 4], np.int64)
     col = np.array([0, 1, 0, 1], np.int32)
     val = np.array([1.0, 2.0, 1.0, 2.0])
