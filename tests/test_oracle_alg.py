@@ -319,3 +319,20 @@ def test_vertex_enumeration_matches_highs(seed):
     assert hi.status == 0
     assert abs(hi.fun - obj_ref) <= 1e-9 * (1 + abs(obj_ref))
     assert np.abs(A @ x_ref - b).max() <= 1e-9 * (1 + np.abs(b).max()) and x_ref.min() >= 0
+
+
+def test_y_is_the_weighted_least_squares_multiplier():
+    """y is not formed by the paper; the oracle takes the multiplier of the
+    projection solve, (g - v)/mu.  At a solution it must agree with the plain
+    definition: the least-squares y of A_hat'y = c_hat - z_hat in the scaled
+    space (z_hat = O z, since O(A'y + z - c) = 0), y = M^-1 A_hat (c_hat - z_hat)."""
+    inst = I.small_lp()
+    A = inst.to_scipy()
+    r = alg.algorithm2(A, inst.b, inst.c, inst.n, [], L=SCHEDS["lp"], max_iter=6000, tol=1e-10)
+    assert r.status == "solved"
+    Ah = (A @ sp.diags(r.O)).toarray()
+    y_ls = np.linalg.solve(Ah @ Ah.T, Ah @ (r.O * inst.c - r.O * r.z))
+    assert np.linalg.norm(r.y - y_ls) <= 1e-7 * (1 + np.linalg.norm(r.y))
+    # and the wrong sign or a missing O would not agree
+    y_bad = np.linalg.solve(Ah @ Ah.T, Ah @ (inst.c - r.z))
+    assert np.linalg.norm(r.y - y_bad) > 1e-3 * np.linalg.norm(r.y)
