@@ -191,6 +191,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HBM_SPEC_GBS = 7900.0   # nominal HBM3e bandwidth of one GB300, for context beside the measured peak
+
+
+def roofline_entry(kernel: str, alg_bytes: float, launch_ms: float, traffic=None, **extra) -> dict:
+    """The HBM roofline object of a kernel: algorithmic bytes per launch over the
+    launch's device time, against the measured copy bandwidth (and, for context,
+    the nominal one); traffic = DRAM bytes per launch from an ncu capture, or None."""
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+           "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
+           "spec_peak": HBM_SPEC_GBS, "frac_of_spec": achieved / HBM_SPEC_GBS,
+           "traffic_gbs": traffic / (launch_ms / 1e3) / 1e9 if traffic else None}
+    out.update(extra)
+    return out
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -345,14 +363,13 @@ def gpu_arm(args) -> None:
     value = replica_throughput(world, args.steps, elapsed_ms / 1e3)
 
     # roofline of the persistent iteration kernel (the only kernel of a solve
-    # besides three tiny initialisation launches)
+    # besides four small initialisation launches; its FP64 continuation
+    # launch returns at once unless the FP32 loop handed over)
     alg_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
     # every stored entry of every matrix pass costs one random gather from an
     # L2-resident vector: the rate that actually bounds these passes
     n_cg_A, n_cg_AT, n64_A, n64_AT = (int(v) for v in counters[:4])
     gathers = float(n_cg_A + n64_A) * info["padded_A"] + float(n_cg_AT + n64_AT) * info["padded_AT"]
-    peak, peak_kind = measured_peak_hbm()
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = args.traffic
     if traffic is None and args.workload == TRAFFIC_RECORD["workload"] and tol > 0 \
             and kernel_source_sha16() == TRAFFIC_RECORD["source_sha16"]:
@@ -408,11 +425,8 @@ def gpu_arm(args) -> None:
                        "frac": gathers / (launch_ms / 1e3) / 1e9 / GATHER_PROBE_G_PER_S,
                        "note": "matrix passes x stored entries / launch time, against random 4-byte "
                                "gathers from an L2-resident vector measured by a standalone probe"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "iter_kernel<float>",
-                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
-                         "step_ms_median": statistics.median(step_ms)},
+            "roofline": roofline_entry("iter_kernel<float>", alg_bytes, launch_ms, traffic,
+                                       step_ms_median=statistics.median(step_ms)),
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": 6 * args.steps,
@@ -536,8 +550,6 @@ def batch_arm(args) -> None:
         d2h = 8 * (2 * info0["sum_n"] + info0["sum_m"])
         e2e = {"value": solved / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
-    peak, peak_kind = measured_peak_hbm()
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     it_s = iters[st == capi.SOLVED]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -558,9 +570,7 @@ def batch_arm(args) -> None:
                   "how": "single-problem API, one member after another, size-stratified sample "
                          "extrapolated to all members"},
         "batched_over_plain": value / plain_value if plain_value > 0 else None,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "batch_kernel",
-                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms},
+        "roofline": roofline_entry("batch_kernel", alg_bytes, launch_ms),
         "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "cpu_baseline": None,
     }
     if rank == 0:
@@ -667,6 +677,13 @@ def serve_arm(args) -> None:
         "clocks": clk,
         "e2e": {"value": best["solves_per_s"], "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "served throughput is already end to end: host arrays in, results in host memory"},
+        "roofline": None,
+        "roofline_note": "rounds are timed on the host clock with their bookkeeping; the team kernel's "
+                         "roofline is the batch workload's line",
+        # one cooperative launch per round; a request run alone takes the
+        # single-problem path (four small initialisation launches, the FP32
+        # iteration launch and its FP64 continuation)
+        "gpu_launches": int(sum(t["rounds"] + 6 * t["large_alone"] for t in table)),
         "cpu_baseline": None,
     }
     if rank == 0:

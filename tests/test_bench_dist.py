@@ -73,3 +73,17 @@ def test_affine_residuals_of_the_bench():
     r = bench.affine_residuals(inst, x, inst.y_star, inst.s_star)
     assert r["r_p"] > 1e-6 and r["obj_rel_err"] > 0
     assert bench.worst_of([{"a": 1.0}, {"a": 3.0, "b": 2.0}]) == {"a": 3.0, "b": 2.0}
+
+
+def test_roofline_entry():
+    import json
+    import os
+    import bench
+    r = bench.roofline_entry("k", 400e9, 200.0, 360e9, step_ms_median=201.0)
+    peak = json.load(open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    assert r["achieved"] == 2000.0 and r["peak"] == peak and r["frac"] == 2000.0 / peak
+    assert r["frac_of_spec"] == 2000.0 / bench.HBM_SPEC_GBS and r["traffic_gbs"] == 1800.0
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["step_ms_median"] == 201.0
+    assert bench.roofline_entry("k", 1e9, 1.0)["traffic_gbs"] is None
+    json.dumps(r)
