@@ -220,6 +220,20 @@ int acs_problem_info(acs_problem* p, int32_t* out8);
  * trap; the context and the handle stay usable).  Returns the recorded
  * status and the time CTA 0 waited (ms). */
 int acs_debug_barrier_timeout(acs_problem* p, double* waited_ms);
+/* Host-only check of the preparation acs_problem_create does (no device
+ * involved): the row relabelling and the sliced-ELLPACK image of A (which =
+ * 0) or A' (which = 1) built for products run by `warps` warps.  A slice
+ * holds 32 / g rows; entry k of local row r of slice q sits at
+ * sptr[q] + 32 (k / g) + r g + (k mod g); padding entries have column 0 and
+ * value 0.  Row r of the relabelled A is row perm[r] of the input; the rows
+ * of A' list relabelled rows in increasing order.  The CSR is validated as
+ * by acs_problem_create (all coordinates orthant).  info[4] = {rows, slices,
+ * g, stored entries}; perm[m], sptr[slices + 1], slen[slices] (chunks of 32
+ * entries per slice), col / val[stored] are written where not NULL (call
+ * once with NULL arrays for the sizes).  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
+int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   int32_t which, int64_t warps, int32_t* info, int32_t* perm, int32_t* sptr, int32_t* slen,
+                   int32_t* out_col, double* out_val);
 
 /*
  * KKT residuals of a caller-supplied point, for callers that cannot allocate

@@ -134,6 +134,8 @@ def lib():
         L.acs_server_stats.argtypes = [P, dp]
         L.acs_server_destroy.argtypes = [P]
         L.acs_debug_assign_teams.argtypes = [C.c_int32, dp, C.c_int32, ip]
+        L.acs_debug_sell.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, C.c_int32, C.c_int64,
+                                     ip, ip, ip, ip, ip, dp]
         L.acs_debug_arena.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64)]
         L.acs_server_destroy.restype = None
@@ -720,3 +722,28 @@ def acs_debug_arena(cap: int, ops):
     if rc != 0:
         raise AcsError(rc, "acs_debug_arena")
     return off[:o.size], int(up[0]), int(up[1])
+
+
+def acs_debug_sell(m, n, row_ptr, col, val, which: int, warps: int) -> dict:
+    """The relabelling and sliced-ELLPACK image of A (which=0) or A' (which=1)
+    as acs_problem_create prepares them (host-only check)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    info = np.zeros(4, dtype=np.int32)
+    args = (int(m), int(n), _ptr(rp, C.c_int64), _ptr(ci, C.c_int32), _ptr(va, C.c_double), int(which), int(warps))
+    rc = lib().acs_debug_sell(*args, _ptr(info, C.c_int32), None, None, None, None, None)
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_sell")
+    rows, slices, g, stored = (int(v) for v in info)
+    perm = np.zeros(m, dtype=np.int32)
+    sptr = np.zeros(slices + 1, dtype=np.int32)
+    slen = np.zeros(max(slices, 1), dtype=np.int32)
+    oc = np.zeros(max(stored, 1), dtype=np.int32)
+    ov = np.zeros(max(stored, 1), dtype=np.float64)
+    rc = lib().acs_debug_sell(*args, _ptr(info, C.c_int32), _ptr(perm, C.c_int32), _ptr(sptr, C.c_int32),
+                              _ptr(slen, C.c_int32), _ptr(oc, C.c_int32), _ptr(ov, C.c_double))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_sell")
+    return dict(rows=rows, slices=slices, g=g, stored=stored, perm=perm, sptr=sptr, slen=slen[:slices],
+                col=oc[:stored], val=ov[:stored])

@@ -332,6 +332,29 @@ int acs_debug_barrier_timeout(acs_problem* h, double* waited_ms) {
     return rc;
 }
 
+int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   int32_t which, int64_t warps, int32_t* info, int32_t* perm, int32_t* sptr, int32_t* slen,
+                   int32_t* out_col, double* out_val) {
+    if (!info || (which != 0 && which != 1) || warps <= 0 || m <= 0 || n <= 0) return ACS_ERR_ARG;
+    std::vector<double> b((size_t)m, 0.0), c((size_t)n, 0.0);
+    const int v = acs::host::validate(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr);
+    if (v != ACS_SOLVED) return v;
+    acs::host::HostProblem H;
+    if (acs::host::build(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr, warps, warps, H) != ACS_SOLVED)
+        return ACS_ERR_CSR;
+    const acs::host::HostSell& S = which == 0 ? H.A : H.AT;
+    info[0] = S.nrows;
+    info[1] = S.nslices;
+    info[2] = S.g;
+    info[3] = (int32_t)S.col.size();
+    if (perm) std::copy(H.perm.begin(), H.perm.end(), perm);
+    if (sptr) std::copy(S.sptr.begin(), S.sptr.end(), sptr);
+    if (slen) std::copy(S.slen.begin(), S.slen.end(), slen);
+    if (out_col) std::copy(S.col.begin(), S.col.end(), out_col);
+    if (out_val) std::copy(S.val.begin(), S.val.end(), out_val);
+    return ACS_SOLVED;
+}
+
 int acs_last_launch_ms(acs_problem* h, double* ms) {
     Problem* P = reinterpret_cast<Problem*>(h);
     if (!P || !ms) return ACS_ERR_ARG;

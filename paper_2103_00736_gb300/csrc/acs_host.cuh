@@ -152,8 +152,7 @@ inline HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, 
 }
 
 // Lanes per row: enough slices for four per warp of the team that runs the
-// products (load balance), but no more lanes than about half the average row
-// length.
+// products (load balance), but no more lanes than the average row length.
 inline int choose_g(long long nrows, long long nnz, long long warps) {
     const double avg = nrows > 0 ? (double)nnz / (double)nrows : 1.0;
     int g = 1;
