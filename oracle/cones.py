@@ -32,6 +32,8 @@ def soc_offsets(n_orth: int, soc_dims) -> np.ndarray:
 
 
 def check_cones(n: int, n_orth: int, soc_dims) -> None:
+    """K is a product of Lorentz cones (Section II): n_orth size-1 cones, then
+    cones of size >= 2, covering all n coordinates."""
     dims = np.asarray(soc_dims, dtype=np.int64)
     if n_orth < 0 or np.any(dims < 2) or n_orth + int(dims.sum()) != n:
         raise ValueError("cone sizes must be n_orth >= 0, each soc dim >= 2, total n")

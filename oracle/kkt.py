@@ -28,6 +28,8 @@ KEYS = ("r_p", "r_d", "r_gap", "r_cone", "obj_p", "obj_d")
 
 
 def residuals(A, b, c, x, y, z, n_orth: int, soc_dims=()) -> dict:
+    """r_p, r_d, r_gap, r_cone of the optimality system (Lemma 2, Eqs. 19a-19c)
+    as defined above, plus the two objectives c'x and b'y."""
     A = sp.csr_matrix(A)
     obj_p = float(c @ x)
     obj_d = float(b @ y)
@@ -41,6 +43,7 @@ def residuals(A, b, c, x, y, z, n_orth: int, soc_dims=()) -> dict:
 
 
 def max_residual(res: dict) -> float:
+    """The stopping quantity: the largest of the four relative residuals."""
     return max(res["r_p"], res["r_d"], res["r_gap"], res["r_cone"])
 
 
