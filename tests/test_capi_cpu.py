@@ -141,3 +141,26 @@ def test_settings_of_the_projection_are_validated(capi):
             capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
                                     inst.n_orth, inst.soc_dims, capi.acs_settings_default(**kw))
         assert e.value.code == capi.ERR_ARG, kw
+
+
+def test_missing_library_fails_loudly(capi, monkeypatch, tmp_path):
+    """No CPU fallback: without the CUDA library every entry point raises."""
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libacs.so"))
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.acs_settings_default()
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.acs_problem_create(1, 1, np.array([0, 1], np.int64), np.array([0], np.int32), [1.0], [1.0],
+                                [1.0], 1, [], None)
+
+
+def test_product_path_does_not_load_the_oracle():
+    """The package and the benchmark's GPU arms import nothing from oracle/
+    (only the CPU-baseline leg does, inside its own subprocess)."""
+    import subprocess
+    import sys
+    code = ("import sys; import paper_2103_00736_gb300.capi, paper_2103_00736_gb300.instances, bench; "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
