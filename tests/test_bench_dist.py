@@ -87,3 +87,19 @@ def test_roofline_entry():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["step_ms_median"] == 201.0
     assert bench.roofline_entry("k", 1e9, 1.0)["traffic_gbs"] is None
     json.dumps(r)
+
+
+def test_oracle_extrapolation_rules():
+    import bench
+    s = {"first_iter_s": 5.0, "per_iter_s": 2.0, "iters": 3}
+    v, d = bench.oracle_solves_per_s(s, "large_lp")
+    n, pre, r = bench.ORACLE_ITERS_LARGE_LP, bench.ORACLE_PRE_COND_ITERS, bench.ORACLE_LATE_COST_RATIO
+    assert abs(1 / v - (5.0 + (pre - 1) * 2.0 + (n - pre) * r * 2.0)) < 1e-9
+    assert f"{n} iterations the oracle needs" in d
+    v, d = bench.oracle_solves_per_s(s, "socp")
+    assert abs(1 / v - (5.0 + (bench.GPU_ITERS_SOCP - 1) * 2.0)) < 1e-9
+    assert "has not been run to completion" in d
+    v, d = bench.oracle_solves_per_s({"complete_s": 0.25, "iters": 310, "status": "solved"}, "small_lp")
+    assert v == 4.0 and "complete solve" in d
+    with pytest.raises(ValueError):
+        bench.oracle_solves_per_s(s, "batch")
