@@ -174,6 +174,18 @@ def acs_settings_default(**overrides) -> acs_settings:
     return s
 
 
+def _check_lengths(m, n, row_ptr, col, val, b, c, where):
+    """The C entry points read m + 1 row pointers, row_ptr[m] entries and m, n
+    vector entries from these arrays: refuse shorter arrays here instead of
+    letting them read past the end (the C side validates the contents)."""
+    ok = row_ptr.size == int(m) + 1 and b.size == int(m) and c.size == int(n)
+    if ok and col is not None:
+        nnz = int(row_ptr[-1])
+        ok = 0 <= nnz <= min(col.size, val.size)
+    if not ok:
+        raise AcsError(ERR_ARG, f"{where}: array lengths do not match m, n and row_ptr[m]")
+
+
 def acs_problem_create(m, n, row_ptr, col, val, b, c, n_orthant, soc_dims=(), settings=None):
     """Returns an opaque handle (int); raises AcsError on failure."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -182,6 +194,7 @@ def acs_problem_create(m, n, row_ptr, col, val, b, c, n_orthant, soc_dims=(), se
     b = np.ascontiguousarray(b, dtype=np.float64)
     c = np.ascontiguousarray(c, dtype=np.float64)
     dims = np.ascontiguousarray(soc_dims, dtype=np.int32)
+    _check_lengths(m, n, row_ptr, col, val, b, c, "acs_problem_create")
     h = C.c_void_p()
     rc = lib().acs_problem_create(int(m), int(n), _ptr(row_ptr, C.c_int64), _ptr(col, C.c_int32),
                                   _ptr(val, C.c_double), _ptr(b, C.c_double), _ptr(c, C.c_double),
@@ -371,15 +384,22 @@ def acs_batch_create(instances, settings=None, mapping=None, share=None):
         j = -1 if share is None else int(share[i])
         a = arr[i]
         a.m, a.n = int(inst.m), int(inst.n)
-        if j < 0:
-            rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64)
-            cl = np.ascontiguousarray(inst.col, dtype=np.int32)
-            vl = np.ascontiguousarray(inst.val, dtype=np.float64)
-            keep += [rp, cl, vl]
-            a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)
         b = np.ascontiguousarray(inst.b, dtype=np.float64)
         c = np.ascontiguousarray(inst.c, dtype=np.float64)
         d = np.ascontiguousarray(inst.soc_dims, dtype=np.int32)
+        rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64) if j < 0 else np.zeros(int(inst.m) + 1, np.int64)
+        try:
+            if j < 0:
+                cl = np.ascontiguousarray(inst.col, dtype=np.int32)
+                vl = np.ascontiguousarray(inst.val, dtype=np.float64)
+                _check_lengths(inst.m, inst.n, rp, cl, vl, b, c, f"acs_batch_create (member {i})")
+                keep += [rp, cl, vl]
+                a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)
+            else:
+                _check_lengths(inst.m, inst.n, rp, None, None, b, c, f"acs_batch_create (member {i})")
+        except AcsError as err:
+            err.member = i
+            raise
         keep += [b, c, d]
         a.b, a.c = _ptr(b, C.c_double), _ptr(c, C.c_double)
         a.n_orthant, a.n_soc = int(inst.n_orth), int(d.size)
@@ -595,6 +615,7 @@ def acs_server_submit(h, inst, tol: float = 1e-6, max_iter: int = 10000, setting
     b = np.ascontiguousarray(inst.b, dtype=np.float64)
     c = np.ascontiguousarray(inst.c, dtype=np.float64)
     d = np.ascontiguousarray(inst.soc_dims, dtype=np.int32)
+    _check_lengths(inst.m, inst.n, rp, cl, vl, b, c, "acs_server_submit")
     a = acs_instance()
     a.m, a.n = int(inst.m), int(inst.n)
     a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)

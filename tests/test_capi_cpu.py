@@ -164,3 +164,42 @@ def test_product_path_does_not_load_the_oracle():
             "assert not bad, bad")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_refuses_short_arrays(capi):
+    """Arrays shorter than m, n and row_ptr[m] say are refused by the binding,
+    before the C side would read past their ends."""
+    rp = np.array([0, 2, 4], np.int64)
+    col = np.array([0, 1, 1, 2], np.int32)
+    val = np.array([1.0, 2.0, 3.0, 4.0])
+    for args in ((2, 3, rp, col[:3], val, np.ones(2), np.ones(3)),
+                 (2, 3, rp, col, val[:3], np.ones(2), np.ones(3)),
+                 (2, 3, rp[:2], col, val, np.ones(2), np.ones(3)),
+                 (2, 3, rp, col, val, np.ones(1), np.ones(3)),
+                 (2, 3, rp, col, val, np.ones(2), np.ones(2))):
+        with pytest.raises(capi.AcsError) as e:
+            capi.acs_problem_create(*args, 3, [])
+        assert e.value.code == capi.ERR_ARG and "array lengths" in str(e.value)
+    from paper_2103_00736_gb300 import instances as I
+    good = I.bernoulli_lp(11, 6, 15, density=0.3)
+    short = I.bernoulli_lp(12, 6, 15, density=0.3)
+    short.c = short.c[:-1]
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_batch_create([good, good, short])
+    assert e.value.code == capi.ERR_ARG and e.value.member == 2
+
+
+def test_abi_rejects_more_than_2_31_stored_entries(capi):
+    """The C ABI's own check (called without the binding): row_ptr[m] >= 2^31
+    is refused from the row pointers alone, before col or val are read."""
+    import ctypes as C
+    L = capi.lib()
+    rp = np.array([0, 1, 1 << 31], np.int64)
+    col = np.zeros(1, np.int32)
+    val = np.ones(1)
+    b, c = np.ones(2), np.ones(2)
+    h = C.c_void_p()
+    rc = L.acs_problem_create(2, 2, rp.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+                              val.ctypes.data_as(C.POINTER(C.c_double)), b.ctypes.data_as(C.POINTER(C.c_double)),
+                              c.ctypes.data_as(C.POINTER(C.c_double)), 2, 0, None, None, C.byref(h))
+    assert rc == capi.ERR_CSR and not h.value
