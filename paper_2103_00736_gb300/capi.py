@@ -254,6 +254,9 @@ def acs_set_state(h, s, O, w, l: int, step=None):
     O = np.ascontiguousarray(O, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     st = None if step is None else np.ascontiguousarray(step, dtype=np.float64)
+    info = acs_problem_info(h)
+    if s.size != info["n"] or O.size != info["n"] or w.size != info["m"] or (st is not None and st.size < 3):
+        raise AcsError(ERR_ARG, "acs_set_state: array lengths do not match the problem's m and n")
     rc = lib().acs_set_state(C.c_void_p(h), _ptr(s, C.c_double), _ptr(O, C.c_double),
                              _ptr(w, C.c_double), int(l), _ptr(st, C.c_double))
     if rc != 0:
