@@ -216,8 +216,16 @@ def acs_solve_async(h, tol: float, max_iter: int) -> int:
     return rc
 
 
+def _check_shape(h, m, n, where):
+    """The C side writes the problem's own m and n entries: refuse other sizes."""
+    info = acs_problem_info(h)
+    if (int(m), int(n)) != (info["m"], info["n"]):
+        raise AcsError(ERR_ARG, f"{where}: m, n = {m}, {n} but the problem is {info['m']} x {info['n']}")
+
+
 def acs_get(h, m: int, n: int):
     """(status, x, y, s, iters, residuals[8])."""
+    _check_shape(h, m, n, "acs_get")
     x = np.empty(n)
     y = np.empty(m)
     s = np.empty(n)
@@ -237,6 +245,7 @@ def acs_get_residuals(h):
 
 
 def acs_get_state(h, m: int, n: int):
+    _check_shape(h, m, n, "acs_get_state")
     s = np.empty(n)
     O = np.empty(n)
     w = np.empty(m)
@@ -254,8 +263,8 @@ def acs_set_state(h, s, O, w, l: int, step=None):
     O = np.ascontiguousarray(O, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     st = None if step is None else np.ascontiguousarray(step, dtype=np.float64)
-    info = acs_problem_info(h)
-    if s.size != info["n"] or O.size != info["n"] or w.size != info["m"] or (st is not None and st.size < 3):
+    _check_shape(h, w.size, s.size, "acs_set_state")
+    if O.size != s.size or (st is not None and st.size < 3):
         raise AcsError(ERR_ARG, "acs_set_state: array lengths do not match the problem's m and n")
     rc = lib().acs_set_state(C.c_void_p(h), _ptr(s, C.c_double), _ptr(O, C.c_double),
                              _ptr(w, C.c_double), int(l), _ptr(st, C.c_double))
