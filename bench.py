@@ -49,6 +49,18 @@ ORACLE_LATE_COST_RATIO = 13.5
 # schedule) costed like the early ones, which understates the oracle's time.
 GPU_ITERS_SOCP = 1550
 SOCP_PRE_COND_ITERS = 199
+# Batch and served stream: a size-stratified sample of this many members or
+# distinct requests.  Batch members (m <= 2000) are solved to completion.
+# Served requests reach m = 1e5, which the oracle cannot finish in bounded
+# time: their first iterations are timed and extrapolated to the oracle's
+# median iteration count for their type, measured once on the 22 of the 48
+# distinct requests with m <= 2500 (LPs 330 under the LP schedule, requests
+# with cones 270 under the SOCP schedule), every iteration costed like the
+# sampled ones (which understates the large LPs after their rescaling).
+CPU_SAMPLE_MEMBERS = 12
+ORACLE_ITERS_SERVE_LP = 330
+ORACLE_ITERS_SERVE_SOC = 270
+SERVE_DISTINCT = 48
 
 WORKLOADS = {
     "large_lp": dict(desc="LP m=200000 n=1000000 nnz=1e7 (10/col, N(0,1), row scales 10^U[-2,2], 30% x* > 0)",
@@ -232,9 +244,14 @@ def measured_peak_hbm():
 def cpu_sample(workload: str, iters: int) -> dict:
     """Time the FP64 oracle on the workload: the first iteration (includes the
     l = 1 conditioning, i.e. the factor/solve set-up) and `iters` further ones;
-    the small LP is solved to completion instead (about a second)."""
+    the small LP is solved to completion instead (about a second); the batch
+    and the served stream are sampled member by member."""
     import numpy as np  # noqa: F401
     from oracle import alg
+    if workload == "batch":
+        return _cpu_sample_batch(alg, iters)
+    if workload == "serve":
+        return _cpu_sample_serve(alg, iters)
     inst = make_instance(workload)
     A = inst.to_scipy()
     st = WORKLOADS[workload]["settings"]
@@ -257,6 +274,56 @@ def cpu_sample(workload: str, iters: int) -> dict:
     return {"first_iter_s": first, "per_iter_s": per_iter, "iters": len(stamps)}
 
 
+def _stratified(sizes, k: int):
+    """Indices of k items spread evenly over the items sorted by size."""
+    import numpy as np
+    order = np.argsort(np.asarray(sizes), kind="stable")
+    return [int(i) for i in order[np.linspace(0, len(sizes) - 1, min(k, len(sizes))).astype(int)]]
+
+
+def _cpu_sample_batch(alg, iters: int) -> dict:
+    from paper_2103_00736_gb300 import instances as I
+    count = 4096
+    sizes = I.batch_sizes(count)
+    ms = [1000 if i < count // 4 else sizes[i][0] for i in range(count)]
+    st = WORKLOADS["batch"]["settings"]
+    L = alg.Schedule(first=st["cond_first"], period=st["cond_period"])
+    total, solved, picked = 0.0, 0, []
+    for i in _stratified(ms, CPU_SAMPLE_MEMBERS):
+        x = I.batch_member(i, count, sizes=sizes)
+        A = x.to_scipy()
+        t0 = time.perf_counter()
+        r = alg.algorithm2(A, x.b, x.c, x.n_orth, x.soc_dims, mu=st["mu"], t=st["t"], L=L,
+                           max_iter=BATCH_MAX_ITER, tol=TOL, check_every=10)
+        total += time.perf_counter() - t0
+        solved += r.status == "solved"
+        picked.append(x.m)
+    return {"members_s": total, "members": len(picked), "solved": solved, "m_min": min(picked),
+            "m_max": max(picked), "count": count}
+
+
+def _cpu_sample_serve(alg, iters: int) -> dict:
+    from paper_2103_00736_gb300 import instances as I
+    kinds = [I.serve_request_kind(i) for i in range(SERVE_DISTINCT)]
+    total, picked = 0.0, []
+    for i in _stratified([m for m, _ in kinds], CPU_SAMPLE_MEMBERS):
+        m, soc = kinds[i]
+        x = I.serve_request(i)
+        A = x.to_scipy()
+        st = WORKLOADS["socp" if soc else "serve"]["settings"]
+        L = alg.Schedule(first=st["cond_first"], period=st["cond_period"])
+        stamps = []
+        t0 = time.perf_counter()
+        alg.algorithm2(A, x.b, x.c, x.n_orth, x.soc_dims, mu=st["mu"], t=st["t"], L=L, max_iter=1 + iters,
+                       tol=0.0, check_every=10 ** 9, on_iter=lambda *a: stamps.append(time.perf_counter()))
+        per = (stamps[-1] - stamps[0]) / max(1, len(stamps) - 1)
+        n_it = ORACLE_ITERS_SERVE_SOC if soc else ORACLE_ITERS_SERVE_LP
+        total += (stamps[0] - t0) + (n_it - 1) * per
+        picked.append(m)
+    return {"requests_s": total, "requests": len(picked), "m_min": min(picked), "m_max": max(picked),
+            "distinct": SERVE_DISTINCT}
+
+
 def run_cpu_sample_subprocess(workload: str, iters: int) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
@@ -267,7 +334,28 @@ def run_cpu_sample_subprocess(workload: str, iters: int) -> dict:
     raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
 
 
+def oracle_baseline(workload: str, args, rank: int, world: int):
+    """The cpu_baseline object of a bench line (rank 0 of a 1-GPU run only)."""
+    if rank != 0 or world != 1 or args.no_cpu:
+        return None
+    v, desc = oracle_solves_per_s(run_cpu_sample_subprocess(workload, args.cpu_iters), workload)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+
 def oracle_solves_per_s(sample: dict, workload: str) -> tuple[float, str]:
+    if "members_s" in sample:
+        return sample["solved"] / sample["members_s"], (
+            f"FP64 oracle, 1 thread: {sample['members']} of the {sample['count']} members, stratified by size "
+            f"(m {sample['m_min']}..{sample['m_max']}), solved one after another to {TOL:g} KKT within "
+            f"{BATCH_MAX_ITER} iterations each: {sample['solved']} solved in {sample['members_s']:.1f} s; "
+            f"the batch's rate taken as the sample's")
+    if "requests_s" in sample:
+        return sample["requests"] / sample["requests_s"], (
+            f"FP64 oracle, 1 thread: {sample['requests']} of the {sample['distinct']} distinct requests, "
+            f"stratified by size (m {sample['m_min']}..{sample['m_max']}); each one's first iterations timed "
+            f"and extrapolated to the oracle's median count for its type ({ORACLE_ITERS_SERVE_LP} for LPs, "
+            f"{ORACLE_ITERS_SERVE_SOC} with cones), every iteration costed like the sampled ones: "
+            f"{sample['requests_s']:.1f} s for the sample, one request after another")
     if "complete_s" in sample:
         return 1.0 / sample["complete_s"], (f"FP64 oracle, 1 thread: complete solve to {TOL:g} KKT, "
                                             f"{sample['iters']} iterations ({sample['status']}), "
@@ -424,11 +512,7 @@ def gpu_arm(args) -> None:
     accuracy = affine_residuals(inst, xs, ys, zs)
     capi.acs_problem_destroy(h)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        sample = run_cpu_sample_subprocess(args.workload, args.cpu_iters)
-        v, desc = oracle_solves_per_s(sample, args.workload)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    cpu = oracle_baseline(args.workload, args, rank, world)
 
     if rank == 0:
         line = {
@@ -592,7 +676,8 @@ def batch_arm(args) -> None:
                          "extrapolated to all members"},
         "batched_over_plain": value / plain_value if plain_value > 0 else None,
         "roofline": roofline_entry("batch_kernel", alg_bytes, launch_ms),
-        "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "cpu_baseline": None,
+        "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
+        "cpu_baseline": oracle_baseline("batch", args, rank, world),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -705,7 +790,7 @@ def serve_arm(args) -> None:
         # single-problem path (four small initialisation launches, the FP32
         # iteration launch and its FP64 continuation)
         "gpu_launches": int(sum(t["rounds"] + 6 * t["large_alone"] for t in table)),
-        "cpu_baseline": None,
+        "cpu_baseline": oracle_baseline("serve", args, rank, world),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -301,25 +301,36 @@ def batch_sizes(count: int = 4096, mmin: int = 50, mmax: int = 2000, ratio: floa
     return [(int(m), int(round(ratio * m))) for m in ms]
 
 
+def batch_member(i: int, count: int = 4096, shared: int | None = None, m_shared: int = 1000,
+                 mmin: int = 50, mmax: int = 2000, sizes=None) -> Instance:
+    """Member i of batch(count, ...), generated alone (the same arrays)."""
+    if shared is None:
+        shared = count // 4
+    if i < shared:
+        m = m_shared
+        n = int(round(2.5 * m))
+        inst = bernoulli_lp(seed_for(K_BATCH, i), m, n, pattern_seed=seed_for(K_BATCH, 999))
+    else:
+        m, n = (batch_sizes(count, mmin, mmax) if sizes is None else sizes)[i]
+        inst = bernoulli_lp(seed_for(K_BATCH, i), m, n)
+    inst.meta["shared_A"] = i < shared
+    return inst
+
+
 def batch(count: int = 4096, shared: int | None = None, m_shared: int = 1000,
           mmin: int = 50, mmax: int = 2000) -> list[Instance]:
     """Uneven LP batch: the first ``shared`` members (default count/4) share one
     A of size m_shared x 2.5*m_shared; the rest draw their own sizes and A."""
-    if shared is None:
-        shared = count // 4
     sizes = batch_sizes(count, mmin, mmax)
-    out = []
-    for i in range(count):
-        if i < shared:
-            m = m_shared
-            n = int(round(2.5 * m))
-            inst = bernoulli_lp(seed_for(K_BATCH, i), m, n, pattern_seed=seed_for(K_BATCH, 999))
-        else:
-            m, n = sizes[i]
-            inst = bernoulli_lp(seed_for(K_BATCH, i), m, n)
-        inst.meta["shared_A"] = i < shared
-        out.append(inst)
-    return out
+    return [batch_member(i, count, shared, m_shared, mmin, mmax, sizes) for i in range(count)]
+
+
+def serve_request_kind(i: int, mmin: int = 100, mmax: int = 100_000) -> tuple[int, bool]:
+    """(m, with Lorentz cones) of serve_request(i) without generating it: the
+    first two draws of its generator."""
+    rng = np.random.default_rng(seed_for(K_SERVE, i))
+    m = int(round(math.exp(rng.uniform(math.log(mmin), math.log(mmax)))))
+    return m, bool(rng.random() < 0.5)
 
 
 def serve_request(i: int, mmin: int = 100, mmax: int = 100_000) -> Instance:

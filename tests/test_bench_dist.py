@@ -103,3 +103,16 @@ def test_oracle_extrapolation_rules():
     assert v == 4.0 and "complete solve" in d
     with pytest.raises(ValueError):
         bench.oracle_solves_per_s(s, "batch")
+
+
+def test_oracle_baseline_object():
+    """Only rank 0 of a 1-GPU run times the oracle; the object has the contract's keys."""
+    import argparse
+    import bench
+    a = argparse.Namespace(no_cpu=False, cpu_iters=2)
+    assert bench.oracle_baseline("small_lp", a, 1, 1) is None
+    assert bench.oracle_baseline("small_lp", a, 0, 2) is None
+    assert bench.oracle_baseline("small_lp", argparse.Namespace(no_cpu=True, cpu_iters=2), 0, 1) is None
+    b = bench.oracle_baseline("small_lp", a, 0, 1)
+    assert set(b) == {"value", "unit", "cores", "kind", "sample"}
+    assert b["value"] > 0 and b["cores"] == 1 and b["kind"] == "oracle" and "complete solve" in b["sample"]

@@ -105,3 +105,14 @@ def test_poisson_arrivals():
     assert np.all(gaps > 0)
     assert abs(gaps.mean() - 0.01) < 0.0005                   # rate 100/s
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05          # exponential gaps
+
+
+def test_members_generated_alone_equal_the_batch_and_stream():
+    mem = I.batch(count=16, m_shared=120, mmin=50, mmax=400)
+    for i in (0, 3, 4, 15):
+        x = I.batch_member(i, count=16, m_shared=120, mmin=50, mmax=400)
+        for f in ("row_ptr", "col", "val", "b", "c", "x_star"):
+            assert np.array_equal(getattr(x, f), getattr(mem[i], f)), (i, f)
+    for i in range(8):
+        r = I.serve_request(i, mmax=1500)
+        assert I.serve_request_kind(i, mmax=1500) == (r.m, bool(len(r.soc_dims)))
