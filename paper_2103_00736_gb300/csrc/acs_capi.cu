@@ -57,13 +57,22 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
     rc |= upload(P, slen, H.slen.data(), H.slen.size());
     rc |= upload(P, col, H.col.data(), tot);
+    // the narrow copy of the values, converted over parts of the image in parallel
+    const int T = acs::host::host_threads((long long)tot);
     if (bf16) {
-        std::vector<unsigned short> h(tot);
-        for (size_t k = 0; k < tot; ++k) h[k] = acs::host::to_bf16(H.val[k]);
+        acs::host::raw_vector<unsigned short> h(tot);
+        acs::host::parallel_for(T, [&](int t) {
+            const size_t k1 = (size_t)acs::host::part_lo((long long)tot, t + 1, T);
+            for (size_t k = (size_t)acs::host::part_lo((long long)tot, t, T); k < k1; ++k)
+                h[k] = acs::host::to_bf16(H.val[k]);
+        });
         rc |= upload(P, v16, h.data(), tot);
     } else {
-        std::vector<float> f(tot);
-        for (size_t k = 0; k < tot; ++k) f[k] = (float)H.val[k];
+        acs::host::raw_vector<float> f(tot);
+        acs::host::parallel_for(T, [&](int t) {
+            const size_t k1 = (size_t)acs::host::part_lo((long long)tot, t + 1, T);
+            for (size_t k = (size_t)acs::host::part_lo((long long)tot, t, T); k < k1; ++k) f[k] = (float)H.val[k];
+        });
         rc |= upload(P, v32, f.data(), tot);
     }
     rc |= upload(P, v64, H.val.data(), tot);

@@ -12,6 +12,9 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <memory>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "../../include/acs.h"
@@ -21,10 +24,106 @@ namespace host {
 
 constexpr int kSortWindow = 2048;   // rows of A are sorted by length within windows of this size
 
+// Host threads for preparing a matrix of `entries` stored entries: one below
+// 2^20 entries (thread start-up would cost more than it saves, e.g. for each
+// member of a batch), else one per hardware thread, at most 16.
+inline int host_threads(long long entries) {
+    if (entries < (1LL << 20)) return 1;
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h, 16u));
+}
+
+// Runs f(0), ..., f(T-1) on up to T host threads (the caller runs f(0)); a
+// part whose thread cannot be started runs on the caller afterwards.  Every
+// part writes its own outputs, so the result does not depend on T or on
+// the order in which the parts run.
+template <typename F>
+void parallel_for(int T, const F& f) {
+    std::vector<std::thread> th;
+    std::vector<int> on_caller;
+    for (int t = 1; t < T; ++t) {
+        try {
+            th.emplace_back([&f, t] { f(t); });
+        } catch (const std::system_error&) {
+            on_caller.push_back(t);
+        }
+    }
+    f(0);
+    for (int t : on_caller) f(t);
+    for (auto& x : th) x.join();
+}
+
+// [lo, hi) of part t of T equal parts of [0, N).
+inline long long part_lo(long long N, int t, int T) { return N * t / T; }
+
+// Vectors whose resize leaves the new elements uninitialised: the large host
+// images are written in full by the threads that fill them, so their pages
+// are first touched (and zeroed by the OS) in parallel, not by one thread.
+template <typename T>
+struct uninit_alloc : std::allocator<T> {
+    template <typename U>
+    struct rebind { using other = uninit_alloc<U>; };
+    uninit_alloc() = default;
+    template <typename U>
+    uninit_alloc(const uninit_alloc<U>&) {}
+    template <typename U>
+    void construct(U* p) noexcept { ::new ((void*)p) U; }
+    template <typename U, typename... A>
+    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+template <typename T>
+using raw_vector = std::vector<T, uninit_alloc<T>>;
+
 inline bool finite_all(const double* v, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
     return true;
+}
+
+// Checks of the problem statement (Section II, Eq. (1)) as the ABI states
+// them: CSR shape and order, finite data, cone sizes adding up to n.
+inline int validate(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                    const double* b, const double* c, int32_t n_orthant, int32_t n_soc,
+                    const int32_t* soc_dims) {
+    if (m <= 0 || n <= 0 || !row_ptr || !b || !c) return ACS_ERR_ARG;
+    if (row_ptr[0] != 0) return ACS_ERR_CSR;
+    for (int i = 0; i < m; ++i)
+        if (row_ptr[i + 1] <= row_ptr[i]) return ACS_ERR_CSR;    // non-monotone or empty row
+    const int64_t nnz64 = row_ptr[m];
+    if (nnz64 <= 0 || nnz64 >= (int64_t)1 << 31) return ACS_ERR_CSR;
+    if (!col || !val) return ACS_ERR_ARG;
+    const int nnz = (int)nnz64;
+    // the per-entry checks run over row ranges in parallel; each kind of
+    // check is decided over all rows before the next, so the code returned
+    // is the one a single pass in this order would return
+    const int T = host_threads(nnz);
+    std::vector<char> bad_col(T, 0), bad_val(T, 0);
+    parallel_for(T, [&](int t) {
+        const int i1 = (int)part_lo(m, t + 1, T);
+        for (int i = (int)part_lo(m, t, T); i < i1 && !bad_col[t]; ++i) {
+            int prev = -1;
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int j = col[k];
+                if (j < 0 || j >= n || j <= prev) { bad_col[t] = 1; break; }
+                prev = j;
+            }
+        }
+        const long long k0 = part_lo(nnz, t, T), k1 = part_lo(nnz, t + 1, T);
+        bad_val[t] = finite_all(val + k0, (size_t)(k1 - k0)) ? 0 : 1;
+    });
+    for (char f : bad_col)
+        if (f) return ACS_ERR_CSR;
+    for (char f : bad_val)
+        if (f) return ACS_ERR_ARG;
+    if (!finite_all(b, m) || !finite_all(c, n)) return ACS_ERR_ARG;
+    if (n_orthant < 0 || n_soc < 0 || (n_soc > 0 && !soc_dims)) return ACS_ERR_CONES;
+    int64_t tot = n_orthant;
+    for (int i = 0; i < n_soc; ++i) {
+        if (soc_dims[i] < 2) return ACS_ERR_CONES;
+        tot += soc_dims[i];
+    }
+    if (tot != n) return ACS_ERR_CONES;
+    return ACS_SOLVED;
 }
 
 constexpr int kDenseLimit = 4096;   // largest m for the cached dense projection operator
@@ -73,50 +172,20 @@ inline int dense_mode(const acs_settings& set, int m) {
     return 0;
 }
 
-// Checks of the problem statement (Section II, Eq. (1)) as the ABI states
-// them: CSR shape and order, finite data, cone sizes adding up to n.
-inline int validate(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
-                    const double* b, const double* c, int32_t n_orthant, int32_t n_soc,
-                    const int32_t* soc_dims) {
-    if (m <= 0 || n <= 0 || !row_ptr || !b || !c) return ACS_ERR_ARG;
-    if (row_ptr[0] != 0) return ACS_ERR_CSR;
-    for (int i = 0; i < m; ++i)
-        if (row_ptr[i + 1] <= row_ptr[i]) return ACS_ERR_CSR;    // non-monotone or empty row
-    const int64_t nnz64 = row_ptr[m];
-    if (nnz64 <= 0 || nnz64 >= (int64_t)1 << 31) return ACS_ERR_CSR;
-    if (!col || !val) return ACS_ERR_ARG;
-    const int nnz = (int)nnz64;
-    for (int i = 0; i < m; ++i) {
-        int prev = -1;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            const int j = col[k];
-            if (j < 0 || j >= n || j <= prev) return ACS_ERR_CSR;
-            prev = j;
-        }
-    }
-    if (!finite_all(val, nnz) || !finite_all(b, m) || !finite_all(c, n)) return ACS_ERR_ARG;
-    if (n_orthant < 0 || n_soc < 0 || (n_soc > 0 && !soc_dims)) return ACS_ERR_CONES;
-    int64_t tot = n_orthant;
-    for (int i = 0; i < n_soc; ++i) {
-        if (soc_dims[i] < 2) return ACS_ERR_CONES;
-        tot += soc_dims[i];
-    }
-    if (tot != n) return ACS_ERR_CONES;
-    return ACS_SOLVED;
-}
 
 // Host image of a sliced-ELLPACK matrix with G lanes per row.
 struct HostSell {
     int nrows = 0, nslices = 0, g = 1;
-    std::vector<int> sptr, slen, col;
-    std::vector<double> val;
+    std::vector<int> sptr, slen;
+    raw_vector<int> col;
+    raw_vector<double> val;
 };
 
 // Rows are given by (beg[r], end[r]) ranges into (cols, vals); padding
 // entries repeat column 0 with value 0.  nslices = -1 if the padded size
 // does not fit 32-bit offsets.
 inline HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, const std::vector<long long>& end,
-                           const int* cols, const double* vals) {
+                           const int* cols, const double* vals, int threads = 1) {
     HostSell H;
     const int h = 32 / g;                     // rows per slice
     H.nrows = nrows;
@@ -135,19 +204,26 @@ inline HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, 
     }
     H.sptr[H.nslices] = (int)std::min<long long>(total, INT32_MAX);
     if (total >= INT32_MAX) { H.col.clear(); H.nslices = -1; return H; }
-    H.col.assign(total, 0);
-    H.val.assign(total, 0.0);
-    for (int sl = 0; sl < H.nslices; ++sl)
-        for (int lr = 0; lr < h; ++lr) {
-            const int r = sl * h + lr;
-            if (r >= nrows) break;
-            long long k = 0;
-            for (long long e = beg[r]; e < end[r]; ++e, ++k) {
-                const long long idx = H.sptr[sl] + 32 * (k / g) + lr * g + (k % g);
-                H.col[idx] = cols[e];
-                H.val[idx] = vals[e];
+    H.col.resize(total);
+    H.val.resize(total);
+    // slices own disjoint ranges of the image: zero (the padding) and fill
+    // them in parallel
+    parallel_for(threads, [&](int t) {
+        const int s0 = (int)part_lo(H.nslices, t, threads), s1 = (int)part_lo(H.nslices, t + 1, threads);
+        std::fill(H.col.begin() + H.sptr[s0], H.col.begin() + H.sptr[s1], 0);
+        std::fill(H.val.begin() + H.sptr[s0], H.val.begin() + H.sptr[s1], 0.0);
+        for (int sl = s0; sl < s1; ++sl)
+            for (int lr = 0; lr < h; ++lr) {
+                const int r = sl * h + lr;
+                if (r >= nrows) break;
+                long long k = 0;
+                for (long long e = beg[r]; e < end[r]; ++e, ++k) {
+                    const long long idx = H.sptr[sl] + 32 * (k / g) + lr * g + (k % g);
+                    H.col[idx] = cols[e];
+                    H.val[idx] = vals[e];
+                }
             }
-        }
+    });
     return H;
 }
 
@@ -158,6 +234,102 @@ inline int choose_g(long long nrows, long long nnz, long long warps) {
     int g = 1;
     while (g < 32 && (nrows * g) / 32 < 4 * warps && 2 * g <= avg) g *= 2;
     return g;
+}
+
+// A' of the relabelled A: for each coordinate j, the relabelled rows r with
+// A[perm[r], j] != 0, in increasing order, as CSR (rpT[n + 1], rows, vals).
+// Below 2^20 entries a plain counting sort (one pass, everything in cache).
+// Above, a counting sort would scatter every entry to a random place in
+// arrays of 12 bytes per entry; instead the entries first go to buckets of
+// kBucketCols consecutive columns (pass 2), then each bucket is sorted by
+// column within a cache-sized window (pass 3).  Thread t takes the relabelled rows
+// [m t / T, m (t + 1) / T) in passes 1 and 2 and places its entries after
+// those of the threads before it in every bucket, so every bucket holds its
+// entries in increasing row order and the stable sort of pass 3 keeps it:
+// the result is the same for any number of threads.
+constexpr int kBucketCols = 1024;
+
+inline void transpose_relabelled(int m, int n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                                 const std::vector<int>& perm, int T, std::vector<long long>& rpT,
+                                 raw_vector<int>& rows, raw_vector<double>& vals) {
+    const long long nnz = row_ptr[m];
+    if (nnz < (1LL << 20)) {
+        rpT.assign((size_t)n + 1, 0);
+        for (long long k = 0; k < nnz; ++k) rpT[col[k] + 1]++;
+        for (int j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+        rows.resize(nnz);
+        vals.resize(nnz);
+        std::vector<long long> cur(rpT.begin(), rpT.end() - 1);
+        for (int r = 0; r < m; ++r) {
+            const int i = perm[r];
+            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const long long d = cur[col[k]]++;
+                rows[d] = r;
+                vals[d] = val[k];
+            }
+        }
+        return;
+    }
+    const int B = (n + kBucketCols - 1) / kBucketCols;
+    // pass 1: entries per (thread, bucket)
+    std::vector<long long> cnt((size_t)T * B, 0);
+    parallel_for(T, [&](int t) {
+        long long* c = cnt.data() + (size_t)t * B;
+        const int r1 = (int)part_lo(m, t + 1, T);
+        for (int r = (int)part_lo(m, t, T); r < r1; ++r) {
+            const int i = perm[r];
+            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) ++c[col[k] / kBucketCols];
+        }
+    });
+    // bucket by bucket, thread by thread: where each thread's entries go
+    std::vector<long long> off((size_t)T * B), bstart((size_t)B + 1);
+    long long pos = 0;
+    for (int b = 0; b < B; ++b) {
+        bstart[b] = pos;
+        for (int t = 0; t < T; ++t) {
+            off[(size_t)t * B + b] = pos;
+            pos += cnt[(size_t)t * B + b];
+        }
+    }
+    bstart[B] = pos;
+    // pass 2: stage (row, column, value) in the buckets
+    raw_vector<int> sr(nnz), sc(nnz);
+    raw_vector<double> sv(nnz);
+    parallel_for(T, [&](int t) {
+        long long* o = off.data() + (size_t)t * B;
+        const int r1 = (int)part_lo(m, t + 1, T);
+        for (int r = (int)part_lo(m, t, T); r < r1; ++r) {
+            const int i = perm[r];
+            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const long long p = o[col[k] / kBucketCols]++;
+                sr[p] = r;
+                sc[p] = col[k];
+                sv[p] = val[k];
+            }
+        }
+    });
+    // pass 3: a stable counting sort by column inside every bucket
+    rpT.assign((size_t)n + 1, 0);
+    rows.resize(nnz);
+    vals.resize(nnz);
+    parallel_for(T, [&](int t) {
+        std::vector<long long> cur(kBucketCols + 1);
+        const int b1 = (int)part_lo(B, t + 1, T);
+        for (int b = (int)part_lo(B, t, T); b < b1; ++b) {
+            const int j0 = b * kBucketCols, w = std::min(n, j0 + kBucketCols) - j0;
+            std::fill(cur.begin(), cur.begin() + w + 1, 0LL);
+            for (long long p = bstart[b]; p < bstart[b + 1]; ++p) ++cur[sc[p] - j0 + 1];
+            cur[0] = bstart[b];
+            for (int q = 0; q < w; ++q) cur[q + 1] += cur[q];
+            for (int q = 0; q < w; ++q) rpT[j0 + q] = cur[q];
+            for (long long p = bstart[b]; p < bstart[b + 1]; ++p) {
+                const long long d = cur[sc[p] - j0]++;
+                rows[d] = sr[p];
+                vals[d] = sv[p];
+            }
+        }
+    });
+    rpT[n] = nnz;
 }
 
 // Everything the device needs of one problem, in host memory.  Row r of the
@@ -190,29 +362,19 @@ inline int build(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* co
             return (row_ptr[a + 1] - row_ptr[a]) > (row_ptr[b2 + 1] - row_ptr[b2]);
         });
     }
+    const int T = host_threads(nnz);
     {
         std::vector<long long> beg(m), end(m);
         for (int r = 0; r < m; ++r) { beg[r] = row_ptr[perm[r]]; end[r] = row_ptr[perm[r] + 1]; }
-        H.A = build_sell(m, choose_g(m, nnz, warps_A), beg, end, col, val);
+        H.A = build_sell(m, choose_g(m, nnz, warps_A), beg, end, col, val, T);
     }
     {
-        // A' by counting sort over the relabelled rows
-        std::vector<long long> rpT(n + 1, 0);
-        for (int k = 0; k < nnz; ++k) rpT[col[k] + 1]++;
-        for (int j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
-        std::vector<int> ciT(nnz);
-        std::vector<double> valT(nnz);
-        std::vector<long long> cur(rpT.begin(), rpT.end() - 1);
-        for (int r = 0; r < m; ++r) {
-            const int i = perm[r];
-            for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const long long pos = cur[col[k]]++;
-                ciT[pos] = r;
-                valT[pos] = val[k];
-            }
-        }
+        std::vector<long long> rpT;
+        raw_vector<int> ciT;
+        raw_vector<double> valT;
+        transpose_relabelled(m, n, row_ptr, col, val, perm, T, rpT, ciT, valT);
         std::vector<long long> beg(rpT.begin(), rpT.end() - 1), end(rpT.begin() + 1, rpT.end());
-        H.AT = build_sell(n, choose_g(n, nnz, warps_AT), beg, end, ciT.data(), valT.data());
+        H.AT = build_sell(n, choose_g(n, nnz, warps_AT), beg, end, ciT.data(), valT.data(), T);
     }
     if (H.A.nslices < 0 || H.AT.nslices < 0) return ACS_ERR_CSR;
     H.bperm.resize(m);

@@ -139,3 +139,53 @@ def test_sell_rejects_malformed_csr(capi):
     with pytest.raises(capi.AcsError) as e:
         capi.acs_debug_sell(2, 3, row_ptr, np.array([0, 1, 2], np.int32), np.ones(3), 2, 8)   # which
     assert e.value.code == capi.ERR_ARG
+
+
+def _decode(S, indptr):
+    """Positions in the image of every entry of the CSR rows given by
+    indptr (row r's k-th entry), and a mask of the padding positions."""
+    g, h = S["g"], 32 // S["g"]
+    lens = np.diff(indptr)
+    r = np.repeat(np.arange(lens.size), lens)
+    k = np.arange(indptr[-1]) - np.repeat(indptr[:-1], lens)
+    idx = S["sptr"][r // h].astype(np.int64) + 32 * (k // g) + (r % h) * g + (k % g)
+    pad = np.ones(S["stored"], bool)
+    pad[idx] = False
+    return idx, pad
+
+
+def test_sell_image_above_2_20_entries(capi):
+    """Above 2^20 entries the preparation runs on several threads and sorts
+    A' through column buckets; the image is the same exact layout."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(21)
+    m, n, per = 20000, 150001, 8
+    rows = np.concatenate([rng.choice(m, per, replace=False) for _ in range(n)])
+    cols = np.repeat(np.arange(n), per)
+    A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(m, n))
+    A.sort_indices()
+    assert A.nnz >= 1 << 20
+    rp, ci, va = A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data
+    S = capi.acs_debug_sell(m, n, rp, ci, va, 0, 152 * 32)
+    Ap = A[S["perm"]]
+    idx, pad = _decode(S, Ap.indptr)
+    assert np.array_equal(S["col"][idx], Ap.indices) and np.array_equal(S["val"][idx], Ap.data)
+    assert not S["col"][pad].any() and not S["val"][pad].any()
+    T = capi.acs_debug_sell(m, n, rp, ci, va, 1, 152 * 32)
+    At = Ap.T.tocsr()
+    At.sort_indices()                                  # relabelled rows increasing in every column
+    idx, pad = _decode(T, At.indptr)
+    assert np.array_equal(T["col"][idx], At.indices) and np.array_equal(T["val"][idx], At.data)
+    assert not T["col"][pad].any() and not T["val"][pad].any()
+    # the checks of the input run in parallel too, with the serial order's codes
+    bad_v = va.copy()
+    bad_v[-3] = np.nan
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_debug_sell(m, n, rp, ci, bad_v, 0, 152 * 32)
+    assert e.value.code == capi.ERR_ARG
+    bad_c = ci.copy()
+    bad_c[-2] = n                                     # column out of range in the last row
+    for v in (va, bad_v):                             # ... with or without a NaN as well: CSR first
+        with pytest.raises(capi.AcsError) as e:
+            capi.acs_debug_sell(m, n, rp, bad_c, v, 0, 152 * 32)
+        assert e.value.code == capi.ERR_CSR
