@@ -366,6 +366,15 @@ int acs_batch_phase_ms(acs_batch* b, int32_t i, double* ms, long long* count, in
 
 void acs_batch_destroy(acs_batch* b);
 
+/* Host-only check of the preparation acs_batch_create does before it uses
+ * the device: validation, relabelling and images of every distinct A, and
+ * the host image of the batch's static device region (matrices, b, c, cone
+ * offsets, member order) at its final offsets.  *hash = FNV-1a of that image,
+ * *static_bytes = its size.  Errors: those of acs_batch_create's host
+ * checks, with *bad_member as there. */
+int acs_debug_batch_image(int32_t count, const acs_instance* members, const acs_settings* settings,
+                          uint64_t* hash, int64_t* static_bytes, int32_t* bad_member);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent solves.
  *

@@ -134,6 +134,8 @@ def lib():
         L.acs_server_stats.argtypes = [P, dp]
         L.acs_server_destroy.argtypes = [P]
         L.acs_debug_assign_teams.argtypes = [C.c_int32, dp, C.c_int32, ip]
+        L.acs_debug_batch_image.argtypes = [C.c_int32, C.POINTER(acs_instance), C.POINTER(acs_settings),
+                                             C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.acs_debug_sell.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, C.c_int32, C.c_int64,
                                      ip, ip, ip, ip, ip, dp]
         L.acs_debug_arena.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -780,3 +782,36 @@ def acs_debug_sell(m, n, row_ptr, col, val, which: int, warps: int) -> dict:
         raise AcsError(rc, "acs_debug_sell")
     return dict(rows=rows, slices=slices, g=g, stored=stored, perm=perm, sptr=sptr, slen=slen[:slices],
                 col=oc[:stored], val=ov[:stored])
+
+
+def acs_debug_batch_image(instances, settings=None, share=None):
+    """(FNV-1a hash, bytes) of the host image acs_batch_create would upload
+    (host-only check); raises AcsError (with .member) like acs_batch_create."""
+    count = len(instances)
+    arr = (acs_instance * count)()
+    keep = []
+    for i, inst in enumerate(instances):
+        j = -1 if share is None else int(share[i])
+        a = arr[i]
+        a.m, a.n = int(inst.m), int(inst.n)
+        if j < 0:
+            rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(inst.col, dtype=np.int32)
+            vl = np.ascontiguousarray(inst.val, dtype=np.float64)
+            keep += [rp, cl, vl]
+            a.row_ptr, a.col, a.val = _ptr(rp, C.c_int64), _ptr(cl, C.c_int32), _ptr(vl, C.c_double)
+        b = np.ascontiguousarray(inst.b, dtype=np.float64)
+        c = np.ascontiguousarray(inst.c, dtype=np.float64)
+        d = np.ascontiguousarray(inst.soc_dims, dtype=np.int32)
+        keep += [b, c, d]
+        a.b, a.c = _ptr(b, C.c_double), _ptr(c, C.c_double)
+        a.n_orthant, a.n_soc, a.soc_dims = int(inst.n_orth), int(d.size), _ptr(d, C.c_int32)
+        a.share_A_with = j
+    h, nbytes, bad = C.c_uint64(), C.c_int64(), C.c_int32(-1)
+    rc = lib().acs_debug_batch_image(count, arr, C.byref(settings) if settings is not None else None,
+                                     C.byref(h), C.byref(nbytes), C.byref(bad))
+    if rc != 0:
+        err = AcsError(rc, f"acs_debug_batch_image (member {bad.value})")
+        err.member = bad.value
+        raise err
+    return h.value, nbytes.value

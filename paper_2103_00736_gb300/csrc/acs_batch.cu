@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <new>
+#include <atomic>
 #include <numeric>
 #include <vector>
 
@@ -250,6 +251,134 @@ void layout(Batch* B, Pool& P) {
     B->total_bytes = P.off;
 }
 
+// Host preparation of every member (no device involved): validation,
+// relabelling and images of each distinct A, b in relabelled order, norms,
+// and the members in decreasing order of work.  On failure returns the code
+// of the first failing member in member order and its index in *bad.
+int prepare_members(Batch* B, int count, const acs_instance* members, int* bad) {
+    // lanes per row are chosen for the smallest team (one 256-thread CTA,
+    // 8 warps) so that any mapping can run
+    const long long warps = 8;
+    // members are independent: prepared on up to 16 host threads (a few
+    // members stay on the caller), each taking the next unprepared member
+    const int T = count >= 64 ? host::host_threads(1LL << 20) : 1;
+    B->mem.resize(count);
+    std::vector<int> rc(count, ACS_SOLVED);
+    std::vector<Matrix> own(count);                      // built by the members that hold an A
+    std::atomic<int> next{0};
+    host::parallel_for(T, [&](int) {
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+            const acs_instance& I = members[i];
+            if (I.share_A_with >= 0) {
+                const int j = I.share_A_with;
+                if (j >= i || I.m != members[j].m || I.n != members[j].n) { rc[i] = ACS_ERR_ARG; continue; }
+                int root = j;                            // the member that holds the data
+                while (members[root].share_A_with >= 0) {
+                    // a link that does not point back fails an earlier member,
+                    // which is the one reported
+                    if (members[root].share_A_with >= root) { rc[i] = ACS_ERR_ARG; break; }
+                    root = members[root].share_A_with;
+                }
+                if (rc[i] != ACS_SOLVED) continue;
+                rc[i] = host::validate(I.m, I.n, members[root].row_ptr, members[root].col, members[root].val,
+                                       I.b, I.c, I.n_orthant, I.n_soc, I.soc_dims);
+            } else {
+                if (I.share_A_with < -1) { rc[i] = ACS_ERR_ARG; continue; }
+                rc[i] = host::validate(I.m, I.n, I.row_ptr, I.col, I.val, I.b, I.c, I.n_orthant, I.n_soc,
+                                       I.soc_dims);
+                if (rc[i] != ACS_SOLVED) continue;
+                if (host::build(I.m, I.n, I.row_ptr, I.col, I.val, I.b, I.c, I.n_orthant, I.n_soc, I.soc_dims,
+                                warps, warps, own[i].H) != ACS_SOLVED) {
+                    rc[i] = ACS_ERR_CSR;
+                    continue;
+                }
+                own[i].stored = (long long)own[i].H.A.col.size();
+            }
+        }
+    });
+    // the first failing member, in member order
+    for (int i = 0; i < count; ++i)
+        if (rc[i] != ACS_SOLVED) {
+            *bad = i;
+            return rc[i];
+        }
+    // distinct matrices in member order
+    std::vector<int> mat_of(count, -1);
+    for (int i = 0; i < count; ++i) {
+        if (members[i].share_A_with >= 0) {
+            mat_of[i] = mat_of[members[i].share_A_with];
+        } else {
+            mat_of[i] = (int)B->mats.size();
+            B->mats.push_back(std::move(own[i]));
+        }
+    }
+    host::parallel_for(T, [&](int t) {
+        const int i1 = (int)host::part_lo(count, t + 1, T);
+        for (int i = (int)host::part_lo(count, t, T); i < i1; ++i) {
+            const acs_instance& I = members[i];
+            Member& M = B->mem[i];
+            const Matrix& X = B->mats[mat_of[i]];
+            M.m = I.m; M.n = I.n; M.n_orth = I.n_orthant; M.n_soc = I.n_soc; M.mat = mat_of[i];
+            M.dense = host::dense_mode(B->set, I.m);
+            M.nnz = X.stored;
+            M.b.resize(I.m);
+            for (int r = 0; r < I.m; ++r) M.b[r] = I.b[X.H.perm[r]];
+            M.c.assign(I.c, I.c + I.n);
+            M.soc_off.resize(I.n_soc + 1);
+            M.soc_off[0] = I.n_orthant;
+            for (int k = 0; k < I.n_soc; ++k) M.soc_off[k + 1] = M.soc_off[k] + I.soc_dims[k];
+            double bn = 0, cn = 0;
+            for (int r = 0; r < I.m; ++r) bn += I.b[r] * I.b[r];
+            for (int j = 0; j < I.n; ++j) cn += I.c[j] * I.c[j];
+            M.bnorm = sqrt(bn);
+            M.cnorm = sqrt(cn);
+        }
+    });
+    for (const Member& M : B->mem)
+        if (M.dense) B->dense_m2 = std::max(B->dense_m2, (long long)M.m * M.m);
+    // members in decreasing order of work (stored entries of A and A', plus vectors)
+    B->order.resize(count);
+    std::iota(B->order.begin(), B->order.end(), 0);
+    std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b2) {
+        const Member& x = B->mem[a];
+        const Member& y = B->mem[b2];
+        return 2 * x.nnz + 4LL * (x.m + x.n) > 2 * y.nnz + 4LL * (y.m + y.n);
+    });
+    return ACS_SOLVED;
+}
+
+// The host image of the static region (matrices, b, c, cone offsets, the
+// conditioning list and the member order) at the offsets of layout().  The
+// parts are disjoint: zeroed, then written, on up to 16 host threads.
+void fill_image(Batch* B, host::raw_vector<char>& img) {
+    const size_t bytes = B->static_bytes;
+    img.resize(bytes);
+    const int T = host::host_threads((long long)(bytes / 16));
+    host::parallel_for(T, [&](int t) {
+        const size_t a = (size_t)host::part_lo((long long)bytes, t, T);
+        const size_t e = (size_t)host::part_lo((long long)bytes, t + 1, T);
+        memset(img.data() + a, 0, e - a);
+    });
+    const size_t nm = B->mats.size(), nmem = B->mem.size();
+    std::atomic<size_t> next{0};
+    host::parallel_for(T, [&](int) {
+        for (size_t k = next.fetch_add(1); k < nm + nmem; k = next.fetch_add(1)) {
+            if (k < nm) {
+                const Matrix& X = B->mats[k];
+                image_sell(img, X.H.A, X.dA);
+                image_sell(img, X.H.AT, X.dAT);
+            } else {
+                const Member& M = B->mem[k - nm];
+                put_bytes(img.data(), M.db, M.b.data(), M.b.size());
+                put_bytes(img.data(), M.dc, M.c.data(), M.c.size());
+                put_bytes(img.data(), M.dsoc, M.soc_off.data(), M.soc_off.size());
+            }
+        }
+    });
+    put_bytes(img.data(), B->d_cond_list, B->cond_list_host.data(), B->cond_list_host.size());
+    put_bytes(img.data(), B->d_order, B->order.data(), B->order.size());
+}
+
 void free_batch(Batch* B) {
     if (!B) return;
     drop_graph(B);
@@ -297,63 +426,11 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         return rc;
     };
 
-    // host preparation of every member (validation first, so that malformed
-    // input is rejected without a device); lanes per row are chosen for the
-    // smallest team (one 256-thread CTA, 8 warps) so that any mapping can run
-    const long long warps = 8;
-    B->mem.resize(count);
-    std::vector<int> mat_of(count, -1);
-    for (int i = 0; i < count; ++i) {
-        const acs_instance& I = members[i];
-        Member& M = B->mem[i];
-        if (I.share_A_with >= 0) {
-            const int j = I.share_A_with;
-            if (j >= i || I.m != members[j].m || I.n != members[j].n) return fail(ACS_ERR_ARG, i);
-            int root = j;                                // the member that holds the data
-            while (members[root].share_A_with >= 0) root = members[root].share_A_with;
-            const int rc = host::validate(I.m, I.n, members[root].row_ptr, members[root].col, members[root].val,
-                                          I.b, I.c, I.n_orthant, I.n_soc, I.soc_dims);
-            if (rc != ACS_SOLVED) return fail(rc, i);
-            mat_of[i] = mat_of[j];
-        } else {
-            if (I.share_A_with < -1) return fail(ACS_ERR_ARG, i);
-            const int rc = host::validate(I.m, I.n, I.row_ptr, I.col, I.val, I.b, I.c, I.n_orthant, I.n_soc,
-                                          I.soc_dims);
-            if (rc != ACS_SOLVED) return fail(rc, i);
-            Matrix X;
-            if (host::build(I.m, I.n, I.row_ptr, I.col, I.val, I.b, I.c, I.n_orthant, I.n_soc, I.soc_dims, warps,
-                            warps, X.H) != ACS_SOLVED)
-                return fail(ACS_ERR_CSR, i);
-            X.stored = (long long)X.H.A.col.size();
-            mat_of[i] = (int)B->mats.size();
-            B->mats.push_back(std::move(X));
-        }
-        const Matrix& X = B->mats[mat_of[i]];
-        M.m = I.m; M.n = I.n; M.n_orth = I.n_orthant; M.n_soc = I.n_soc; M.mat = mat_of[i];
-        M.dense = host::dense_mode(set, I.m);
-        if (M.dense) B->dense_m2 = std::max(B->dense_m2, (long long)I.m * I.m);
-        M.nnz = X.stored;
-        M.b.resize(I.m);
-        for (int r = 0; r < I.m; ++r) M.b[r] = I.b[X.H.perm[r]];
-        M.c.assign(I.c, I.c + I.n);
-        M.soc_off.resize(I.n_soc + 1);
-        M.soc_off[0] = I.n_orthant;
-        for (int k = 0; k < I.n_soc; ++k) M.soc_off[k + 1] = M.soc_off[k] + I.soc_dims[k];
-        double bn = 0, cn = 0;
-        for (int r = 0; r < I.m; ++r) bn += I.b[r] * I.b[r];
-        for (int j = 0; j < I.n; ++j) cn += I.c[j] * I.c[j];
-        M.bnorm = sqrt(bn);
-        M.cnorm = sqrt(cn);
+    {
+        int bad = -1;
+        const int rc = prepare_members(B, count, members, &bad);
+        if (rc != ACS_SOLVED) return fail(rc, bad);
     }
-    // members in decreasing order of work (stored entries of A and A', plus vectors)
-    B->order.resize(count);
-    std::iota(B->order.begin(), B->order.end(), 0);
-    std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b2) {
-        const Member& x = B->mem[a];
-        const Member& y = B->mem[b2];
-        return 2 * x.nnz + 4LL * (x.m + x.n) > 2 * y.nnz + 4LL * (y.m + y.n);
-    });
-
     // the device is touched only once every member has passed the host checks
     if (cudaSetDevice(B->device) != cudaSuccess) return fail(ACS_ERR_CUDA, -1);
     if (cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess)
@@ -379,23 +456,12 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
         return fail(ACS_ERR_OOM, -1);
     }
     {
-        std::vector<char> img;
+        host::raw_vector<char> img;
         try {
-            img.assign(B->static_bytes, 0);
+            fill_image(B, img);
         } catch (...) {
             return fail(ACS_ERR_OOM, -1);
         }
-        for (Matrix& X : B->mats) {
-            image_sell(img, X.H.A, X.dA);
-            image_sell(img, X.H.AT, X.dAT);
-        }
-        for (Member& M : B->mem) {
-            put_bytes(img, M.db, M.b.data(), M.b.size());
-            put_bytes(img, M.dc, M.c.data(), M.c.size());
-            put_bytes(img, M.dsoc, M.soc_off.data(), M.soc_off.size());
-        }
-        put_bytes(img, B->d_cond_list, B->cond_list_host.data(), B->cond_list_host.size());
-        put_bytes(img, B->d_order, B->order.data(), B->order.size());
         if (cudaMemcpy(B->pool, img.data(), B->static_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(ACS_ERR_CUDA, -1);
     }
@@ -643,6 +709,38 @@ int acs_batch_phase_ms(acs_batch* h, int32_t i, double* ms, long long* count, in
             count[k] += (long long)B->ctl_host[j].phase_n[k];
         }
     return acs::PH_COUNT;
+}
+
+int acs_debug_batch_image(int32_t count, const acs_instance* members, const acs_settings* settings,
+                          uint64_t* hash, int64_t* static_bytes, int32_t* bad_member) {
+    using namespace acs;
+    if (bad_member) *bad_member = -1;
+    if (count <= 0 || !members || !hash || !static_bytes) return ACS_ERR_ARG;
+    Batch B;
+    if (settings) B.set = *settings; else acs_settings_default(&B.set);
+    if (!host::valid_settings(B.set)) return ACS_ERR_ARG;
+    if (B.set.n_cond_list > 0) B.cond_list_host.assign(B.set.cond_list, B.set.cond_list + B.set.n_cond_list);
+    B.set.cond_list = nullptr;
+    B.count = count;
+    int bad = -1;
+    const int rc = prepare_members(&B, count, members, &bad);
+    if (rc != ACS_SOLVED) {
+        if (bad_member) *bad_member = bad;
+        return rc;
+    }
+    B.max_ctas = 152 * 8;           // sizes only the state region, which the image does not hold
+    Pool dry;
+    layout(&B, dry);
+    host::raw_vector<char> img;
+    fill_image(&B, img);
+    uint64_t h = 1469598103934665603ull;          // FNV-1a
+    for (char ch : img) {
+        h ^= (unsigned char)ch;
+        h *= 1099511628211ull;
+    }
+    *hash = h;
+    *static_bytes = (int64_t)B.static_bytes;
+    return ACS_SOLVED;
 }
 
 void acs_batch_destroy(acs_batch* h) {

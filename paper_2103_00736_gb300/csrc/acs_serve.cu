@@ -209,9 +209,9 @@ void request_image(Request* R) {
     R->image.assign(R->static_bytes, 0);
     image_sell(R->image, R->X.H.A, R->X.dA);
     image_sell(R->image, R->X.H.AT, R->X.dAT);
-    put_bytes(R->image, R->M.db, R->M.b.data(), R->M.b.size());
-    put_bytes(R->image, R->M.dc, R->M.c.data(), R->M.c.size());
-    put_bytes(R->image, R->M.dsoc, R->M.soc_off.data(), R->M.soc_off.size());
+    put_bytes(R->image.data(), R->M.db, R->M.b.data(), R->M.b.size());
+    put_bytes(R->image.data(), R->M.dc, R->M.c.data(), R->M.c.size());
+    put_bytes(R->image.data(), R->M.dsoc, R->M.soc_off.data(), R->M.soc_off.size());
 }
 
 Control fresh_control(double eta0) {

@@ -229,23 +229,24 @@ inline void layout_sell(Pool& P, const host::HostSell& H, DevSell& D, bool bf16)
 }
 
 template <typename T>
-void put_bytes(std::vector<char>& img, const void* dev_off, const T* src, size_t count);
+void put_bytes(char* img, const void* dev_off, const T* src, size_t count);
 
 // Host image of one matrix at the offsets of layout_sell.
-inline void image_sell(std::vector<char>& img, const host::HostSell& H, const DevSell& D) {
-    put_bytes(img, D.sptr, H.sptr.data(), H.sptr.size());
-    put_bytes(img, D.slen, H.slen.data(), H.slen.size());
-    put_bytes(img, D.col, H.col.data(), H.col.size());
+template <typename Img>
+void image_sell(Img& img, const host::HostSell& H, const DevSell& D) {
+    put_bytes(img.data(), D.sptr, H.sptr.data(), H.sptr.size());
+    put_bytes(img.data(), D.slen, H.slen.data(), H.slen.size());
+    put_bytes(img.data(), D.col, H.col.data(), H.col.size());
     if (D.v16) {
         std::vector<unsigned short> h(H.val.size());
         for (size_t k = 0; k < h.size(); ++k) h[k] = host::to_bf16(H.val[k]);
-        put_bytes(img, D.v16, h.data(), h.size());
+        put_bytes(img.data(), D.v16, h.data(), h.size());
     } else {
         std::vector<float> f(H.val.size());
         for (size_t k = 0; k < f.size(); ++k) f[k] = (float)H.val[k];
-        put_bytes(img, D.v32, f.data(), f.size());
+        put_bytes(img.data(), D.v32, f.data(), f.size());
     }
-    put_bytes(img, D.v64, H.val.data(), H.val.size());
+    put_bytes(img.data(), D.v64, H.val.data(), H.val.size());
 }
 
 // Device addresses of a matrix laid out at offsets from base.
@@ -343,8 +344,8 @@ IterParams<T> member_params(const acs_settings& set, const int* d_cond_list, int
 }
 
 template <typename T>
-void put_bytes(std::vector<char>& img, const void* dev_off, const T* src, size_t count) {
-    if (count) memcpy(img.data() + reinterpret_cast<size_t>(dev_off), src, count * sizeof(T));
+void put_bytes(char* img, const void* dev_off, const T* src, size_t count) {
+    if (count) memcpy(img + reinterpret_cast<size_t>(dev_off), src, count * sizeof(T));
 }
 
 template <typename T>

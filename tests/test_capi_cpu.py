@@ -203,3 +203,33 @@ def test_abi_rejects_more_than_2_31_stored_entries(capi):
                               val.ctypes.data_as(C.POINTER(C.c_double)), b.ctypes.data_as(C.POINTER(C.c_double)),
                               c.ctypes.data_as(C.POINTER(C.c_double)), 2, 0, None, None, C.byref(h))
     assert rc == capi.ERR_CSR and not h.value
+
+
+def test_batch_host_image_is_deterministic_and_checked(capi):
+    """The batch's host preparation runs on several threads that take members
+    as they come: the image is the same on every call, changes with any
+    value of the input, and malformed members are reported as by
+    acs_batch_create (first failing member, its code)."""
+    from paper_2103_00736_gb300 import instances as I
+    mem = I.batch(count=96, m_shared=200, mmin=50, mmax=400)
+    share = capi.shared_A_index(mem)
+    h0 = capi.acs_debug_batch_image(mem, share=share)
+    for _ in range(3):
+        assert capi.acs_debug_batch_image(mem, share=share) == h0
+    mem[70].val = mem[70].val.copy()
+    mem[70].val[5] += 1.0
+    h1 = capi.acs_debug_batch_image(mem, share=share)
+    assert h1[0] != h0[0] and h1[1] == h0[1]
+    good = I.bernoulli_lp(11, 6, 15, density=0.3)
+    bad = I.bernoulli_lp(12, 6, 15, density=0.3)
+    bad.row_ptr = bad.row_ptr.copy()
+    bad.row_ptr[2] = bad.row_ptr[1]
+    nan = I.bernoulli_lp(13, 6, 15, density=0.3)
+    nan.val = nan.val.copy()
+    nan.val[3] = np.nan
+    for members, code, where in (([good] * 70 + [nan] + [bad], capi.ERR_ARG, 70),
+                                 ([good] * 65 + [bad] + [good] * 10 + [nan], capi.ERR_CSR, 65)):
+        for fn in (capi.acs_debug_batch_image, capi.acs_batch_create):
+            with pytest.raises(capi.AcsError) as e:
+                fn(members)
+            assert (e.value.code, e.value.member) == (code, where), fn
