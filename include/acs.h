@@ -44,7 +44,7 @@ enum {
     ACS_ERR_CSR = -2,        /* malformed CSR: row_ptr not monotone, col out of
                                 range or unsorted/duplicate within a row, empty row */
     ACS_ERR_CONES = -3,      /* cone sizes do not add up to n, or a size < 2        */
-    ACS_ERR_OOM = -4,        /* device allocation failed                            */
+    ACS_ERR_OOM = -4,        /* device (or host) allocation failed                  */
     ACS_ERR_FACTOR = -5,     /* M = (AO)(AO)' not positive definite (CG breakdown)  */
     ACS_ERR_DEVICE_TIMEOUT = -6, /* a device-side grid barrier did not complete   */
     ACS_ERR_NUMERICAL = -7,  /* NaN or Inf in the iterates or residuals             */

@@ -428,7 +428,7 @@ int acs_batch_create(int32_t count, const acs_instance* members, const acs_setti
 
     {
         int bad = -1;
-        const int rc = prepare_members(B, count, members, &bad);
+        const int rc = host::no_throw([&] { return prepare_members(B, count, members, &bad); });
         if (rc != ACS_SOLVED) return fail(rc, bad);
     }
     // the device is touched only once every member has passed the host checks
@@ -723,7 +723,7 @@ int acs_debug_batch_image(int32_t count, const acs_instance* members, const acs_
     B.set.cond_list = nullptr;
     B.count = count;
     int bad = -1;
-    const int rc = prepare_members(&B, count, members, &bad);
+    const int rc = host::no_throw([&] { return prepare_members(&B, count, members, &bad); });
     if (rc != ACS_SOLVED) {
         if (bad_member) *bad_member = bad;
         return rc;
@@ -732,7 +732,7 @@ int acs_debug_batch_image(int32_t count, const acs_instance* members, const acs_
     Pool dry;
     layout(&B, dry);
     host::raw_vector<char> img;
-    fill_image(&B, img);
+    if (host::no_throw([&] { fill_image(&B, img); return ACS_SOLVED; }) != ACS_SOLVED) return ACS_ERR_OOM;
     uint64_t h = 1469598103934665603ull;          // FNV-1a
     for (char ch : img) {
         h ^= (unsigned char)ch;

@@ -180,7 +180,8 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     acs_settings set;
     if (settings) set = *settings; else acs_settings_default(&set);
     if (!acs::host::valid_settings(set)) return ACS_ERR_ARG;
-    const int vrc = acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims);
+    const int vrc = acs::host::no_throw(
+        [&] { return acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims); });
     if (vrc != ACS_SOLVED) return vrc;
     const int nnz = (int)row_ptr[m];
     Problem* P = new (std::nothrow) Problem();
@@ -201,9 +202,9 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (acs::occupancy_grid(P) != ACS_SOLVED) { free_all(P); delete P; return ACS_ERR_CUDA; }
     const long long warps = (long long)P->grid32 * acs::kThreads / 32;
     acs::host::HostProblem H;
-    if (acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H) != ACS_SOLVED) {
-        free_all(P); delete P; return ACS_ERR_CSR;
-    }
+    const int brc = acs::host::no_throw(
+        [&] { return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H); });
+    if (brc != ACS_SOLVED) { free_all(P); delete P; return brc; }
     P->perm = H.perm;
     P->padded_A = (long long)H.A.col.size();
     P->padded_AT = (long long)H.AT.col.size();
@@ -214,7 +215,10 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     const std::vector<double>& bperm = H.bperm;
     const std::vector<int>& off = H.soc_off;
 
-    if (upload_sell(P, HA, P->A) || upload_sell(P, HT, P->AT)) { free_all(P); delete P; return ACS_ERR_OOM; }
+    if (acs::host::no_throw([&] { return upload_sell(P, HA, P->A); }) ||
+        acs::host::no_throw([&] { return upload_sell(P, HT, P->AT); })) {
+        free_all(P); delete P; return ACS_ERR_OOM;
+    }
     rc |= dalloc(P, &P->soc_off, n_soc + 1);
     rc |= dalloc(P, &P->b, m); rc |= dalloc(P, &P->c, n);
     rc |= dalloc(P, &P->x, n); rc |= dalloc(P, &P->z, n);
@@ -345,23 +349,25 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
                    int32_t which, int64_t warps, int32_t* info, int32_t* perm, int32_t* sptr, int32_t* slen,
                    int32_t* out_col, double* out_val) {
     if (!info || (which != 0 && which != 1) || warps <= 0 || m <= 0 || n <= 0) return ACS_ERR_ARG;
-    std::vector<double> b((size_t)m, 0.0), c((size_t)n, 0.0);
-    const int v = acs::host::validate(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr);
-    if (v != ACS_SOLVED) return v;
-    acs::host::HostProblem H;
-    if (acs::host::build(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr, warps, warps, H) != ACS_SOLVED)
-        return ACS_ERR_CSR;
-    const acs::host::HostSell& S = which == 0 ? H.A : H.AT;
-    info[0] = S.nrows;
-    info[1] = S.nslices;
-    info[2] = S.g;
-    info[3] = (int32_t)S.col.size();
-    if (perm) std::copy(H.perm.begin(), H.perm.end(), perm);
-    if (sptr) std::copy(S.sptr.begin(), S.sptr.end(), sptr);
-    if (slen) std::copy(S.slen.begin(), S.slen.end(), slen);
-    if (out_col) std::copy(S.col.begin(), S.col.end(), out_col);
-    if (out_val) std::copy(S.val.begin(), S.val.end(), out_val);
-    return ACS_SOLVED;
+    return acs::host::no_throw([&]() -> int {
+        std::vector<double> b((size_t)m, 0.0), c((size_t)n, 0.0);
+        const int v = acs::host::validate(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr);
+        if (v != ACS_SOLVED) return v;
+        acs::host::HostProblem H;
+        if (acs::host::build(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr, warps, warps, H) != ACS_SOLVED)
+            return ACS_ERR_CSR;
+        const acs::host::HostSell& S = which == 0 ? H.A : H.AT;
+        info[0] = S.nrows;
+        info[1] = S.nslices;
+        info[2] = S.g;
+        info[3] = (int32_t)S.col.size();
+        if (perm) std::copy(H.perm.begin(), H.perm.end(), perm);
+        if (sptr) std::copy(S.sptr.begin(), S.sptr.end(), sptr);
+        if (slen) std::copy(S.slen.begin(), S.slen.end(), slen);
+        if (out_col) std::copy(S.col.begin(), S.col.end(), out_col);
+        if (out_val) std::copy(S.val.begin(), S.val.end(), out_val);
+        return ACS_SOLVED;
+    });
 }
 
 int acs_last_launch_ms(acs_problem* h, double* ms) {

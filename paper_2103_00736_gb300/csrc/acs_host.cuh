@@ -12,7 +12,9 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <exception>
 #include <memory>
+#include <new>
 #include <system_error>
 #include <thread>
 #include <vector>
@@ -36,21 +38,44 @@ inline int host_threads(long long entries) {
 // Runs f(0), ..., f(T-1) on up to T host threads (the caller runs f(0)); a
 // part whose thread cannot be started runs on the caller afterwards.  Every
 // part writes its own outputs, so the result does not depend on T or on
-// the order in which the parts run.
+// the order in which the parts run.  An exception of a part (an allocation
+// that failed) is rethrown on the caller once every part has ended.
 template <typename F>
 void parallel_for(int T, const F& f) {
+    std::vector<std::exception_ptr> err((size_t)std::max(T, 1));
+    auto run = [&f, &err](int t) {
+        try {
+            f(t);
+        } catch (...) {
+            err[t] = std::current_exception();
+        }
+    };
     std::vector<std::thread> th;
     std::vector<int> on_caller;
     for (int t = 1; t < T; ++t) {
         try {
-            th.emplace_back([&f, t] { f(t); });
+            th.emplace_back(run, t);
         } catch (const std::system_error&) {
             on_caller.push_back(t);
         }
     }
-    f(0);
-    for (int t : on_caller) f(t);
+    run(0);
+    for (int t : on_caller) run(t);
     for (auto& x : th) x.join();
+    for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+}
+
+// The C entry points call host code that allocates; a host allocation that
+// fails (the only exception this code raises) must not leave through the C
+// ABI as an exception: it becomes ACS_ERR_OOM.
+template <typename F>
+int no_throw(const F& f) {
+    try {
+        return f();
+    } catch (...) {
+        return ACS_ERR_OOM;
+    }
 }
 
 // [lo, hi) of part t of T equal parts of [0, N).

@@ -653,68 +653,78 @@ int acs_server_submit(acs_server* h, const acs_instance* I, double tol, int32_t 
         rs.check_every = per_request->check_every;
         if (!host::valid_settings(rs)) return ACS_ERR_ARG;
     }
-    const int vrc = host::validate(I->m, I->n, I->row_ptr, I->col, I->val, I->b, I->c, I->n_orthant, I->n_soc,
-                                   I->soc_dims);
+    const int vrc = host::no_throw([&] {
+        return host::validate(I->m, I->n, I->row_ptr, I->col, I->val, I->b, I->c, I->n_orthant, I->n_soc,
+                              I->soc_dims);
+    });
     if (vrc != ACS_SOLVED) return vrc;
     const Clock::time_point t_entry = Clock::now();   // latency includes the host preparation
     Request* R = new (std::nothrow) Request();
     if (!R) return ACS_ERR_OOM;
-    R->tol = tol;
-    R->max_iter = max_iter;
-    R->set = rs;
-    const long long nnz = I->row_ptr[I->m];
-    R->large = nnz > S->cfg.large_nnz;
-    if (R->large) {
-        R->row_ptr.assign(I->row_ptr, I->row_ptr + I->m + 1);
-        R->col.assign(I->col, I->col + nnz);
-        R->val.assign(I->val, I->val + nnz);
-        R->b.assign(I->b, I->b + I->m);
-        R->c.assign(I->c, I->c + I->n);
-        R->dims.assign(I->soc_dims, I->soc_dims + I->n_soc);
-        R->n_orth = I->n_orthant;
-    } else {
-        // the same preparation as a batch member (lanes per row for one CTA)
-        if (host::build(I->m, I->n, I->row_ptr, I->col, I->val, I->b, I->c, I->n_orthant, I->n_soc, I->soc_dims,
-                        (long long)S->map.threads_per_cta / 32, (long long)S->map.threads_per_cta / 32,
-                        R->X.H) != ACS_SOLVED) {
-            delete R;
-            return ACS_ERR_CSR;
+    const int prc = host::no_throw([&]() -> int {
+        R->tol = tol;
+        R->max_iter = max_iter;
+        R->set = rs;
+        const long long nnz = I->row_ptr[I->m];
+        R->large = nnz > S->cfg.large_nnz;
+        if (R->large) {
+            R->row_ptr.assign(I->row_ptr, I->row_ptr + I->m + 1);
+            R->col.assign(I->col, I->col + nnz);
+            R->val.assign(I->val, I->val + nnz);
+            R->b.assign(I->b, I->b + I->m);
+            R->c.assign(I->c, I->c + I->n);
+            R->dims.assign(I->soc_dims, I->soc_dims + I->n_soc);
+            R->n_orth = I->n_orthant;
+        } else {
+            // the same preparation as a batch member (lanes per row for one CTA)
+            if (host::build(I->m, I->n, I->row_ptr, I->col, I->val, I->b, I->c, I->n_orthant, I->n_soc, I->soc_dims,
+                            (long long)S->map.threads_per_cta / 32, (long long)S->map.threads_per_cta / 32,
+                            R->X.H) != ACS_SOLVED)
+                return ACS_ERR_CSR;
+            R->X.stored = (long long)R->X.H.A.col.size();
+            Member& M = R->M;
+            M.m = I->m; M.n = I->n; M.n_orth = I->n_orthant; M.n_soc = I->n_soc; M.mat = 0;
+            M.dense = host::dense_mode(rs, I->m);
+            M.nnz = R->X.stored;
+            M.b = R->X.H.bperm;
+            M.c.assign(I->c, I->c + I->n);
+            M.soc_off = R->X.H.soc_off;
+            M.bnorm = R->X.H.bnorm;
+            M.cnorm = R->X.H.cnorm;
+            Pool dry;
+            request_layout(R, dry);
+            if (R->bytes + 4096 > S->arena.cap) return ACS_ERR_LIMIT;
+            request_image(R);
+            auto shape = [](const host::HostSell& H, SellMat& Sm) {
+                Sm.nrows = H.nrows; Sm.nslices = H.nslices; Sm.g = H.g;
+            };
+            shape(R->X.H.A, R->X.A);
+            shape(R->X.H.AT, R->X.AT);
+            // the host images are no longer needed (keep the row relabelling)
+            std::vector<int> perm = std::move(R->X.H.perm);
+            R->X.H = host::HostProblem();
+            R->X.H.perm = std::move(perm);
+            std::vector<double>().swap(M.b);
+            std::vector<double>().swap(M.c);
         }
-        R->X.stored = (long long)R->X.H.A.col.size();
-        Member& M = R->M;
-        M.m = I->m; M.n = I->n; M.n_orth = I->n_orthant; M.n_soc = I->n_soc; M.mat = 0;
-        M.dense = host::dense_mode(rs, I->m);
-        M.nnz = R->X.stored;
-        M.b = R->X.H.bperm;
-        M.c.assign(I->c, I->c + I->n);
-        M.soc_off = R->X.H.soc_off;
-        M.bnorm = R->X.H.bnorm;
-        M.cnorm = R->X.H.cnorm;
-        Pool dry;
-        request_layout(R, dry);
-        if (R->bytes + 4096 > S->arena.cap) {
-            delete R;
-            return ACS_ERR_LIMIT;
-        }
-        request_image(R);
-        auto shape = [](const host::HostSell& H, SellMat& Sm) {
-            Sm.nrows = H.nrows; Sm.nslices = H.nslices; Sm.g = H.g;
-        };
-        shape(R->X.H.A, R->X.A);
-        shape(R->X.H.AT, R->X.AT);
-        // the host images are no longer needed (keep the row relabelling)
-        std::vector<int> perm = std::move(R->X.H.perm);
-        R->X.H = host::HostProblem();
-        R->X.H.perm = std::move(perm);
-        std::vector<double>().swap(M.b);
-        std::vector<double>().swap(M.c);
+        return ACS_SOLVED;
+    });
+    if (prc != ACS_SOLVED) {
+        delete R;
+        return prc;
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R->id = S->next_id++;
         R->t_submit = t_entry;
-        S->reqs[R->id] = R;
-        S->pending.push_back(R);
+        try {
+            S->reqs[R->id] = R;
+            S->pending.push_back(R);
+        } catch (...) {                                  // host memory: undo the registration
+            S->reqs.erase(R->id);
+            delete R;
+            return ACS_ERR_OOM;
+        }
         *id = R->id;
     }
     S->cv.notify_one();
@@ -793,36 +803,40 @@ int acs_server_stats(acs_server* h, double* out) {
 
 int acs_debug_assign_teams(int32_t n, const double* work, int32_t grid, int32_t* cta) {
     if (n <= 0 || grid <= 0 || n > grid || !work || !cta) return ACS_ERR_ARG;
-    std::vector<double> w(work, work + n);
-    for (double v : w)
-        if (!(v > 0)) return ACS_ERR_ARG;
-    std::vector<int> c;
-    acs::assign_teams_w(w, grid, c);
-    std::copy(c.begin(), c.end(), cta);
-    return ACS_SOLVED;
+    return acs::host::no_throw([&]() -> int {
+        std::vector<double> w(work, work + n);
+        for (double v : w)
+            if (!(v > 0)) return ACS_ERR_ARG;
+        std::vector<int> c;
+        acs::assign_teams_w(w, grid, c);
+        std::copy(c.begin(), c.end(), cta);
+        return ACS_SOLVED;
+    });
 }
 
 int acs_debug_arena(int64_t cap, int32_t nops, const int64_t* ops, int64_t* offsets, int64_t* used_peak) {
     if (cap <= 0 || nops < 0 || (nops > 0 && (!ops || !offsets)) || !used_peak) return ACS_ERR_ARG;
-    acs::Arena A;
-    A.init((size_t)cap);
-    std::vector<int64_t> size_of(nops, 0);
-    for (int k = 0; k < nops; ++k) {
-        if (ops[k] > 0) {
-            size_t off = 0;
-            offsets[k] = A.alloc((size_t)ops[k], &off) ? (int64_t)off : -1;
-            size_of[k] = offsets[k] >= 0 ? ops[k] : 0;
-        } else {
-            const int64_t j = -ops[k] - 1;              // free the block of op j
-            if (j < 0 || j >= k || ops[j] <= 0 || offsets[j] < 0 || size_of[j] == 0) return ACS_ERR_ARG;
-            A.release((size_t)offsets[j], (size_t)size_of[j]);
-            size_of[j] = 0;
-            offsets[k] = -1;
+    return acs::host::no_throw([&]() -> int {
+        acs::Arena A;
+        A.init((size_t)cap);
+        std::vector<int64_t> size_of(nops, 0);
+        for (int k = 0; k < nops; ++k) {
+            if (ops[k] > 0) {
+                size_t off = 0;
+                offsets[k] = A.alloc((size_t)ops[k], &off) ? (int64_t)off : -1;
+                size_of[k] = offsets[k] >= 0 ? ops[k] : 0;
+            } else {
+                const int64_t j = -ops[k] - 1;              // free the block of op j
+                if (j < 0 || j >= k || ops[j] <= 0 || offsets[j] < 0 || size_of[j] == 0) return ACS_ERR_ARG;
+                A.release((size_t)offsets[j], (size_t)size_of[j]);
+                size_of[j] = 0;
+                offsets[k] = -1;
+            }
         }
-    }
-    used_peak[0] = (int64_t)A.used;
-    used_peak[1] = (int64_t)A.peak;
-    return ACS_SOLVED;
+        used_peak[0] = (int64_t)A.used;
+        used_peak[1] = (int64_t)A.peak;
+        return ACS_SOLVED;
+    });
 }
 
 void acs_server_destroy(acs_server* h) {
