@@ -336,3 +336,31 @@ def test_y_is_the_weighted_least_squares_multiplier():
     # and the wrong sign or a missing O would not agree
     y_bad = np.linalg.solve(Ah @ Ah.T, Ah @ (inst.c - r.z))
     assert np.linalg.norm(r.y - y_bad) > 1e-3 * np.linalg.norm(r.y)
+
+
+def test_iterates_follow_a_reordering_of_coordinates_and_cones():
+    """K is a product: reordering the orthant coordinates and the order of the
+    Lorentz cones (moving whole blocks), with the matching columns of A and
+    entries of c, reorders Algorithm 2's iterates the same way (through two
+    rescalings), up to rounding."""
+    inst = I.socp(scale=0.001)
+    A = inst.to_scipy().tocsc()
+    n_orth, dims = inst.n_orth, np.asarray(inst.soc_dims)
+    rng = np.random.default_rng(4)
+    off = C.soc_offsets(n_orth, dims)
+    order = rng.permutation(len(dims))
+    perm = np.concatenate([rng.permutation(n_orth)] +
+                          [np.arange(off[k], off[k + 1]) for k in order]).astype(int)
+    L = alg.Schedule(first=1, period=7)
+    kw = dict(t=1.7, L=L, max_iter=20, tol=0.0, keep_x=20)
+    r0 = alg.algorithm2(A, inst.b, inst.c, n_orth, dims, **kw)
+    r1 = alg.algorithm2(A[:, perm], inst.b, inst.c[perm], n_orth, dims[order], **kw)
+    scale = np.abs(r0.x).max()
+    np.testing.assert_allclose(r1.x, r0.x[perm], atol=1e-9 * scale)
+    np.testing.assert_allclose(r1.z, r0.z[perm], atol=1e-9 * np.abs(r0.z).max())
+    np.testing.assert_allclose(r1.O, r0.O[perm], rtol=1e-9)
+    np.testing.assert_allclose(r1.y, r0.y, atol=1e-9 * np.abs(r0.y).max())
+    # a cone reordered without its coordinates is a different problem
+    r2 = alg.algorithm2(A[:, perm], inst.b, inst.c[perm], n_orth, dims, **kw)
+    if not np.array_equal(dims[order], dims):
+        assert np.abs(r2.x - r0.x[perm]).max() > 1e-6 * scale
