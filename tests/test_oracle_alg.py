@@ -364,3 +364,22 @@ def test_iterates_follow_a_reordering_of_coordinates_and_cones():
     r2 = alg.algorithm2(A[:, perm], inst.b, inst.c[perm], n_orth, dims, **kw)
     if not np.array_equal(dims[order], dims):
         assert np.abs(r2.x - r0.x[perm]).max() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("mu", [1.0, 0.6])
+def test_algorithm2_without_rescaling_is_algorithm1(mu):
+    """With no rescaling after l = 1 (where x = z = e gives o = 1, O = I),
+    Algorithm 2 (one-solve form of d, steps 17-21) is Algorithm 1 (steps 2-6)
+    started from s = x/O - mu O z = (1 - mu) e."""
+    inst = I.socp(scale=0.001)
+    A = inst.to_scipy()
+    for k in (1, 7, 40):
+        r = alg.algorithm2(A, inst.b, inst.c, inst.n_orth, inst.soc_dims, mu=mu, L=alg.NO_SCHEDULE,
+                           max_iter=k, tol=0.0)
+        assert np.all(r.O == 1.0)
+        e = C.cone_identity(inst.n, inst.n_orth, inst.soc_dims)
+        x, z, s, p, d = alg.algorithm1(A, inst.b, inst.c, inst.n_orth, inst.soc_dims, mu=mu,
+                                       s0=(1.0 - mu) * e, iters=k)
+        np.testing.assert_allclose(r.s, s, atol=1e-10 * (1 + np.abs(s).max()))
+        np.testing.assert_allclose(r.x, x, atol=1e-10 * (1 + np.abs(x).max()))
+        np.testing.assert_allclose(r.z, z, atol=1e-10 * (1 + np.abs(z).max()))
