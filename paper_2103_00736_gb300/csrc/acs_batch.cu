@@ -273,11 +273,13 @@ int prepare_members(Batch* B, int count, const acs_instance* members, int* bad) 
                 const int j = I.share_A_with;
                 if (j >= i || I.m != members[j].m || I.n != members[j].n) { rc[i] = ACS_ERR_ARG; continue; }
                 int root = j;                            // the member that holds the data
-                while (members[root].share_A_with >= 0) {
-                    // a link that does not point back fails an earlier member,
-                    // which is the one reported
-                    if (members[root].share_A_with >= root) { rc[i] = ACS_ERR_ARG; break; }
-                    root = members[root].share_A_with;
+                while (members[root].share_A_with != -1) {
+                    // a link that does not point back, or an invalid one, fails
+                    // an earlier member, which is the one reported; its arrays
+                    // are not read here
+                    const int up = members[root].share_A_with;
+                    if (up < -1 || up >= root) { rc[i] = ACS_ERR_ARG; break; }
+                    root = up;
                 }
                 if (rc[i] != ACS_SOLVED) continue;
                 rc[i] = host::validate(I.m, I.n, members[root].row_ptr, members[root].col, members[root].val,

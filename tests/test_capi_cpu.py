@@ -233,3 +233,38 @@ def test_batch_host_image_is_deterministic_and_checked(capi):
             with pytest.raises(capi.AcsError) as e:
                 fn(members)
             assert (e.value.code, e.value.member) == (code, where), fn
+
+
+def test_batch_share_chains_through_invalid_members(capi):
+    """A member that shares the A of an invalid member: the invalid one is
+    reported (it comes first), and its arrays are never read."""
+    from paper_2103_00736_gb300 import capi as c
+    import ctypes as C
+    from paper_2103_00736_gb300 import instances as I
+    good = I.bernoulli_lp(11, 6, 15, density=0.3)
+    count = 80
+    arr = (c.acs_instance * count)()
+    keep = []
+    for i in range(count):
+        rp = np.ascontiguousarray(good.row_ptr, np.int64)
+        cl = np.ascontiguousarray(good.col, np.int32)
+        vl = np.ascontiguousarray(good.val, np.float64)
+        b = np.ascontiguousarray(good.b, np.float64)
+        cc = np.ascontiguousarray(good.c, np.float64)
+        keep += [rp, cl, vl, b, cc]
+        a = arr[i]
+        a.m, a.n = good.m, good.n
+        a.row_ptr, a.col, a.val = c._ptr(rp, C.c_int64), c._ptr(cl, C.c_int32), c._ptr(vl, C.c_double)
+        a.b, a.c = c._ptr(b, C.c_double), c._ptr(cc, C.c_double)
+        a.n_orthant, a.n_soc, a.soc_dims = good.n, 0, None
+        a.share_A_with = -1
+    # member 40: an invalid share index and a row pointer that must not be read
+    arr[40].share_A_with = -7
+    arr[40].row_ptr = C.cast(C.c_void_p(16), C.POINTER(C.c_int64))
+    arr[70].share_A_with = 40                 # shares with the invalid member
+    h, bad = C.c_void_p(), C.c_int32(-1)
+    hh, nb = C.c_uint64(), C.c_int64()
+    rc = c.lib().acs_debug_batch_image(count, arr, None, C.byref(hh), C.byref(nb), C.byref(bad))
+    assert (rc, bad.value) == (c.ERR_ARG, 40)
+    rc = c.lib().acs_batch_create(count, arr, None, None, C.byref(h), C.byref(bad))
+    assert (rc, bad.value) == (c.ERR_ARG, 40) and not h.value
