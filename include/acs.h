@@ -231,6 +231,11 @@ int acs_debug_barrier_timeout(acs_problem* p, double* waited_ms);
  * g, stored entries}; perm[m], sptr[slices + 1], slen[slices] (chunks of 32
  * entries per slice), col / val[stored] are written where not NULL (call
  * once with NULL arrays for the sizes).  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
+/* Host-only check of the BF16 storage of A (a_storage = ACS_STORE_BF16):
+ * out[k] = the BF16 bit pattern stored for the finite value v[k], i.e. its
+ * FP32 value rounded to the nearest BF16 value, ties to even.  Errors:
+ * ACS_ERR_ARG. */
+int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out);
 int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                    int32_t which, int64_t warps, int32_t* info, int32_t* perm, int32_t* sptr, int32_t* slen,
                    int32_t* out_col, double* out_val);

@@ -136,6 +136,7 @@ def lib():
         L.acs_debug_assign_teams.argtypes = [C.c_int32, dp, C.c_int32, ip]
         L.acs_debug_batch_image.argtypes = [C.c_int32, C.POINTER(acs_instance), C.POINTER(acs_settings),
                                              C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.acs_debug_to_bf16.argtypes = [C.c_int64, dp, C.POINTER(C.c_uint16)]
         L.acs_debug_sell.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, C.c_int32, C.c_int64,
                                      ip, ip, ip, ip, ip, dp]
         L.acs_debug_arena.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -815,3 +816,13 @@ def acs_debug_batch_image(instances, settings=None, share=None):
         err.member = bad.value
         raise err
     return h.value, nbytes.value
+
+
+def acs_debug_to_bf16(v) -> np.ndarray:
+    """uint16 BF16 patterns the library stores for the values v (host-only check)."""
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(a.size, dtype=np.uint16)
+    rc = lib().acs_debug_to_bf16(int(a.size), _ptr(a, C.c_double), _ptr(out, C.c_uint16))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_to_bf16")
+    return out

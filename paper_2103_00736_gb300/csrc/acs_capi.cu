@@ -370,6 +370,12 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
     });
 }
 
+int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out) {
+    if (n < 0 || (n > 0 && (!v || !out))) return ACS_ERR_ARG;
+    for (int64_t k = 0; k < n; ++k) out[k] = acs::host::to_bf16(v[k]);
+    return ACS_SOLVED;
+}
+
 int acs_last_launch_ms(acs_problem* h, double* ms) {
     Problem* P = reinterpret_cast<Problem*>(h);
     if (!P || !ms) return ACS_ERR_ARG;

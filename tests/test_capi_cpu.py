@@ -268,3 +268,29 @@ def test_batch_share_chains_through_invalid_members(capi):
     assert (rc, bad.value) == (c.ERR_ARG, 40)
     rc = c.lib().acs_batch_create(count, arr, None, None, C.byref(h), C.byref(bad))
     assert (rc, bad.value) == (c.ERR_ARG, 40) and not h.value
+
+
+def _bf16_value(t):
+    """The float value of BF16 pattern(s) t (upper half of an FP32)."""
+    return (np.asarray(t, np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_bf16_storage_rounds_to_nearest_even(capi):
+    """The stored BF16 value of x is the BF16 value nearest to its FP32 value,
+    ties to the even pattern (checked against both neighbours, not by
+    repeating the bit trick)."""
+    rng = np.random.default_rng(17)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000),
+                        [0.0, -0.0, 1.0, -1.0, 3.0, 1e-40, -1e-40]])
+    f = x.astype(np.float32)
+    lo = (f.view(np.uint32) >> 16).astype(np.uint32)         # truncation toward zero in magnitude
+    hi = lo + 1
+    d_lo = np.abs(_bf16_value(lo) - f.astype(np.float64))
+    d_hi = np.abs(_bf16_value(hi) - f.astype(np.float64))
+    want = np.where(d_lo < d_hi, lo, np.where(d_hi < d_lo, hi, np.where(lo % 2 == 0, lo, hi)))
+    got = capi.acs_debug_to_bf16(x)
+    assert np.array_equal(got, want.astype(np.uint16))
+    # exact ties (low half 0x8000) go to the even pattern, both ways
+    ties = (np.array([0x3F808000, 0x3F818000, 0xBF808000, 0xC0418000], np.uint32)).view(np.float32)
+    got = capi.acs_debug_to_bf16(ties.astype(np.float64))
+    assert list(got) == [0x3F80, 0x3F82, 0xBF80, 0xC042]
