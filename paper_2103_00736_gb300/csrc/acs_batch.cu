@@ -274,11 +274,16 @@ int prepare_members(Batch* B, int count, const acs_instance* members, int* bad) 
                 if (j >= i || I.m != members[j].m || I.n != members[j].n) { rc[i] = ACS_ERR_ARG; continue; }
                 int root = j;                            // the member that holds the data
                 while (members[root].share_A_with != -1) {
-                    // a link that does not point back, or an invalid one, fails
-                    // an earlier member, which is the one reported; its arrays
-                    // are not read here
+                    // a link that does not point back, an invalid one, or one to
+                    // a member of other dimensions fails an earlier member, which
+                    // is the one reported; the arrays along the chain are not
+                    // read here (a member of other dimensions has arrays of
+                    // other lengths)
                     const int up = members[root].share_A_with;
-                    if (up < -1 || up >= root) { rc[i] = ACS_ERR_ARG; break; }
+                    if (up < -1 || up >= root || members[up].m != I.m || members[up].n != I.n) {
+                        rc[i] = ACS_ERR_ARG;
+                        break;
+                    }
                     root = up;
                 }
                 if (rc[i] != ACS_SOLVED) continue;

@@ -26,12 +26,10 @@ constexpr int kMaxN = 1 << 20;                 // largest n accepted (1,048,576)
 constexpr int kMaxBlocks = 1024;               // grid size of the two reduction kernels
 constexpr int kVals = 8;                       // partials per block
 constexpr int kThreadsNA = 256;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_noalloc_scratch[kMaxN + kMaxBlocks * kVals];
 
 std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 __device__ __forceinline__ double warp_sum_na(double x) {
 #pragma unroll
@@ -139,23 +137,20 @@ __global__ void finish_kernel(int nb_rows, int nb_cols, const double* prow, cons
     out[5] = by;
 }
 
-// Device address of the scratch array for the current device, looked up once.
+// Device address of the scratch array in the current device's context,
+// looked up on every call: a lookup is a host-side table query that
+// allocates nothing, and a cached address would outlive the context it
+// belongs to (after cudaDeviceReset the module is loaded again elsewhere).
+// The first lookup in a context loads the module; the lock keeps concurrent
+// first calls from racing in the runtime's lazy loading.
 double* scratch_for_current_device(int* err) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    double* p = nullptr;
+    if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) {
         *err = ACS_ERR_CUDA;
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        double* p = nullptr;
-        if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            *err = ACS_ERR_CUDA;
-            return nullptr;
-        }
-        g_scratch_ptr[dev] = p;
-    }
-    return g_scratch_ptr[dev];
+    return p;
 }
 
 }  // namespace
@@ -168,15 +163,19 @@ extern "C" int acs_kkt_residuals_noalloc(int32_t m, int32_t n, const int32_t* ro
         n_orthant < 0 || n_soc < 0 || (n_soc > 0 && !soc_offsets) || n_orthant > n)
         return ACS_ERR_ARG;
     if (n > kMaxN) return ACS_ERR_LIMIT;
+    // an error left by an earlier, unrelated launch is not this call's
+    cudaGetLastError();
     int err = ACS_SOLVED;
     double* scratch = scratch_for_current_device(&err);
     if (!scratch) return err;
     double* aty = scratch;
     double* prow = scratch + kMaxN;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int nb_rows = (m + kThreadsNA - 1) / kThreadsNA < kMaxBlocks / 2 ? (m + kThreadsNA - 1) / kThreadsNA : kMaxBlocks / 2;
-    const int nb_cols_n = (n + kThreadsNA - 1) / kThreadsNA;
-    const int nb_cols = nb_cols_n < kMaxBlocks / 2 ? nb_cols_n : kMaxBlocks / 2;
+    // block counts in 64-bit arithmetic (m + kThreadsNA - 1 may exceed INT32_MAX)
+    const long long rows_need = ((long long)m + kThreadsNA - 1) / kThreadsNA;
+    const long long cols_need = ((long long)n + kThreadsNA - 1) / kThreadsNA;
+    const int nb_rows = (int)(rows_need < kMaxBlocks / 2 ? rows_need : kMaxBlocks / 2);
+    const int nb_cols = (int)(cols_need < kMaxBlocks / 2 ? cols_need : kMaxBlocks / 2);
     double* pcol = prow + (kMaxBlocks / 2) * kVals;
     if (cudaMemsetAsync(aty, 0, sizeof(double) * (size_t)n, st) != cudaSuccess) return ACS_ERR_CUDA;
     rows_kernel<<<nb_rows, kThreadsNA, 0, st>>>(m, row_ptr, col, val, b, x, y, aty, prow);

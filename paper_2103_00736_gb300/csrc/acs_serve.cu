@@ -290,13 +290,17 @@ void retire(Server* S, Request* R, const Control& C) {
     R->x.resize(M.n);
     R->s.resize(M.n);
     std::vector<double> w(M.m);
-    cudaMemcpyAsync(R->x.data(), M.x, sizeof(double) * M.n, cudaMemcpyDeviceToHost, S->stream);
-    cudaMemcpyAsync(R->s.data(), M.z, sizeof(double) * M.n, cudaMemcpyDeviceToHost, S->stream);
-    cudaMemcpyAsync(w.data(), M.X.w, sizeof(double) * M.m, cudaMemcpyDeviceToHost, S->stream);
-    cudaStreamSynchronize(S->stream);
+    // a copy that fails leaves the host results undefined: the request then
+    // reports the CUDA error instead of its device-side status
+    cudaError_t e = cudaMemcpyAsync(R->x.data(), M.x, sizeof(double) * M.n, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R->s.data(), M.z, sizeof(double) * M.n, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.data(), M.X.w, sizeof(double) * M.m, cudaMemcpyDeviceToHost, S->stream);
+    const cudaError_t es = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = es;
     R->y.resize(M.m);
     for (int r = 0; r < M.m; ++r) R->y[R->X.H.perm[r]] = w[r] / S->set.mu;
-    R->status = member_status(C);
+    R->status = e == cudaSuccess ? member_status(C) : ACS_ERR_CUDA;
     R->iters = C.l;
     for (int k = 0; k < 6; ++k) R->res[k] = C.res[k];
     R->res[6] = (double)C.cg_iters;

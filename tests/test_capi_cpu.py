@@ -270,6 +270,60 @@ def test_batch_share_chains_through_invalid_members(capi):
     assert (rc, bad.value) == (c.ERR_ARG, 40) and not h.value
 
 
+_CHAIN_CHILD = r"""
+import ctypes as C, mmap, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2103_00736_gb300 import capi as c, instances as I
+small = I.bernoulli_lp(11, 5, 12, density=0.4)          # m = 5: row_ptr has 6 entries
+big = I.bernoulli_lp(12, 10, 12, density=0.4)           # m = 10, same n
+PAGE = mmap.PAGESIZE
+buf = mmap.mmap(-1, 2 * PAGE, prot=mmap.PROT_READ | mmap.PROT_WRITE)
+base = C.addressof(C.c_char.from_buffer(buf))
+libc = C.CDLL(None)
+libc.mprotect.argtypes = [C.c_void_p, C.c_size_t, C.c_int]
+# member 0's row pointer ends where a page that must not be read begins
+rp_addr = base + PAGE - 8 * (small.m + 1)
+C.memmove(rp_addr, np.ascontiguousarray(small.row_ptr, np.int64).ctypes.data, 8 * (small.m + 1))
+assert libc.mprotect(base + PAGE, PAGE, 0) == 0
+keep = []
+arr = (c.acs_instance * 3)()
+for i, x in enumerate((small, big, big)):
+    cl = np.ascontiguousarray(x.col, np.int32); vl = np.ascontiguousarray(x.val, np.float64)
+    b = np.ascontiguousarray(x.b, np.float64); cc = np.ascontiguousarray(x.c, np.float64)
+    rp = np.ascontiguousarray(x.row_ptr, np.int64)
+    keep += [cl, vl, b, cc, rp]
+    a = arr[i]
+    a.m, a.n = x.m, x.n
+    a.row_ptr = C.cast(C.c_void_p(rp_addr), C.POINTER(C.c_int64)) if i == 0 else c._ptr(rp, C.c_int64)
+    a.col, a.val = c._ptr(cl, C.c_int32), c._ptr(vl, C.c_double)
+    a.b, a.c = c._ptr(b, C.c_double), c._ptr(cc, C.c_double)
+    a.n_orthant, a.n_soc, a.soc_dims = x.n, 0, None
+    a.share_A_with = -1
+arr[1].share_A_with = 0      # invalid: member 0 has other dimensions
+arr[2].share_A_with = 1      # passes the direct check; the chain leads to member 0
+bad = C.c_int32(-1)
+hh, nb = C.c_uint64(), C.c_int64()
+rc = c.lib().acs_debug_batch_image(3, arr, None, C.byref(hh), C.byref(nb), C.byref(bad))
+print("RESULT", rc, bad.value)
+"""
+
+
+def test_batch_share_chain_of_other_dimensions(capi):
+    """A chain 2 -> 1 -> 0 whose middle link has other dimensions than its
+    ends: member 1 is reported, and member 2's check stops at the link
+    instead of reading member 0's arrays with member 2's sizes (member 0's
+    row pointer ends at a page that may not be read; the check runs in a
+    child process, so a read past it would show as a crash)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CHAIN_CHILD, root], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")][-1].split()
+    assert (int(line[1]), int(line[2])) == (capi.ERR_ARG, 1)
+
+
 def _bf16_value(t):
     """The float value of BF16 pattern(s) t (upper half of an FP32)."""
     return (np.asarray(t, np.uint32) << 16).view(np.float32).astype(np.float64)

@@ -4,9 +4,10 @@ Callers that cannot allocate device memory (code running inside another
 framework's memory pool, under a fixed memory budget, or in a loop that must
 not enter the allocator) pass every input and the output in device memory
 they own; the entry point keeps its temporaries in a fixed device array.  This
-file checks it through the C ABI against the residuals the solver itself
-reports (acs_get), on several calls in a row, so that a call that fails to
-clear the shared array would show up.  It is collected last on purpose.
+file checks it through the C ABI, on several calls in a row (a call that
+failed to clear the shared array would show up), against the residuals the
+solver itself reports (acs_get) and against the FP64 CPU oracle's residual
+function evaluated on the same point.  It is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -16,6 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2103_00736_gb300 import capi, instances as I  # noqa: E402
+from oracle import kkt  # noqa: E402
 
 
 def _dev(a, dtype):
@@ -46,6 +48,13 @@ def _solve_and_compare(inst, **settings):
         assert abs(got[k] - res[k]) <= 1e-9 + 1e-6 * res[k], (k, got[k], res[k])
     for k in (4, 5):                        # c'x, b'y
         assert abs(got[k] - res[k]) <= 1e-9 * (1.0 + abs(res[k])), (k, got[k], res[k])
+    ref = kkt.residuals(inst.to_scipy(), inst.b, inst.c, x, y, z, inst.n_orth, inst.soc_dims)
+    for k, key in enumerate(("r_p", "r_d", "r_gap", "r_cone")):
+        # FP64 sums in another order: the residuals are differences of large
+        # terms, so their last few digits are rounding
+        assert abs(got[k] - ref[key]) <= 1e-12 + 1e-6 * ref[key], (key, got[k], ref[key])
+    for k, key in ((4, "obj_p"), (5, "obj_d")):
+        assert abs(got[k] - ref[key]) <= 1e-12 * (1.0 + abs(ref[key])), (key, got[k], ref[key])
     return got
 
 
