@@ -407,6 +407,19 @@ def dist_info():
     return rank, world, local
 
 
+PRECISIONS = {"mixed": 0, "fp32": 1, "fp64": 2}
+
+
+def solver_overrides(args) -> dict:
+    """Settings chosen on the command line (precision mode, column blocks)."""
+    out = {}
+    if args.precision is not None:
+        out["precision"] = PRECISIONS[args.precision]
+    if args.col_block is not None:
+        out["col_block"] = args.col_block
+    return out
+
+
 def gpu_arm(args) -> None:
     import numpy as np
     import torch
@@ -424,10 +437,12 @@ def gpu_arm(args) -> None:
     # a dedicated stream: the library launches on it and the events below time it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    settings = capi.acs_settings_default(cuda_stream=stream.cuda_stream, device=local, **wl["settings"])
+    settings = capi.acs_settings_default(cuda_stream=stream.cuda_stream, device=local, **wl["settings"],
+                                         **solver_overrides(args))
     h = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
                                 inst.n_orth, inst.soc_dims, settings)
     info = capi.acs_problem_info(h)
+    layout = capi.acs_debug_layout(h)
 
     tol, max_iter = args.tol, args.max_iter
     expect = capi.SOLVED if tol > 0 else capi.MAX_ITER
@@ -442,6 +457,8 @@ def gpu_arm(args) -> None:
         raise RuntimeError(f"warm-up solve did not converge: {capi.acs_status_string(st)} {res}")
     counters = capi.acs_debug_counters(h)
     launch_ms_warm = capi.acs_last_launch_ms(h)
+    phases = capi.acs_debug_phase_times(h) if args.phases else None
+    passes = capi.acs_debug_pass_counts(h)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -536,7 +553,11 @@ def gpu_arm(args) -> None:
             "e2e": e2e,
             "gpu_launches": 6 * args.steps,
             "cpu_baseline": cpu,
+            "layout": layout,
+            "passes": passes,
         }
+        if phases is not None:
+            line["phases_ms"] = phases
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -842,6 +863,11 @@ def main():
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--round-ms", type=float, default=2.0)
     ap.add_argument("--clients", type=int, default=4)
+    ap.add_argument("--precision", default=None, choices=sorted(PRECISIONS),
+                    help="solver precision mode (default: the library's)")
+    ap.add_argument("--col-block", type=int, default=None,
+                    help="column-block width limit of the FP32 passes (-1: off; default: the library's)")
+    ap.add_argument("--phases", action="store_true", help="add the per-phase device times of a warm-up solve")
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.workload, args.cpu_iters)), flush=True)

@@ -52,7 +52,7 @@ enum {
     ACS_ERR_LIMIT = -9       /* a size exceeds a fixed limit of the entry point     */
 };
 
-enum { ACS_PREC_MIXED = 0, ACS_PREC_FP64 = 2 };
+enum { ACS_PREC_MIXED = 0, ACS_PREC_FP32 = 1, ACS_PREC_FP64 = 2 };
 
 typedef struct acs_problem acs_problem;
 
@@ -71,7 +71,14 @@ typedef struct {
                                 projection solve by an FP32 correction CG (mixed-precision
                                 refinement), handed over to an FP64 correction CG for the
                                 rest of the solve if the FP32 one cannot reach the accuracy
-                                the iteration needs; ACS_PREC_FP64: FP64 correction CG      */
+                                the iteration needs; ACS_PREC_FP32: as MIXED, and the two
+                                matrix products of the outer iteration (the projection
+                                residual b_tilde - A_hat (p + q) and the update's A_hat' w)
+                                are FP32 column-blocked passes too until every KKT residual
+                                is <= outer32_tol or stops falling, after which they are FP64
+                                (the polish that finishes the solve); needs the column-
+                                blocked layout (col_block >= 0, FP32 storage, CG projection),
+                                else it runs as MIXED; ACS_PREC_FP64: FP64 correction CG     */
     double cg_eta;           /* inexact projection: CG stops once its error estimate
                                 sqrt(r' J^-1 r) <= eta * ||s_l - s_{l-1}||, eta starting at
                                 cg_eta (default 0.3) and shrunk tenfold whenever the step
@@ -110,6 +117,17 @@ typedef struct {
                                 nearest even; the FP64 passes -- residual of the projection
                                 system, update, KKT -- still read the FP64 values, so the
                                 refinement converges to the same FP64 iterate)                 */
+    int32_t col_block;       /* FP32 matrix passes of acs_solve (single-problem launch): the
+                                columns are cut into blocks whose FP32 vector entries fit one
+                                CTA's shared memory, and every pass gathers from the staged
+                                block instead of from L2; each row's partial sums are added in
+                                block order.  0: blocks of at most 49152 columns; k > 0: at
+                                most k columns (smaller blocks, for tests); -1 (default): off,
+                                every pass gathers from L2 (the batched launch's layout).
+                                Not used with a_storage = ACS_STORE_BF16 or when the cached
+                                operator runs from the first iteration                         */
+    double outer32_tol;      /* ACS_PREC_FP32: KKT level at which the outer products return
+                                to FP64; default 1e-5                                          */
 } acs_settings;
 
 enum { ACS_STORE_FP32 = 0, ACS_STORE_BF16 = 1 };
@@ -206,8 +224,10 @@ int acs_last_launch_ms(acs_problem* p, double* ms);
  * the device's global timer, barrier wait included) and how often it ran, in
  * the order: rescale-o, rescale-apply, b_tilde, q-refresh, abs_K, CG-rhs,
  * CG A' pass, CG A pass, CG vector step, update, KKT, cached-operator
- * factorisation, cached-operator correction.  n >= 13.  Returns the number of
- * phases written or an error. */
+ * factorisation, cached-operator correction, and for the column-blocked
+ * passes the three phases that add up their partial sums: t = O^2 A'u of
+ * the CG, the projection residual and the update of the FP32 outer passes.
+ * n >= 16.  Returns the number of phases written or an error. */
 int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t n);
 /* Mean time (ns) of one grid-wide reduce-and-barrier of the persistent
  * kernel's launch shape, over n back-to-back barriers. */
@@ -239,6 +259,68 @@ int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out);
 int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                    int32_t which, int64_t warps, int32_t* info, int32_t* perm, int32_t* sptr, int32_t* slen,
                    int32_t* out_col, double* out_val);
+/* Host-only check of the column-blocked image acs_problem_create builds for
+ * the FP32 passes (setting col_block): of the relabelled A (which = 0) or of
+ * A' (which = 1), with blocks of at most width_limit (>= 4) columns, its
+ * items dealt to `ctas` CTAs.  The columns are cut into nblocks blocks of
+ * `width` columns (the last may be shorter); item = block * nsl + slice, a
+ * slice being 32 rows; lane r of an item holds row
+ * (slice / 64) * 2048 + rowid[item * 32 + r] (0xFFFF: no row), the rows of
+ * each window of 2048 sorted by decreasing count of entries in the block
+ * (stable); entry k of that row sits at sptr[item] + 32 k + r with the column
+ * out_col - block * width and the FP32 value out_val; padding has column 0
+ * and value 0; every item has at least one chunk of 32 entries, and bit
+ * c mod 32 of cend[c / 32] is set exactly when chunk c (entries 32c ..
+ * 32c + 31) is the last chunk of its item.  Items [cta_beg[c], cta_beg[c + 1])
+ * go to CTA c.  info[6] = {rows, columns, width, nblocks, nsl, stored
+ * entries}; perm[m] (the row relabelling, as acs_debug_sell),
+ * sptr[nblocks * nsl + 1], rowid[32 * nblocks * nsl], out_col /
+ * out_val[stored], cta_beg[ctas + 1], cend[stored / 1024 + 2] are written
+ * where not NULL.  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
+int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                     int32_t which, int32_t width_limit, int32_t ctas, int64_t* info, int32_t* perm,
+                     int32_t* sptr, uint16_t* rowid, uint16_t* out_col, float* out_val, int32_t* cta_beg,
+                     uint32_t* cend);
+/* Pass counters of the last solve: out[12] = {FP32 CG A passes, FP32 CG A'
+ * passes, FP64 A passes, FP64 A' passes, rescalings, KKT checks, FP32 outer
+ * A passes, FP32 outer A' passes, iteration at which the FP32 outer passes
+ * ended (0 = never ran or did not end), iterations, CG iterations, iteration
+ * of the FP32-to-FP64 CG hand-over}; n >= 12.  Waits for queued work.
+ * acs_debug_layout: out[10] = {column-blocked layout in use, blocks of A,
+ * width, stored entries, blocks of A', width, stored entries, dynamic shared
+ * memory of the FP32 launch (bytes), stored entries of the sliced-ELLPACK A
+ * and A'}; n >= 10.  Both return the number of values written or an error. */
+int acs_debug_pass_counts(acs_problem* p, int64_t* out, int32_t n);
+int acs_debug_layout(acs_problem* p, int64_t* out, int32_t n);
+
+/* Benchmarks (not part of a solve).
+ * acs_bench_passes: device time (us) of one phase of the persistent kernel
+ * on the problem's data, repeated `reps` times, each followed by a grid
+ * barrier of the solve's launch shape (kind 9 times the barrier alone).
+ * Kinds: 0 column-blocked A' pass of the CG (partial sums of A'u), 1 its
+ * combine (t = O^2 A'u and u'Mu), 2 column-blocked A pass, 3 CG vector step
+ * with the A pass's combine, 4 / 5 / 6 the same CG phases on the L2-gather
+ * layout (FP32 values; only with col_block = -1), 7 FP64 projection-residual
+ * pass over A, 8 FP64 pass over A', 9 barrier, 10 abs_K, 11 KKT residuals,
+ * 12 / 13 FP32 outer projection residual (pass, combine), 14 / 15 FP32 outer
+ * update (pass, combine), 16 / 17 the staging of the column-blocked A pass
+ * alone (from an FP32 / an FP64 vector), 18 the column-blocked A' pass without
+ * its gathers, 19 without its staging, 20 / 21 each CTA's entries of the A'
+ * image read as one linear stream (columns and values / values only)
+ * (diagnostics: the values they produce are meaningless).  smem_bytes: dynamic shared memory of the launch
+ * (< 0: the solve's; more shrinks the L1 cache the same way a wider block
+ * would; at least the solve's, except for kinds 18, 20 and 21, which read no
+ * shared memory);
+ * at most 196608.  The iterate state is left undefined: the next
+ * acs_solve starts from x = z = e.  Errors: ACS_ERR_ARG, ACS_ERR_CUDA.
+ * acs_bench_gather: random 4-byte gathers per second over the whole device
+ * from a vector of `entries` floats (a power of two, 32 .. 2^24): mode 0
+ * default loads, 1 L2-only loads, 2 read-only path, 3 from a copy in shared
+ * memory (entries <= 49152); one CTA of 1024 threads per SM, 8 independent
+ * gathers in flight per thread, `steps` rounds.  Allocates and frees its own
+ * device buffers.  Errors: ACS_ERR_ARG, ACS_ERR_OOM, ACS_ERR_CUDA. */
+int acs_bench_passes(acs_problem* p, int32_t kind, int32_t reps, int32_t smem_bytes, double* us_per_rep);
+int acs_bench_gather(int32_t device, int64_t entries, int32_t mode, int32_t steps, double* gathers_per_s);
 
 /*
  * KKT residuals of a caller-supplied point, for callers that cannot allocate
@@ -256,12 +338,21 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
  *   b[m], c[n], x[n], y[m], z[n] : DEVICE vectors (z is the dual slack).
  *   n_orthant, n_soc, soc_offsets : cones as in acs_problem_create, with
  *                     soc_offsets a DEVICE int32[n_soc+1] array of absolute
- *                     start offsets (soc_offsets[0] = n_orthant, last = n).
+ *                     start offsets (soc_offsets[0] = n_orthant, increasing,
+ *                     last = n).  The offsets live on the device and are not
+ *                     checked (that would need a copy back to the host): a
+ *                     malformed array makes the kernels read x and z out of
+ *                     bounds.  Likewise row_ptr and col must describe a valid
+ *                     CSR of A with columns in [0, n).
  *   residuals       : DEVICE double[6], written asynchronously.
  *   cuda_stream     : stream to run on (NULL = legacy default stream).
  * The call is asynchronous: results are ready when the stream reaches them.
- * The first call on a device looks up the array's device address (once per
- * device, under a lock); make that first call before any stream capture.
+ * Every call looks up the array's device address in the current context (a
+ * host-side query that allocates nothing; the first one in a context loads
+ * the library's device code), so the entry point stays valid after
+ * cudaDeviceReset; make the first call in a context before any stream
+ * capture.  An error left by an earlier, unrelated launch is cleared at the
+ * start of the call and not reported by it.
  * Every call clears the part of the array it accumulates into; calls that
  * overlap on the GPU share the array and race, so order them.  The A'y part
  * is accumulated with atomic adds, so r_d may differ in its last bits from
@@ -365,7 +456,7 @@ int acs_batch_counters(acs_batch* b, long long* out);
 int acs_batch_member_ms(acs_batch* b, double* ms);
 
 /* Per-phase device times (ms) and counts of member i's last solve, or summed
- * over all members for i = -1, in the order of acs_debug_phase_times; n >= 13.
+ * over all members for i = -1, in the order of acs_debug_phase_times; n >= 16.
  * Returns the number of phases written or an error. */
 int acs_batch_phase_ms(acs_batch* b, int32_t i, double* ms, long long* count, int32_t n);
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libacs.so")
 SOLVED, MAX_ITER = 0, 1
 ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
 ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
-PREC_MIXED, PREC_FP64 = 0, 2
+PREC_MIXED, PREC_FP32, PREC_FP64 = 0, 1, 2
 PROJ_AUTO, PROJ_CG, PROJ_DENSE = 0, 1, 2
 STORE_FP32, STORE_BF16 = 0, 1
 
@@ -47,6 +47,8 @@ class acs_settings(C.Structure):
         ("dense_switch_cg", C.c_int32),
         ("extrapolation", C.c_double),
         ("a_storage", C.c_int32),
+        ("col_block", C.c_int32),
+        ("outer32_tol", C.c_double),
     ]
 
 
@@ -141,6 +143,14 @@ def lib():
                                      ip, ip, ip, ip, ip, dp]
         L.acs_debug_arena.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64)]
+        u16p = C.POINTER(C.c_uint16)
+        L.acs_debug_cbsell.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, C.c_int32, C.c_int32,
+                                       C.c_int32, C.POINTER(C.c_int64), ip, ip, u16p, u16p,
+                                       C.POINTER(C.c_float), ip, C.POINTER(C.c_uint32)]
+        L.acs_debug_pass_counts.argtypes = [P, C.POINTER(C.c_int64), C.c_int32]
+        L.acs_debug_layout.argtypes = [P, C.POINTER(C.c_int64), C.c_int32]
+        L.acs_bench_passes.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, dp]
+        L.acs_bench_gather.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_int32, dp]
         L.acs_server_destroy.restype = None
         L.acs_batch_destroy.restype = None
         _lib = L
@@ -289,7 +299,8 @@ def acs_debug_counters(h) -> np.ndarray:
 
 
 PHASES = ("rescale_o", "rescale_apply", "b_tilde", "q_refresh", "abs_K", "cg_rhs", "cg_At",
-          "cg_A", "cg_vec", "update", "kkt", "dense_factor", "dense_solve")
+          "cg_A", "cg_vec", "update", "kkt", "dense_factor", "dense_solve", "cg_tcomb", "rhs_comb",
+          "update_comb")
 
 
 def acs_debug_phase_times(h) -> dict:
@@ -785,6 +796,61 @@ def acs_debug_sell(m, n, row_ptr, col, val, which: int, warps: int) -> dict:
                 col=oc[:stored], val=ov[:stored])
 
 
+def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas: int) -> dict:
+    """The column-blocked image of the relabelled A (which=0) or of A'
+    (which=1) that acs_problem_create builds for the FP32 passes (host-only
+    check)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    info = np.zeros(6, dtype=np.int64)
+    args = (int(m), int(n), _ptr(rp, C.c_int64), _ptr(ci, C.c_int32), _ptr(va, C.c_double), int(which),
+            int(width_limit), int(ctas))
+    rc = lib().acs_debug_cbsell(*args, _ptr(info, C.c_int64), None, None, None, None, None, None, None)
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_cbsell")
+    rows, cols, width, nblocks, nsl, stored = (int(v) for v in info)
+    items = nblocks * nsl
+    perm = np.zeros(m, dtype=np.int32)
+    sptr = np.zeros(items + 1, dtype=np.int32)
+    rowid = np.zeros(items * 32, dtype=np.uint16)
+    oc = np.zeros(max(stored, 1), dtype=np.uint16)
+    ov = np.zeros(max(stored, 1), dtype=np.float32)
+    cta = np.zeros(ctas + 1, dtype=np.int32)
+    cend = np.zeros(stored // 1024 + 2, dtype=np.uint32)
+    rc = lib().acs_debug_cbsell(*args, _ptr(info, C.c_int64), _ptr(perm, C.c_int32), _ptr(sptr, C.c_int32),
+                                _ptr(rowid, C.c_uint16), _ptr(oc, C.c_uint16), _ptr(ov, C.c_float),
+                                _ptr(cta, C.c_int32), _ptr(cend, C.c_uint32))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_cbsell")
+    return dict(rows=rows, cols=cols, width=width, nblocks=nblocks, nsl=nsl, stored=stored, perm=perm,
+                sptr=sptr, rowid=rowid, col=oc[:stored], val=ov[:stored], cta_beg=cta, cend=cend)
+
+
+PASS_COUNTS = ("cg_A", "cg_At", "fp64_A", "fp64_At", "rescalings", "checks", "fp32_outer_A",
+               "fp32_outer_At", "outer32_end", "iterations", "cg_iterations", "cg_switch_at")
+
+
+def acs_debug_pass_counts(h) -> dict:
+    out = np.zeros(16, dtype=np.int64)
+    rc = lib().acs_debug_pass_counts(C.c_void_p(h), _ptr(out, C.c_int64), 16)
+    if rc < 0:
+        raise AcsError(rc, "acs_debug_pass_counts")
+    return {k: int(out[i]) for i, k in enumerate(PASS_COUNTS)}
+
+
+LAYOUT = ("col_blocked", "A_blocks", "A_width", "A_stored", "At_blocks", "At_width", "At_stored",
+          "dyn_smem", "sell_A_stored", "sell_At_stored")
+
+
+def acs_debug_layout(h) -> dict:
+    out = np.zeros(16, dtype=np.int64)
+    rc = lib().acs_debug_layout(C.c_void_p(h), _ptr(out, C.c_int64), 16)
+    if rc < 0:
+        raise AcsError(rc, "acs_debug_layout")
+    return {k: int(out[i]) for i, k in enumerate(LAYOUT)}
+
+
 def acs_debug_batch_image(instances, settings=None, share=None):
     """(FNV-1a hash, bytes) of the host image acs_batch_create would upload
     (host-only check); raises AcsError (with .member) like acs_batch_create."""
@@ -826,3 +892,28 @@ def acs_debug_to_bf16(v) -> np.ndarray:
     if rc != 0:
         raise AcsError(rc, "acs_debug_to_bf16")
     return out
+
+
+BENCH_KINDS = ("cb_At", "cb_tcomb", "cb_A", "cb_vec", "l2_At", "l2_A", "l2_vec", "fp64_rhs", "fp64_At",
+               "barrier", "abs_K", "kkt", "o32_rhs", "o32_rhs_comb", "o32_upd", "o32_upd_comb",
+               "cb_stage32", "cb_stage64", "cb_At_nogather", "cb_At_nostage",
+               "stream_At", "stream_At_val")
+
+
+def acs_bench_passes(h, kind, reps: int = 50, smem_bytes: int = -1) -> float:
+    """Device microseconds of one phase (+ one grid barrier) on the problem's data."""
+    k = BENCH_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    us = C.c_double()
+    rc = lib().acs_bench_passes(C.c_void_p(h), k, int(reps), int(smem_bytes), C.byref(us))
+    if rc != 0:
+        raise AcsError(rc, "acs_bench_passes")
+    return us.value
+
+
+def acs_bench_gather(entries: int, mode: int, steps: int = 64, device: int = 0) -> float:
+    """Random 4-byte gathers per second (mode 0 default, 1 .cg, 2 .nc, 3 shared memory)."""
+    g = C.c_double()
+    rc = lib().acs_bench_gather(int(device), int(entries), int(mode), int(steps), C.byref(g))
+    if rc != 0:
+        raise AcsError(rc, "acs_bench_gather")
+    return g.value

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "acs_cbsell.cuh"
 #include "acs_host.cuh"
 #include "acs_internal.cuh"
 
@@ -44,14 +45,15 @@ int upload(Problem* P, T* dst, const T* src, size_t count) {
 }
 
 // FP64 values always; for the FP32 correction CG either FP32 values or,
-// with BF16 storage of A, BF16 bit patterns (v32 is then NULL).
-int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
+// with BF16 storage of A, BF16 bit patterns (v32 is then NULL).  narrow =
+// false: no FP32 copy (the FP32 passes use the column-blocked image).
+int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M, bool narrow = true) {
     int* sptr = nullptr; int* slen = nullptr; int* col = nullptr;
     float* v32 = nullptr; double* v64 = nullptr; unsigned short* v16 = nullptr;
     const size_t tot = H.col.size();
     const bool bf16 = P->set.a_storage == ACS_STORE_BF16;
     if (dalloc(P, &sptr, H.sptr.size()) || dalloc(P, &slen, H.slen.size()) || dalloc(P, &col, tot) ||
-        (bf16 ? dalloc(P, &v16, tot) : dalloc(P, &v32, tot)) || dalloc(P, &v64, tot))
+        (narrow && (bf16 ? dalloc(P, &v16, tot) : dalloc(P, &v32, tot))) || dalloc(P, &v64, tot))
         return ACS_ERR_OOM;
     int rc = 0;
     rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
@@ -59,7 +61,8 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     rc |= upload(P, col, H.col.data(), tot);
     // the narrow copy of the values, converted over parts of the image in parallel
     const int T = acs::host::host_threads((long long)tot);
-    if (bf16) {
+    if (!narrow) {
+    } else if (bf16) {
         acs::host::raw_vector<unsigned short> h(tot);
         acs::host::parallel_for(T, [&](int t) {
             const size_t k1 = (size_t)acs::host::part_lo((long long)tot, t + 1, T);
@@ -81,6 +84,36 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M) {
     M.nrows = H.nrows; M.nslices = H.nslices; M.g = H.g;
     M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64; M.v16 = v16;
     return ACS_SOLVED;
+}
+
+// Column-blocked image: offsets, row ids, 16-bit columns, FP32 values, the
+// CTAs' item ranges and the partial-sum buffer.
+int upload_cb(Problem* P, const acs::host::HostCb& H, acs::CbMat& M) {
+    int* sptr = nullptr; unsigned short* rowid = nullptr; unsigned short* col = nullptr;
+    float* val = nullptr; int* cta = nullptr; float* part = nullptr; unsigned* cend = nullptr;
+    const size_t tot = H.col.size();
+    if (dalloc(P, &sptr, H.sptr.size()) || dalloc(P, &rowid, H.rowid.size()) || dalloc(P, &col, tot) ||
+        dalloc(P, &val, tot) || dalloc(P, &cta, H.cta_beg.size()) || dalloc(P, &cend, H.cend.size()) ||
+        dalloc(P, &part, (size_t)H.nblocks * H.nsl * 32))
+        return ACS_ERR_OOM;
+    int rc = 0;
+    rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
+    rc |= upload(P, rowid, H.rowid.data(), H.rowid.size());
+    rc |= upload(P, col, H.col.data(), tot);
+    rc |= upload(P, val, H.val.data(), tot);
+    rc |= upload(P, cta, H.cta_beg.data(), H.cta_beg.size());
+    rc |= upload(P, cend, H.cend.data(), H.cend.size());
+    if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
+    M.nrows = H.nrows; M.ncols = H.ncols; M.width = H.width; M.nblocks = H.nblocks; M.nsl = H.nsl;
+    M.ctas = (int)H.cta_beg.size() - 1;
+    M.sptr = sptr; M.rowid = rowid; M.col = col; M.val = val; M.cta_beg = cta; M.part = part; M.cend = cend;
+    return ACS_SOLVED;
+}
+
+// Whether acs_solve's FP32 passes use the column-blocked layout: on unless
+// switched off, with FP32 storage of A, when the FP32 launch runs CG at all.
+bool cb_wanted(const acs_settings& set, int dense) {
+    return set.col_block >= 0 && set.a_storage == ACS_STORE_FP32 && dense != 1;
 }
 
 template <typename T>
@@ -148,6 +181,8 @@ int acs_settings_default(acs_settings* s) {
     s->dense_switch_cg = 40;
     s->a_storage = ACS_STORE_FP32;
     s->extrapolation = 0.0;
+    s->col_block = -1;
+    s->outer32_tol = 1e-5;
     return ACS_SOLVED;
 }
 
@@ -202,9 +237,35 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (acs::occupancy_grid(P) != ACS_SOLVED) { free_all(P); delete P; return ACS_ERR_CUDA; }
     const long long warps = (long long)P->grid32 * acs::kThreads / 32;
     acs::host::HostProblem H;
-    const int brc = acs::host::no_throw(
-        [&] { return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H); });
+    acs::host::HostTranspose HT_csr;
+    P->dense = acs::host::dense_mode(set, m);
+    const bool cb = cb_wanted(set, P->dense);
+    const int brc = acs::host::no_throw([&] {
+        return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H,
+                                cb ? &HT_csr : nullptr);
+    });
     if (brc != ACS_SOLVED) { free_all(P); delete P; return brc; }
+    // column-blocked images of A (rows relabelled as above) and A'
+    acs::host::HostCb CA, CT;
+    bool cb_ok = false;
+    if (cb) {
+        const int lim = set.col_block > 0 ? std::min(set.col_block, acs::kCbMaxWidth) : acs::kCbMaxWidth;
+        const int crc = acs::host::no_throw([&] {
+            const int T = acs::host::host_threads(nnz);
+            std::vector<long long> beg(m), end(m);
+            for (int r = 0; r < m; ++r) { beg[r] = row_ptr[H.perm[r]]; end[r] = row_ptr[H.perm[r] + 1]; }
+            if (!acs::host::build_cbsell(m, n, acs::host::cb_width(n, lim), beg, end, col, val, P->grid32, T, CA))
+                return ACS_ERR_CSR;
+            std::vector<long long> begT(HT_csr.rp.begin(), HT_csr.rp.end() - 1), endT(HT_csr.rp.begin() + 1,
+                                                                                     HT_csr.rp.end());
+            if (!acs::host::build_cbsell(n, m, acs::host::cb_width(m, lim), begT, endT, HT_csr.rows.data(),
+                                         HT_csr.vals.data(), P->grid32, T, CT))
+                return ACS_ERR_CSR;
+            return ACS_SOLVED;
+        });
+        cb_ok = crc == ACS_SOLVED;
+        HT_csr = acs::host::HostTranspose();
+    }
     P->perm = H.perm;
     P->padded_A = (long long)H.A.col.size();
     P->padded_AT = (long long)H.AT.col.size();
@@ -215,9 +276,21 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     const std::vector<double>& bperm = H.bperm;
     const std::vector<int>& off = H.soc_off;
 
-    if (acs::host::no_throw([&] { return upload_sell(P, HA, P->A); }) ||
-        acs::host::no_throw([&] { return upload_sell(P, HT, P->AT); })) {
+    if (acs::host::no_throw([&] { return upload_sell(P, HA, P->A, !cb_ok); }) ||
+        acs::host::no_throw([&] { return upload_sell(P, HT, P->AT, !cb_ok); })) {
         free_all(P); delete P; return ACS_ERR_OOM;
+    }
+    if (cb_ok) {
+        if (acs::host::no_throw([&] { return upload_cb(P, CA, P->Acb); }) ||
+            acs::host::no_throw([&] { return upload_cb(P, CT, P->ATcb); })) {
+            free_all(P); delete P; return ACS_ERR_OOM;
+        }
+        P->padded_Acb = (long long)CA.col.size();
+        P->padded_ATcb = (long long)CT.col.size();
+        // one block of the vector in a pass; a window of rows in a combine
+        P->cb_smem = (int)sizeof(float) * std::max(std::max(CA.width, CT.width), acs::kCbWindow);
+        CA = acs::host::HostCb();
+        CT = acs::host::HostCb();
     }
     rc |= dalloc(P, &P->soc_off, n_soc + 1);
     rc |= dalloc(P, &P->b, m); rc |= dalloc(P, &P->c, n);
@@ -228,7 +301,6 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (alloc_outer(P, P->X) || alloc_inner(P, P->V32) || alloc_inner(P, P->V64)) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }
-    P->dense = acs::host::dense_mode(set, m);
     if (P->dense && (dalloc(P, &P->dM, (size_t)m * m) || dalloc(P, &P->dX, (size_t)m * m))) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }
@@ -368,6 +440,79 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
         if (out_val) std::copy(S.val.begin(), S.val.end(), out_val);
         return ACS_SOLVED;
     });
+}
+
+int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                     int32_t which, int32_t width_limit, int32_t ctas, int64_t* info, int32_t* perm,
+                     int32_t* sptr, uint16_t* rowid, uint16_t* out_col, float* out_val, int32_t* cta_beg,
+                     uint32_t* cend) {
+    if (!info || (which != 0 && which != 1) || width_limit < 4 || ctas <= 0 || m <= 0 || n <= 0)
+        return ACS_ERR_ARG;
+    return acs::host::no_throw([&]() -> int {
+        std::vector<double> b((size_t)m, 0.0), c((size_t)n, 0.0);
+        const int v = acs::host::validate(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr);
+        if (v != ACS_SOLVED) return v;
+        acs::host::HostProblem H;
+        acs::host::HostTranspose T;
+        if (acs::host::build(m, n, row_ptr, col, val, b.data(), c.data(), n, 0, nullptr, 1, 1, H, &T) !=
+            ACS_SOLVED)
+            return ACS_ERR_CSR;
+        const int lim = std::min(width_limit, acs::kCbMaxWidth);
+        const int th = acs::host::host_threads(row_ptr[m]);
+        acs::host::HostCb C;
+        bool ok;
+        if (which == 0) {
+            std::vector<long long> beg(m), end(m);
+            for (int r = 0; r < m; ++r) { beg[r] = row_ptr[H.perm[r]]; end[r] = row_ptr[H.perm[r] + 1]; }
+            ok = acs::host::build_cbsell(m, n, acs::host::cb_width(n, lim), beg, end, col, val, ctas, th, C);
+        } else {
+            std::vector<long long> beg(T.rp.begin(), T.rp.end() - 1), end(T.rp.begin() + 1, T.rp.end());
+            ok = acs::host::build_cbsell(n, m, acs::host::cb_width(m, lim), beg, end, T.rows.data(), T.vals.data(),
+                                         ctas, th, C);
+        }
+        if (!ok) return ACS_ERR_CSR;
+        info[0] = C.nrows; info[1] = C.ncols; info[2] = C.width; info[3] = C.nblocks; info[4] = C.nsl;
+        info[5] = (int64_t)C.col.size();
+        if (perm) std::copy(H.perm.begin(), H.perm.end(), perm);
+        if (sptr) std::copy(C.sptr.begin(), C.sptr.end(), sptr);
+        if (rowid) std::copy(C.rowid.begin(), C.rowid.end(), rowid);
+        if (out_col) std::copy(C.col.begin(), C.col.end(), out_col);
+        if (out_val) std::copy(C.val.begin(), C.val.end(), out_val);
+        if (cta_beg) std::copy(C.cta_beg.begin(), C.cta_beg.end(), cta_beg);
+        if (cend) std::copy(C.cend.begin(), C.cend.end(), cend);
+        return ACS_SOLVED;
+    });
+}
+
+int acs_debug_pass_counts(acs_problem* h, int64_t* out, int32_t n) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !out || n < 12) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    acs::Control C;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess ||
+        cudaMemcpy(&C, P->ctl, sizeof(C), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    out[0] = C.n_cg_A; out[1] = C.n_cg_AT; out[2] = C.n_64_A; out[3] = C.n_64_AT;
+    out[4] = C.n_cond; out[5] = C.n_checks; out[6] = C.n_32_A; out[7] = C.n_32_AT;
+    out[8] = C.outer32_end; out[9] = C.l; out[10] = C.cg_iters; out[11] = C.switched_at;
+    return 12;
+}
+
+int acs_bench_passes(acs_problem* h, int32_t kind, int32_t reps, int32_t smem_bytes, double* us_per_rep) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !us_per_rep || kind < 0 || kind > 21) return ACS_ERR_ARG;
+    if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+    return acs::pass_bench(P, kind, reps, smem_bytes < 0 ? P->cb_smem : smem_bytes, us_per_rep);
+}
+
+int acs_debug_layout(acs_problem* h, int64_t* out, int32_t n) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !out || n < 10) return ACS_ERR_ARG;
+    out[0] = P->Acb.nblocks > 0 ? 1 : 0;
+    out[1] = P->Acb.nblocks; out[2] = P->Acb.width; out[3] = P->padded_Acb;
+    out[4] = P->ATcb.nblocks; out[5] = P->ATcb.width; out[6] = P->padded_ATcb;
+    out[7] = P->cb_smem; out[8] = P->padded_A; out[9] = P->padded_AT;
+    return 10;
 }
 
 int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out) {

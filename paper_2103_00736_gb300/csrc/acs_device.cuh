@@ -62,6 +62,11 @@ struct SyncShared {
     int nv;                   // number of values reduced at the next barrier
     int fail;
     unsigned gen;             // barrier generation (same sequence in every CTA)
+    // column-blocked passes: the mbarrier that completes a block's bulk copy
+    // into shared memory, and its phase parity (flips once per block staged)
+    unsigned long long stage_bar;
+    unsigned stage_phase;
+    int cb_next;              // next run of the current segment to deal to a warp
 };
 
 __device__ __forceinline__ SyncShared& sync_smem() {
@@ -419,6 +424,364 @@ __device__ __forceinline__ void sell_rows2(const SellMat& M, G1 g1, G2 g2, Epi e
 }
 
 // ---------------------------------------------------------------------------
+// column-blocked products (layout in acs_internal.cuh / acs_cbsell.cuh)
+// ---------------------------------------------------------------------------
+
+// Dynamic shared memory of the single-problem FP32 launch: the block of the
+// multiplied vector that a column-blocked pass gathers from.
+extern __shared__ __align__(16) float acs_cb_smem[];
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Set up the staging barrier (once per launch, before the first pass).
+__device__ __forceinline__ void cb_init() {
+    SyncShared& S = sync_smem();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.stage_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.stage_phase = 0u;
+    }
+    __syncthreads();
+}
+
+// Bounded wait for the staging barrier's current phase (2 s, then the error
+// word records ACS_ERR_DEVICE_TIMEOUT; the next grid barrier ends the launch).
+__device__ __forceinline__ bool cb_wait(unsigned parity, int* err) {
+    SyncShared& S = sync_smem();
+    const unsigned bar = smem_u32(&S.stage_bar);
+    unsigned done = 0;
+    const unsigned long long t0 = gtimer();
+    int spins = 0;
+    while (true) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (++spins == 64) {
+            spins = 0;
+            if (gtimer() - t0 > kBarrierTimeoutNs) {
+                atomicCAS(err, 0, ACS_ERR_DEVICE_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Stage x[c0, c0 + w) in shared memory as FP32.  The vector was written by
+// other CTAs before the last grid barrier.  An FP32 vector is copied by the
+// bulk-copy engine: thread 0 issues 1-D bulk copies (16-byte multiples; c0 is
+// a multiple of 4 and the vector 16-byte aligned) that complete on the
+// staging mbarrier, the last w mod 4 entries by plain loads; an FP64 vector
+// is read and rounded by all threads, eight loads in flight per thread.
+template <typename Src>
+__device__ __forceinline__ void cb_stage(float* xs, const Src* __restrict__ x, int c0, int w, int* err) {
+    SyncShared& S = sync_smem();
+    if constexpr (sizeof(Src) == 4) {
+        const int w4 = w & ~3;
+        const unsigned parity = S.stage_phase;
+        if (w4 > 0 && threadIdx.x == 0) {
+            const unsigned bar = smem_u32(&S.stage_bar);
+            const unsigned bytes = (unsigned)w4 * 4u;
+            // generic-proxy writes to x (other CTAs, before the grid barrier)
+            // and generic reads of xs (before the CTA barrier) come first
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                         : "memory");
+            constexpr unsigned kChunk = 32768u;
+            const char* src = reinterpret_cast<const char*>(x + c0);
+            char* dst = reinterpret_cast<char*>(xs);
+            for (unsigned o = 0; o < bytes; o += kChunk) {
+                const unsigned len = bytes - o < kChunk ? bytes - o : kChunk;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst + o)),
+                    "l"(src + o), "r"(len), "r"(bar)
+                    : "memory");
+            }
+        }
+        for (int k = w4 + (int)threadIdx.x; k < w; k += blockDim.x) xs[k] = __ldcg(x + c0 + k);
+        if (w4 > 0) {
+            cb_wait(parity, err);
+            __syncthreads();                             // every thread has seen the phase
+            if (threadIdx.x == 0) S.stage_phase = parity ^ 1u;
+        }
+    } else {
+        constexpr int kIn = 8;
+        const int step = (int)blockDim.x * kIn;
+        for (int k0 = threadIdx.x; k0 < w; k0 += step) {
+            double v[kIn];
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                const int k = k0 + u * (int)blockDim.x;
+                v[u] = k < w ? __ldcg(x + c0 + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kIn; ++u) {
+                const int k = k0 + u * (int)blockDim.x;
+                if (k < w) xs[k] = (float)v[u];
+            }
+        }
+    }
+}
+
+template <int U>
+__device__ __forceinline__ void cb_load_batch(const unsigned short* __restrict__ col, const float* __restrict__ val,
+                                              int base, int k, int len, unsigned (&c)[U], float (&a)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (k + u < len) {
+            c[u] = __ldcs(col + base + 32 * (k + u));
+            a[u] = __ldcs(val + base + 32 * (k + u));
+        } else {
+            c[u] = 0u;
+            a[u] = 0.f;
+        }
+    }
+}
+
+// Items are multiplied in runs of kCbRun consecutive items, whose entries
+// are contiguous: a warp streams a run as one sequence of chunks (lane r of
+// chunk c at 32 c + r), whatever the items' lengths, so the next batch of
+// column/value loads can always be issued before the current gathers --
+// across item and run boundaries.  An item ends at the chunk its end mark
+// flags (every item has one).  Runs are dealt to the warps as they ask for
+// them (a shared counter): the items of a window are sorted by length, so a
+// fixed deal would give some warps the long runs every time.  Which warp
+// multiplies a run does not change its sums.
+constexpr int kCbRun = 4;
+
+// The next run for this warp (lane 0 takes it from the counter).
+__device__ __forceinline__ int cb_take_run(int lane) {
+    int r = 0;
+    if (lane == 0) r = atomicAdd(&sync_smem().cb_next, 1);
+    return __shfl_sync(0xffffffffu, r, 0);
+}
+
+// Chunks [c0, c1) of run `run` of the segment [s0, s1) (lanes 0 and 1 load
+// the two offsets).
+__device__ __forceinline__ void cb_run_chunks(const int* __restrict__ sptr, int s0, int s1, int run, int lane,
+                                              int& c0, int& c1) {
+    const int i0 = s0 + run * kCbRun;
+    const int i1 = min(s1, i0 + kCbRun);
+    const int v = lane < 2 ? __ldg(sptr + (lane == 0 ? i0 : i1)) : 0;
+    c0 = __shfl_sync(0xffffffffu, v, 0) >> 5;
+    c1 = __shfl_sync(0xffffffffu, v, 1) >> 5;
+}
+
+// End marks of chunks [c, c + U) as the low U bits (U <= 32).
+template <int U>
+__device__ __forceinline__ unsigned cb_marks(const unsigned* __restrict__ cend, int c) {
+    const unsigned w0 = __ldg(cend + (c >> 5)), w1 = __ldg(cend + (c >> 5) + 1);
+    const unsigned long long w = ((unsigned long long)w1 << 32) | w0;
+    return (unsigned)(w >> (c & 31)) & ((1u << U) - 1u);
+}
+
+// U chunks starting at chunk c: lane r's entries of chunks c .. c + U - 1,
+// those at or past chunk c1 read as (column 0, value 0).
+template <int U>
+__device__ __forceinline__ void cb_load_chunks(const unsigned short* __restrict__ col,
+                                               const float* __restrict__ val, int c, int c1,
+                                               unsigned (&cc)[U], float (&a)[U]) {
+    const size_t e = (size_t)c * 32 + (threadIdx.x & 31);
+    const unsigned short* cp = col + e;
+    const float* vp = val + e;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const bool in = c + u < c1;
+        cc[u] = in ? __ldcs(cp + 32 * u) : 0u;
+        a[u] = in ? __ldcs(vp + 32 * u) : 0.f;
+    }
+}
+
+// The items [s0, s1) of one block (one CTA's segment), in runs dealt to the
+// warps as above: lane r accumulates its row's entries of each item in chunk
+// order (FP32, gathers from the staged block xs) and writes the sum to
+// part[item * 32 + r] (slot order: one coalesced store per item; the combine
+// phases put the rows back in order).  MODE (benchmark variants): 0 the
+// pass, 1 the matrix stream without the gathers, 2 without staging first.
+template <int U, int MODE = 0>
+__device__ __forceinline__ void cb_items(const CbMat& M, const float* xs, int s0, int s1, int warp) {
+    const int nruns = (s1 - s0 + kCbRun - 1) / kCbRun;
+    int run = warp;                                      // the first runs: one per warp
+    if (run >= nruns) return;                            // warp-uniform
+    const int lane = threadIdx.x & 31;
+    int item = s0 + run * kCbRun;                        // item the next chunk belongs to
+    int c, c1;                                           // chunks of the current run
+    cb_run_chunks(M.sptr, s0, s1, run, lane, c, c1);
+    int nrun = cb_take_run(lane), nc = 0, nc1 = 0;       // the following run, one run ahead
+    if (nrun < nruns) cb_run_chunks(M.sptr, s0, s1, nrun, lane, nc, nc1);
+    unsigned cc[U];
+    float a[U];
+    cb_load_chunks<U>(M.col, M.val, c, c1, cc, a);
+    unsigned marks = cb_marks<U>(M.cend, c);
+    float acc = 0.f;
+    while (true) {
+        const bool same = c + U < c1;
+        const bool have_next = same || nrun < nruns;
+        const int cn = same ? c + U : nc;                // first chunk of the next batch
+        const int cn1 = same ? c1 : nc1;
+        unsigned cc2[U];
+        float a2[U];
+        cb_load_chunks<U>(M.col, M.val, cn, have_next ? cn1 : cn, cc2, a2);
+        const unsigned marks2 = have_next ? cb_marks<U>(M.cend, cn) : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c + u < c1) {                            // warp-uniform
+                if (MODE == 1) acc += a[u] + (float)cc[u];
+                else acc = fmaf(a[u], xs[cc[u]], acc);
+                if (marks & (1u << u)) {                 // the item ends at this chunk
+                    __stcg(M.part + (size_t)item * 32 + lane, acc);
+                    acc = 0.f;
+                    ++item;
+                }
+            }
+        }
+        if (!have_next) break;
+        if (!same) {                                     // the next run
+            item = s0 + nrun * kCbRun;
+            nrun = cb_take_run(lane);
+            if (nrun < nruns) cb_run_chunks(M.sptr, s0, s1, nrun, lane, nc, nc1);
+        }
+        c = cn;
+        c1 = cn1;
+        marks = marks2;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = cc2[u];
+            a[u] = a2[u];
+        }
+    }
+}
+
+// One column-blocked pass over the items dealt to this CTA: for each block
+// its range touches, stage the block of x, then multiply the range's items
+// of that block.  Every slot of every item gets its sum written (0 for a row
+// with no entry in the block).  Run by all threads of the CTA, after cb_init
+// in the launch.
+#ifndef ACS_CB_U
+#define ACS_CB_U 6
+#endif
+template <typename Src, int MODE = 0>
+__device__ __forceinline__ void cb_pass(const CbMat& M, const Src* __restrict__ x, int* err) {
+    float* xs = acs_cb_smem;
+    const int rank = team_rank();
+    const int end = __ldg(M.cta_beg + rank + 1);
+    int it = __ldg(M.cta_beg + rank);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (MODE >= 3) {
+        // benchmark variants: the CTA's entries as one linear stream, chunk c
+        // to warp c mod nw (3: columns and values, 4: values only)
+        const int c0 = __ldg(M.sptr + it) >> 5, c1 = __ldg(M.sptr + end) >> 5;
+        float acc = 0.f;
+        for (int c = c0 + warp; c < c1; c += 4 * nw) {
+            float v[4];
+            unsigned cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ch = c + u * nw;
+                const size_t idx = (size_t)ch * 32 + lane;
+                v[u] = ch < c1 ? __ldcs(M.val + idx) : 0.f;
+                cc[u] = (MODE == 3 && ch < c1) ? __ldcs(M.col + idx) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += v[u] + (float)cc[u];
+        }
+        M.part[(size_t)(rank * nw + warp) * 32 + lane] = acc;
+        return;
+    }
+    while (it < end) {                                   // CTA-uniform
+        const int b = it / M.nsl;
+        const int bend = min(end, (b + 1) * M.nsl);
+        const int c0 = b * M.width;
+        __syncthreads();                                 // gathers from the previous block are done
+        if (threadIdx.x == 0) sync_smem().cb_next = nw;  // runs after the first one per warp
+        if (MODE == 0) cb_stage(xs, x, c0, min(M.ncols - c0, M.width), err);
+        __syncthreads();
+        cb_items<ACS_CB_U, MODE>(M, xs, it, bend, warp);
+        it = bend;
+    }
+}
+
+// Adds up the partial sums of the last pass row by row, in block order, and
+// calls epi(row, sum) once for every row.  A CTA takes a window of kCbWindow
+// rows at a time: for each block it reads the window's slots (partial sums
+// and row ids, coalesced) and puts every sum at its row in shared memory
+// (within a block the slots of a window are a permutation of its rows, so
+// no two threads write one row; blocks are separated by a CTA barrier),
+// kCbGroup blocks' loads in flight at once.  Needs kCbWindow floats of
+// dynamic shared memory (free between passes).  Run by all threads of a
+// CTA of kThreads threads (the single-problem launch).
+constexpr int kCbGroup = 4;
+template <typename Epi>
+__device__ __forceinline__ void cb_combine(const CbMat& M, Epi epi) {
+    float* acc = acs_cb_smem;
+    const int R = M.nrows, nb = M.nblocks;
+    const size_t slab = (size_t)M.nsl * 32;              // slots of one block
+    const int nwin = (R + kCbWindow - 1) / kCbWindow;
+    constexpr int kPer = kCbWindow / kThreads;           // slots per thread and block
+    for (int w = team_rank(); w < nwin; w += team_size()) {
+        const int r0 = w * kCbWindow;
+        const int rows = min(kCbWindow, R - r0);
+        const int nslots = (rows + 31) & ~31;
+        for (int b0 = 0; b0 < nb; b0 += kCbGroup) {
+            float v[kCbGroup][kPer];
+            unsigned r[kCbGroup][kPer];
+#pragma unroll
+            for (int g = 0; g < kCbGroup; ++g)
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int sl = (int)threadIdx.x + k * kThreads;
+                    const size_t idx = (size_t)(b0 + g) * slab + (size_t)r0 + sl;
+                    if (b0 + g < nb && sl < nslots) {
+                        r[g][k] = __ldcs(M.rowid + idx);
+                        v[g][k] = __ldcg(M.part + idx);
+                    } else {
+                        r[g][k] = kCbNoRow;
+                        v[g][k] = 0.f;
+                    }
+                }
+#pragma unroll
+            for (int g = 0; g < kCbGroup; ++g) {
+                if (b0 + g < nb) {                       // CTA-uniform
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k)
+                        if (r[g][k] != kCbNoRow) acc[r[g][k]] = (b0 + g == 0) ? v[g][k] : acc[r[g][k]] + v[g][k];
+                    __syncthreads();
+                }
+            }
+        }
+        for (int k = threadIdx.x; k < rows; k += blockDim.x) epi(r0 + k, acc[k]);
+        __syncthreads();                                 // acc is rewritten for the next window
+    }
+}
+
+// The staging of a column-blocked pass alone (every block the CTA's range
+// touches, no products): the benchmark's measure of the copy cost.
+template <typename Src>
+__device__ __forceinline__ void cb_stage_only(const CbMat& M, const Src* __restrict__ x, int* err) {
+    float* xs = acs_cb_smem;
+    const int rank = team_rank();
+    const int end = __ldg(M.cta_beg + rank + 1);
+    int it = __ldg(M.cta_beg + rank);
+    while (it < end) {
+        const int b = it / M.nsl;
+        const int c0 = b * M.width;
+        __syncthreads();
+        cb_stage(xs, x, c0, min(M.ncols - c0, M.width), err);
+        __syncthreads();
+        it = min(end, (b + 1) * M.nsl);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
 // cone helpers
 // ---------------------------------------------------------------------------
 
@@ -613,18 +976,37 @@ __device__ __noinline__ void phase_abs(const IterParams<T>& P, double theta) {
 // i.e. b_tilde - A_hat p - M w); the correction CG starts from it:
 // r = r0, u = J^{-1} r.  Partial gamma = r'u.
 template <typename T>
+__device__ __forceinline__ void rhs_epi(const IterParams<T>& P, int i, double sum, double& gam) {
+    const T r = (T)(P.X.btil[i] - sum);
+    const T u = P.V.jinv[i] * r;
+    P.V.r[i] = r;
+    P.V.u[i] = u;
+    gam += (double)r * (double)u;
+}
+
+template <typename T>
 __device__ __noinline__ void phase_rhs(const IterParams<T>& P) {
     double gam = 0.0;
     const double* g = P.X.g;
     auto gather = [g](int j) { return g[j]; };
-    auto epi = [&](int i, double sum) {
-        const T r = (T)(P.X.btil[i] - sum);
-        const T u = P.V.jinv[i] * r;
-        P.V.r[i] = r;
-        P.V.u[i] = u;
-        gam += (double)r * (double)u;
-    };
+    auto epi = [&](int i, double sum) { rhs_epi(P, i, sum, gam); };
     sell_rows<double>(P.A, gather, epi);
+    const double v[1] = {gam};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// FP32 outer passes: the product A g of the projection residual as a
+// column-blocked FP32 pass (g rounded to FP32 as it is staged) ...
+template <typename T>
+__device__ __noinline__ void phase_rhs_cb(const IterParams<T>& P) {
+    cb_pass(P.Acb, P.X.g, &P.ctl->err);
+}
+// ... and the residual from its partial sums: r0 = b_tilde - A g.
+template <typename T>
+__device__ __noinline__ void phase_rhs_comb(const IterParams<T>& P) {
+    double gam = 0.0;
+    cb_combine(P.Acb, [&](int i, float sum) { rhs_epi(P, i, (double)sum, gam); });
     const double v[1] = {gam};
     const int op[1] = {0};
     block_partials<1>(v, op, P.partials);
@@ -655,16 +1037,45 @@ __device__ __noinline__ void phase_cg_A(const IterParams<T>& P) {
     block_partials<1>(v, op, P.partials);
 }
 
+// Column-blocked CG, first half of M u: the partial sums of A'u ...
+template <typename T>
+__device__ __noinline__ void phase_cg_At_cb(const IterParams<T>& P) {
+    cb_pass(P.ATcb, P.V.u, &P.ctl->err);
+}
+// ... combined: v = A'u, t = O^2 v, and the partial of u'Mu = sum O^2 v^2
+// (= ||A_hat'u||^2, the delta of the CG step, known before the A pass).
+template <typename T>
+__device__ __noinline__ void phase_cg_tcomb(const IterParams<T>& P) {
+    double delta = 0.0;
+    cb_combine(P.ATcb, [&](int j, float sum) {
+        const T v = (T)sum;
+        const T t = P.V.O2[j] * v;
+        P.V.t[j] = t;
+        delta += (double)t * (double)v;
+    });
+    const double v[1] = {delta};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+// Column-blocked CG, second half: the partial sums of A t (= M u), combined
+// in the vector step.
+template <typename T>
+__device__ __noinline__ void phase_cg_A_cb(const IterParams<T>& P) {
+    cb_pass(P.Acb, P.V.t, &P.ctl->err);
+}
+
 // Chronopoulos-Gear vector step: p = u + beta p, sv = au + beta sv,
 // w += alpha p (FP64), r -= alpha sv, u = J^{-1} r; partial gamma = r'u.
-template <typename T>
+// au(i) = (M u)_i: stored by the A pass, or the partial sums of the
+// column-blocked A pass added in block order.
+template <typename T, bool CB>
 __device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, T beta) {
     double gam = 0.0;
     const Inner<T>& V = P.V;
     const T a = (T)alpha;
-    for (int i = global_tid(); i < P.m; i += global_threads()) {
+    auto step = [&](int i, T aui) {
         const T pi = fma(beta, V.p[i], V.u[i]);
-        const T si = fma(beta, V.sv[i], V.au[i]);
+        const T si = fma(beta, V.sv[i], aui);
         V.p[i] = pi;
         V.sv[i] = si;
         P.X.w[i] += alpha * (double)pi;
@@ -673,7 +1084,10 @@ __device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, 
         const T u = V.jinv[i] * r;
         V.u[i] = u;
         gam += (double)r * (double)u;
-    }
+    };
+    if (CB) cb_combine(P.Acb, [&](int i, float sum) { step(i, (T)sum); });
+    else
+        for (int i = global_tid(); i < P.m; i += global_threads()) step(i, V.au[i]);
     const double v[1] = {gam};
     const int op[1] = {0};
     block_partials<1>(v, op, P.partials);
@@ -683,36 +1097,59 @@ __device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, 
 // mu c_hat + q (steps 18-19) and, if want_xz, x = O (p + s)/2 and
 // z = (p - s)/(2 mu O) (steps 20-21).  Partials ||s_new - s||^2, ||s_new||^2.
 template <typename T>
-__device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, bool want_xz) {
-    double ds2 = 0.0, ss2 = 0.0;
-    const double* w = P.X.w;
-    auto gather = [w](int i) { return w[i]; };
-    auto epi = [&](int j, double sum) {
-        const double Oj = P.X.O[j];
-        const double qj = Oj * sum;
-        P.X.q[j] = qj;
-        if (!update) P.X.g[j] = Oj * (P.X.p[j] + qj);   // right-hand side input of a refinement round
-        if (update) {
-            const double pj = P.X.p[j];
-            const double so = P.X.s[j];
-            const double sj = (0.5 * (so + pj) - P.mu * P.X.chat[j]) + qj;
-            P.X.s[j] = sj;
-            ds2 += (sj - so) * (sj - so);
-            ss2 += sj * sj;
-            if (want_xz) {
-                P.x[j] = Oj * (pj + sj) * 0.5;
-                P.z[j] = (pj - sj) / (2.0 * P.mu * Oj);
-            }
+__device__ __forceinline__ void update_epi(const IterParams<T>& P, int j, double sum, bool update, bool want_xz,
+                                           double& ds2, double& ss2) {
+    const double Oj = P.X.O[j];
+    const double qj = Oj * sum;
+    P.X.q[j] = qj;
+    if (!update) P.X.g[j] = Oj * (P.X.p[j] + qj);   // right-hand side input of a refinement round
+    if (update) {
+        const double pj = P.X.p[j];
+        const double so = P.X.s[j];
+        const double sj = (0.5 * (so + pj) - P.mu * P.X.chat[j]) + qj;
+        P.X.s[j] = sj;
+        ds2 += (sj - so) * (sj - so);
+        ss2 += sj * sj;
+        if (want_xz) {
+            P.x[j] = Oj * (pj + sj) * 0.5;
+            P.z[j] = (pj - sj) / (2.0 * P.mu * Oj);
         }
-    };
-    sell_rows<double>(P.AT, gather, epi);
-    // a time-sliced solve: has the deadline passed (one clock read per CTA,
-    // max-reduced, so every CTA of the team takes the same decision)?
+    }
+}
+
+// Partials of the update: ||s_new - s||^2, ||s_new||^2 and, for a
+// time-sliced solve, whether the deadline has passed (one clock read per
+// CTA, max-reduced, so every CTA of the team takes the same decision).
+__device__ __forceinline__ void update_partials(double ds2, double ss2, bool update, double* partials) {
     const unsigned long long dl = sync_smem().deadline;
     const double over = (update && dl != 0ull && threadIdx.x == 0 && gtimer() > dl) ? 1.0 : 0.0;
     const double v[3] = {ds2, ss2, over};
     const int op[3] = {0, 0, 1};
-    block_partials<3>(v, op, P.partials);
+    block_partials<3>(v, op, partials);
+}
+
+template <typename T>
+__device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, bool want_xz) {
+    double ds2 = 0.0, ss2 = 0.0;
+    const double* w = P.X.w;
+    auto gather = [w](int i) { return w[i]; };
+    auto epi = [&](int j, double sum) { update_epi(P, j, sum, update, want_xz, ds2, ss2); };
+    sell_rows<double>(P.AT, gather, epi);
+    update_partials(ds2, ss2, update, P.partials);
+}
+
+// FP32 outer passes: A'w as a column-blocked FP32 pass (w rounded to FP32 as
+// it is staged) ...
+template <typename T>
+__device__ __noinline__ void phase_update_cb(const IterParams<T>& P) {
+    cb_pass(P.ATcb, P.X.w, &P.ctl->err);
+}
+// ... and the update from its partial sums.
+template <typename T>
+__device__ __noinline__ void phase_update_comb(const IterParams<T>& P, bool want_xz) {
+    double ds2 = 0.0, ss2 = 0.0;
+    cb_combine(P.ATcb, [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2); });
+    update_partials(ds2, ss2, true, P.partials);
 }
 
 // FP64 residual partials: ||Ax - b||^2, ||A'y + z - c||^2 (y = w/mu), c'x, b'y,
@@ -982,7 +1419,14 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     bool refresh = P.refresh != 0 || status0 == ST_SWITCH;
     int status = ST_RUNNING;
     long long cg_total = 0;
-    long long nA = 0, nAT = 0, nA64 = 0, nAT64 = 0, ncond = 0, nchk = 0;
+    long long nA = 0, nAT = 0, nA64 = 0, nAT64 = 0, ncond = 0, nchk = 0, nA32 = 0, nAT32 = 0;
+    // FP32 loop of the single-problem launch: column-blocked CG passes, and
+    // FP32 outer passes while P.outer32 is on (until ctl->outer32_end is set)
+    const bool cbcg = sizeof(T) == 4 && P.Acb.nblocks > 0 && P.ATcb.nblocks > 0;
+    int outer32_end = __ldcg(&ctl->outer32_end);
+    bool outer32 = cbcg && P.outer32 != 0 && outer32_end == 0;
+    double best_mx = INFINITY;
+    int flat_checks = 0;
     double res[6];
     for (int i = 0; i < 6; ++i) res[i] = __ldcg(&ctl->res[i]);
     double ds = __ldcg(&ctl->ds), snorm = __ldcg(&ctl->snorm);
@@ -1127,9 +1571,17 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 ++nAT64;
                 ACS_SYNC(PH_QREFRESH);
             }
-            phase_rhs(P);                                       // r0 in FP64
-            ++nA64;
-            ACS_SYNC(PH_RHS);
+            if (outer32) {                                      // r0 from an FP32 product
+                phase_rhs_cb(P);
+                ++nA32;
+                ACS_SYNC(PH_RHS);
+                phase_rhs_comb(P);
+                ACS_SYNC(PH_RHS_COMB);
+            } else {
+                phase_rhs(P);                                   // r0 in FP64
+                ++nA64;
+                ACS_SYNC(PH_RHS);
+            }
             double gam;
             {
                 double t1[1];
@@ -1146,15 +1598,27 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             int k = 0;
             bool broke = false;
             while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
-                phase_cg_At(P);                                 // t = O^2 A' u
-                ++nAT;
-                ACS_SYNC(PH_CG_AT);
-                phase_cg_A(P);                                  // au = A t = M u
-                ++nA;
-                ACS_SYNC(PH_CG_A);
                 double dl[1];
                 const int op1[1] = {0};
-                grid_combine<1>(P.partials, op1, dl);
+                if (cbcg) {
+                    // column-blocked passes: u'Mu = ||A_hat'u||^2 is known after
+                    // the first half, the second half's sums are combined in the
+                    // vector step
+                    phase_cg_At_cb(P);                          // partial sums of A'u
+                    ++nAT;
+                    ACS_SYNC(PH_CG_AT);
+                    phase_cg_tcomb(P);                          // t = O^2 A'u, u'Mu
+                    ACS_SYNC(PH_CG_TCOMB);
+                    grid_combine<1>(P.partials, op1, dl);
+                } else {
+                    phase_cg_At(P);                             // t = O^2 A' u
+                    ++nAT;
+                    ACS_SYNC(PH_CG_AT);
+                    phase_cg_A(P);                              // au = A t = M u
+                    ++nA;
+                    ACS_SYNC(PH_CG_A);
+                    grid_combine<1>(P.partials, op1, dl);
+                }
                 const double beta = (k == 0) ? 0.0 : gam / gam_prev;
                 const double denom = dl[0] - ((k == 0) ? 0.0 : beta * gam / alpha_prev);
                 if (!(denom > 0.0)) {
@@ -1165,7 +1629,14 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                     break;
                 }
                 const double alpha = gam / denom;
-                phase_cg_vec(P, alpha, (T)beta);
+                if (cbcg) {
+                    phase_cg_A_cb(P);                           // partial sums of A t = M u
+                    ++nA;
+                    ACS_SYNC(PH_CG_A);
+                    phase_cg_vec<T, true>(P, alpha, (T)beta);
+                } else {
+                    phase_cg_vec<T, false>(P, alpha, (T)beta);
+                }
                 ACS_SYNC(PH_CG_VEC);
                 double gn[1];
                 grid_combine<1>(P.partials, op1, gn);
@@ -1185,9 +1656,17 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
 
         const bool check = (lnext % P.check_every == 0) || (lnext == P.max_iter);
         const bool want_xz = check || in_schedule(P, lnext + 1);
-        phase_update(P, true, want_xz);                         // steps 18-21
-        ++nAT64;
-        ACS_SYNC(PH_UPDATE);
+        if (outer32) {                                          // steps 18-21, FP32 product
+            phase_update_cb(P);
+            ++nAT32;
+            ACS_SYNC(PH_UPDATE);
+            phase_update_comb(P, want_xz);
+            ACS_SYNC(PH_UPD_COMB);
+        } else {
+            phase_update(P, true, want_xz);                     // steps 18-21
+            ++nAT64;
+            ACS_SYNC(PH_UPDATE);
+        }
         {
             double d2[3];
             const int op[3] = {0, 0, 1};
@@ -1232,6 +1711,21 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             const double mx = fmax(fmax(res[0], res[1]), fmax(res[2], res[3]));
             if (!isfinite(mx)) { status = ACS_ERR_NUMERICAL; break; }
             if (mx <= P.tol) { status = ACS_SOLVED; break; }
+            // FP32 outer passes end once the residuals reach outer32_tol, or
+            // once they stop falling (the FP32 products' rounding floor): the
+            // rest of the solve runs the FP64 passes from the same iterate
+            if (outer32) {
+                if (mx < 0.9 * best_mx) {
+                    best_mx = mx;
+                    flat_checks = 0;
+                } else {
+                    ++flat_checks;
+                }
+                if (mx <= P.outer32_tol || flat_checks >= kOuter32FlatChecks) {
+                    outer32 = false;
+                    outer32_end = l;
+                }
+            }
         }
         if (over && l < P.max_iter) { status = ST_PAUSED; break; }
     }
@@ -1255,6 +1749,9 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         ctl->n_checks += nchk;
         ctl->n_dense_solve += ndense;
         ctl->n_dense_factor += nfactor;
+        ctl->n_32_A += nA32;
+        ctl->n_32_AT += nAT32;
+        ctl->outer32_end = outer32_end;
         ctl->stage = (sizeof(T) == 8 || status == ST_SWITCH) ? 1 : 0;
         ctl->dense_on = (dense || want_dense) ? 1 : 0;
         ctl->factor_ok = factor_ok ? 1 : 0;

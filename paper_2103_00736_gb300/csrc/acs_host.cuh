@@ -158,7 +158,9 @@ inline bool valid_settings(const acs_settings& set) {
     return set.mu > 0 && set.t > 0 && set.check_every > 0 && set.cg_max_iter > 0 && set.cg_refine > 0 &&
            set.cg_refine <= 8 && set.cg_tol >= 0 && set.cg_eta >= 0 && set.cond_period >= 0 && set.cond_first >= 0 &&
            set.n_cond_list >= 0 && !(set.n_cond_list > 0 && !set.cond_list) &&
-           (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP64) &&
+           (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP32 ||
+            set.precision == ACS_PREC_FP64) &&
+           set.col_block >= -1 && set.outer32_tol >= 0 &&
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
            set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit && set.dense_switch_max_m >= 0 &&
            set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0 &&
@@ -372,9 +374,17 @@ struct HostProblem {
 // warps_A / warps_AT: warps of the team that will run the products over the
 // rows of A and of A' (sets the lanes per row).  Inputs must have passed
 // validate().  Returns ACS_ERR_CSR if a padded matrix exceeds 32-bit offsets.
+// The transpose of the relabelled A as CSR (built on the way; kept for a
+// caller that builds another image of A' from it).
+struct HostTranspose {
+    std::vector<long long> rp;
+    raw_vector<int> rows;
+    raw_vector<double> vals;
+};
+
 inline int build(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                  const double* b, const double* c, int32_t n_orthant, int32_t n_soc, const int32_t* soc_dims,
-                 long long warps_A, long long warps_AT, HostProblem& H) {
+                 long long warps_A, long long warps_AT, HostProblem& H, HostTranspose* keep_T = nullptr) {
     const int nnz = (int)row_ptr[m];
     // relabel the constraints: sort rows by length (descending) within windows,
     // so that the rows of a slice have similar lengths and padding is small
@@ -400,6 +410,11 @@ inline int build(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* co
         transpose_relabelled(m, n, row_ptr, col, val, perm, T, rpT, ciT, valT);
         std::vector<long long> beg(rpT.begin(), rpT.end() - 1), end(rpT.begin() + 1, rpT.end());
         H.AT = build_sell(n, choose_g(n, nnz, warps_AT), beg, end, ciT.data(), valT.data(), T);
+        if (keep_T) {
+            keep_T->rp.swap(rpT);
+            keep_T->rows.swap(ciT);
+            keep_T->vals.swap(valT);
+        }
     }
     if (H.A.nslices < 0 || H.AT.nslices < 0) return ACS_ERR_CSR;
     H.bperm.resize(m);

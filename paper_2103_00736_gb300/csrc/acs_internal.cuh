@@ -16,6 +16,9 @@ constexpr int kThreads = 1024;          // threads per CTA of the persistent ker
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRed = 8;              // doubles reduced per grid reduction
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s per barrier
+// FP32 outer passes end after this many KKT checks without a 10 % fall of the
+// largest residual (they have reached the rounding floor of FP32 products)
+constexpr int kOuter32FlatChecks = 10;
 
 // device-side status value of a solve still in progress
 enum : int {
@@ -27,7 +30,11 @@ enum : int {
 // phases of the persistent kernel, for the per-phase time record
 enum Phase : int {
     PH_COND_O = 0, PH_COND_APPLY, PH_BTILDE, PH_QREFRESH, PH_ABS, PH_RHS, PH_CG_AT, PH_CG_A,
-    PH_CG_VEC, PH_UPDATE, PH_KKT, PH_DENSE_FACTOR, PH_DENSE_SOLVE, PH_COUNT
+    PH_CG_VEC, PH_UPDATE, PH_KKT, PH_DENSE_FACTOR, PH_DENSE_SOLVE,
+    PH_CG_TCOMB,     // column-blocked CG: t = O^2 (A'u) from the partial sums, and u'Mu
+    PH_RHS_COMB,     // FP32 outer passes: the projection residual from the partial sums
+    PH_UPD_COMB,     // FP32 outer passes: q = A_hat' w from the partial sums and the update
+    PH_COUNT
 };
 
 // Control block: lives in device memory for the whole solve; the host reads
@@ -47,6 +54,9 @@ struct Control {
     // pass counters (for the algorithmic-byte model of the benchmark)
     long long n_cg_A, n_cg_AT, n_64_A, n_64_AT, n_cond, n_checks;
     long long n_dense_solve, n_dense_factor;   // cached-operator corrections and factorisations
+    long long n_32_A, n_32_AT;                 // FP32 outer passes (projection residual, update)
+    int outer32_end;      // iteration at which the FP32 outer passes ended (0 = not yet)
+    int pad2;
     int stage;            // loop that runs the solve: 0 = FP32 correction CG, 1 = FP64 loop
     int dense_on;         // the cached dense operator is in use (kept across pauses)
     int dense_failed;     // its factorisation failed for this solve
@@ -88,6 +98,26 @@ struct SellMat {
     const unsigned short* v16;   // BF16 bit patterns of the values (BF16 storage of A), else NULL
 };
 
+// Column-blocked sliced ELLPACK of the FP32 passes of the single-problem
+// launch (layout and host builder in acs_cbsell.cuh); nblocks = 0: not used.
+// Lane r of item (block b, slice q) holds row
+// (q / kCbSliceWin) * kCbWindow + rowid[item * 32 + r] (kCbNoRow: none).
+constexpr int kCbWindow = 2048;                 // rows sorted together by their count in a block
+constexpr int kCbSliceWin = kCbWindow / 32;     // slices per window
+constexpr unsigned short kCbNoRow = 0xFFFF;
+struct CbMat {
+    int nrows, ncols, width, nblocks, nsl;      // nsl = slices per block = ceil(nrows / 32)
+    int ctas;                                   // CTAs the item ranges were dealt to
+    const int* sptr;                            // [nblocks * nsl + 1]
+    const unsigned short* rowid;                // [nblocks * nsl * 32]
+    const unsigned short* col;                  // [sptr[last]]
+    const float* val;                           // [sptr[last]]
+    const int* cta_beg;                         // [ctas + 1]
+    const unsigned* cend;                       // item-end marks, one bit per chunk of 32 entries
+    float* part;                                // [nblocks * nsl * 32] partial sums of the last pass,
+                                                //   in slot order (item * 32 + lane)
+};
+
 // Everything one launch of the iteration kernel needs (passed by value).
 template <typename T>
 struct IterParams {
@@ -123,6 +153,10 @@ struct IterParams {
     int own_scratch;                                  // dM/dX belong to this problem and outlive a launch
     double extrap;                                    // factor of the extrapolated start of the projection
                                                       // solve (0 = start from the previous w)
+    CbMat Acb, ATcb;                                  // column-blocked FP32 images of A and A'
+                                                      // (FP32 loop of the single-problem launch only)
+    int outer32;                                      // FP32 outer passes (rhs, update) until the
+    double outer32_tol;                               //   KKT residuals reach outer32_tol
 };
 
 struct Problem {
@@ -138,6 +172,7 @@ struct Problem {
     // is row perm[i] of the caller's A; b, y and w live in that order)
     SellMat A{}, AT{};
     long long padded_A = 0, padded_AT = 0;
+    long long padded_Acb = 0, padded_ATcb = 0;   // stored entries of the column-blocked images
     std::vector<int> perm;
     int* soc_off = nullptr;
     double *b = nullptr, *c = nullptr;
@@ -160,6 +195,8 @@ struct Problem {
     int last_status = ACS_MAX_ITER;
     int dense = 0;                       // cached dense operator: 0 never, 1 always, 2 when CG stalls
     double *dM = nullptr, *dX = nullptr; // its scratch, [m * m] each
+    CbMat Acb{}, ATcb{};                 // column-blocked FP32 images (nblocks = 0: not built)
+    int cb_smem = 0;                     // dynamic shared memory of the FP32 launch (bytes)
     std::vector<void*> allocations;
     cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch
 };
@@ -167,6 +204,8 @@ struct Problem {
 // launches (acs_iter.cu)
 int launch_solve(Problem* P, double tol, int max_iter);
 int occupancy_grid(Problem* P);
+int cb_smem_limit();
+int pass_bench(Problem* P, int kind, int reps, int smem_bytes, double* us);
 int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent = -1);
 
 }  // namespace acs

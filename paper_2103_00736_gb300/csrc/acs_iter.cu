@@ -34,6 +34,7 @@
 // the projection error is kept a fixed fraction eta of the current step, so it
 // vanishes as the iteration converges (a relative inexactness rule).
 
+#include "acs_cbsell.cuh"
 #include "acs_device.cuh"
 #include "acs_host.cuh"
 
@@ -65,12 +66,70 @@ barrier_probe_kernel(Control* ctl, unsigned* flags, double* partials, int n, dou
     }
 }
 
+// Pass micro-benchmark: `reps` repetitions of one kind of phase of the
+// persistent kernel on a prepared problem, each followed by a grid barrier,
+// timed by CTA 0 on the device's global timer.  Kinds: 0 column-blocked A'
+// pass (partial sums of A'u), 1 combine t = O^2 A'u and u'Mu, 2 column-
+// blocked A pass, 3 CG vector step combining its partial sums, 4 / 5 / 6 the
+// same three on the L2-gather layout (FP32 values), 7 FP64 projection
+// residual pass over A, 8 FP64 pass over A' (q = A_hat' w), 9 the barrier
+// alone, 10 abs_K, 11 KKT residuals, 12 / 13 FP32 outer projection residual
+// (pass, combine), 14 / 15 FP32 outer update (pass, combine), 16 / 17 the
+// staging of the column-blocked A pass alone (FP32 / FP64 source), 18 the
+// column-blocked A' pass without its gathers, 19 without its staging, 20 / 21
+// the CTA's entries of the A' image as a plain linear stream (columns and
+// values / values only).  Phases whose
+// layout the problem lacks do nothing.  The iterate state of the problem is
+// left undefined (the next acs_solve starts afresh unless acs_set_state).
+__global__ void __launch_bounds__(kThreads, 1)
+pass_bench_kernel(const __grid_constant__ IterParams<float> P, const __grid_constant__ IterParams<double> P64, int kind,
+                  int reps, double* out_ns) {
+    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials);
+    sync_init(P.ctl->bar_gen);
+    if (P.Acb.nblocks > 0) cb_init();
+    const bool cbA = P.Acb.nblocks > 0, cbT = P.ATcb.nblocks > 0;
+    const bool l2A = P.A.v32 != nullptr, l2T = P.AT.v32 != nullptr;
+    const unsigned long long t0 = gtimer();
+    int r = 0;
+    for (; r < reps; ++r) {
+        switch (kind) {
+            case 0: if (cbT) phase_cg_At_cb(P); break;
+            case 1: if (cbT) phase_cg_tcomb(P); break;
+            case 2: if (cbA) phase_cg_A_cb(P); break;
+            case 3: if (cbA) phase_cg_vec<float, true>(P, 0.0, 0.f); break;
+            case 4: if (l2T) phase_cg_At(P); break;
+            case 5: if (l2A) phase_cg_A(P); break;
+            case 6: if (l2A) phase_cg_vec<float, false>(P, 0.0, 0.f); break;
+            case 7: phase_rhs(P64); break;
+            case 8: phase_update(P64, false, false); break;
+            case 10: phase_abs(P64, 0.0); break;
+            case 11: phase_kkt(P64); break;
+            case 12: if (cbA) phase_rhs_cb(P); break;
+            case 13: if (cbA) phase_rhs_comb(P); break;
+            case 14: if (cbT) phase_update_cb(P); break;
+            case 15: if (cbT) phase_update_comb(P, false); break;
+            case 16: if (cbA) cb_stage_only(P.Acb, P.V.t, &P.ctl->err); break;
+            case 17: if (cbA) cb_stage_only(P.Acb, P.X.g, &P.ctl->err); break;
+            case 18: if (cbT) cb_pass<float, 1>(P.ATcb, P.V.u, &P.ctl->err); break;
+            case 19: if (cbT) cb_pass<float, 2>(P.ATcb, P.V.u, &P.ctl->err); break;
+            case 20: if (cbT) cb_pass<float, 3>(P.ATcb, P.V.u, &P.ctl->err); break;
+            case 21: if (cbT) cb_pass<float, 4>(P.ATcb, P.V.u, &P.ctl->err); break;
+            default: break;
+        }
+        if (!grid_sync(&P.ctl->err)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out_ns[0] = r == reps ? (double)(gtimer() - t0) / reps : -1.0;
+        P.ctl->bar_gen = sync_smem().gen;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the persistent single-problem kernel: one team = the whole grid
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) iter_kernel(IterParams<T> P) {
+__global__ void __launch_bounds__(kThreads, 1) iter_kernel(const __grid_constant__ IterParams<T> P) {
     const int status0 = ld_volatile_int(&P.ctl->status);
     // the FP32 launch runs from a fresh or resumed state; the FP64 launch of a
     // mixed-precision solve runs only if the FP32 launch handed over
@@ -78,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(IterParams<T> P) {
     team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, P.dense ? P.dM : nullptr,
              P.dense ? P.dX : nullptr);
     sync_init(P.ctl->bar_gen);
+    if (P.Acb.nblocks > 0) cb_init();
     solve_loop<T>(P, status0);
 }
 
@@ -124,6 +184,9 @@ __global__ void reset_control(Control* ctl, int l, double ds, double snorm, doub
     ctl->win_cg = 0;
     ctl->extrap_ok = 0;
     ctl->factor_ok = 0;
+    ctl->n_dense_solve = ctl->n_dense_factor = 0;
+    ctl->n_32_A = ctl->n_32_AT = 0;
+    ctl->outer32_end = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -155,20 +218,37 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.cg_max = P->set.cg_max_iter;
     Q.refresh = P->warm ? 1 : 0;
     Q.refine = P->set.cg_refine > 0 ? P->set.cg_refine : 1;
-    Q.switch_ok = P->set.precision == ACS_PREC_MIXED ? 1 : 0;
+    Q.switch_ok = P->set.precision != ACS_PREC_FP64 ? 1 : 0;
     Q.dense = P->dense;
     Q.switch_budget = acs::host::switch_budget(P->set, P->m, P->padded_A);
     Q.extrap = P->set.extrapolation;
     Q.dM = P->dM;
     Q.dX = P->dX;
+    if (sizeof(T) == 4) {                 // column-blocked passes: FP32 loop only
+        Q.Acb = P->Acb;
+        Q.ATcb = P->ATcb;
+        Q.outer32 = P->set.precision == ACS_PREC_FP32 && P->Acb.nblocks > 0 ? 1 : 0;
+        Q.outer32_tol = P->set.outer32_tol;
+    }
     return Q;
 }
+
+// Dynamic shared memory the FP32 launch may ask for: one block of a
+// column-blocked pass (the block width limit in FP32 entries).
+int cb_smem_limit() { return kCbMaxWidth * (int)sizeof(float); }
 
 int occupancy_grid(Problem* P) {
     int nsm = 0, b32 = 0, b64 = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess)
         return ACS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, iter_kernel<float>, kThreads, 0) != cudaSuccess)
+    // the FP32 launch is sized with the largest block it may stage, so that
+    // the grid (and the ranges of items dealt to its CTAs) does not depend on
+    // the block width chosen later
+    if (cudaFuncSetAttribute(iter_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb_smem_limit()) !=
+        cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, iter_kernel<float>, kThreads, cb_smem_limit()) !=
+        cudaSuccess)
         return ACS_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, iter_kernel<double>, kThreads, 0) != cudaSuccess)
         return ACS_ERR_CUDA;
@@ -181,8 +261,43 @@ int occupancy_grid(Problem* P) {
 template <typename T>
 static cudaError_t launch_iter(Problem* P, const IterParams<T>& Q, int grid) {
     void* args[] = {(void*)&Q};
-    return cudaLaunchCooperativeKernel((const void*)iter_kernel<T>, dim3(grid), dim3(kThreads), args, 0,
+    const size_t smem = sizeof(T) == 4 ? (size_t)P->cb_smem : 0;
+    return cudaLaunchCooperativeKernel((const void*)iter_kernel<T>, dim3(grid), dim3(kThreads), args, smem,
                                        P->stream);
+}
+
+int pass_bench(Problem* P, int kind, int reps, int smem_bytes, double* us) {
+    // the stream-only variant (18) reads no shared memory: any size may be asked for
+    const int need = (kind == 18 || kind == 20 || kind == 21) ? 0 : P->cb_smem;
+    if (smem_bytes < need || smem_bytes > cb_smem_limit() || reps <= 0) return ACS_ERR_ARG;
+    cudaStream_t st = P->stream;
+    if (cudaFuncSetAttribute(pass_bench_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cb_smem_limit()) !=
+        cudaSuccess)
+        return ACS_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_bench_kernel, kThreads, smem_bytes) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return ACS_ERR_CUDA;
+    reset_flags<<<1, 256, 0, st>>>(P->flags, P->release, P->max_ctas);
+    reset_control<<<1, 1, 0, st>>>(P->ctl, 0, INFINITY, 0.0, P->set.cg_eta);
+    IterParams<float> Q = make_params<float>(P, 0.0, 1, P->V32);
+    IterParams<double> Q64 = make_params<double>(P, 0.0, 1, P->V64);
+    double* d_out = P->bcast;
+    void* args[] = {(void*)&Q, (void*)&Q64, (void*)&kind, (void*)&reps, (void*)&d_out};
+    // the grid the column-blocked ranges were dealt to
+    if (cudaLaunchCooperativeKernel((const void*)pass_bench_kernel, dim3(P->grid32), dim3(kThreads), args,
+                                    (size_t)smem_bytes, st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    double h = 0.0;
+    int err = 0;
+    if (cudaMemcpyAsync(&h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &P->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (err != 0) return err;
+    *us = h * 1e-3;
+    return ACS_SOLVED;
 }
 
 int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent) {

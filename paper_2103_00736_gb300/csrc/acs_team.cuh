@@ -335,7 +335,7 @@ IterParams<T> member_params(const acs_settings& set, const int* d_cond_list, int
     Q.cg_max = set.cg_max_iter;
     Q.refresh = 0;
     Q.refine = set.cg_refine > 0 ? set.cg_refine : 1;
-    Q.switch_ok = set.precision == ACS_PREC_MIXED ? 1 : 0;
+    Q.switch_ok = set.precision != ACS_PREC_FP64 ? 1 : 0;
     Q.dense = M.dense;
     Q.switch_budget = host::switch_budget(set, M.m, M.nnz);
     Q.extrap = set.extrapolation;
