@@ -276,11 +276,13 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
  * entries}; perm[m] (the row relabelling, as acs_debug_sell),
  * sptr[nblocks * nsl + 1], rowid[32 * nblocks * nsl], out_col /
  * out_val[stored], cta_beg[ctas + 1], cend[stored / 1024 + 2] are written
- * where not NULL.  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
+ * where not NULL, and ipos[32 * nblocks * nsl], the inverse of rowid:
+ * ipos[block * nsl * 32 + row] = the slot (slice within the window * 32 +
+ * lane) that holds the row in that block.  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
 int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                      int32_t which, int32_t width_limit, int32_t ctas, int64_t* info, int32_t* perm,
                      int32_t* sptr, uint16_t* rowid, uint16_t* out_col, float* out_val, int32_t* cta_beg,
-                     uint32_t* cend);
+                     uint32_t* cend, uint16_t* ipos);
 /* Pass counters of the last solve: out[12] = {FP32 CG A passes, FP32 CG A'
  * passes, FP64 A passes, FP64 A' passes, rescalings, KKT checks, FP32 outer
  * A passes, FP32 outer A' passes, iteration at which the FP32 outer passes

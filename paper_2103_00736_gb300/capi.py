@@ -146,7 +146,7 @@ def lib():
         u16p = C.POINTER(C.c_uint16)
         L.acs_debug_cbsell.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), ip, dp, C.c_int32, C.c_int32,
                                        C.c_int32, C.POINTER(C.c_int64), ip, ip, u16p, u16p,
-                                       C.POINTER(C.c_float), ip, C.POINTER(C.c_uint32)]
+                                       C.POINTER(C.c_float), ip, C.POINTER(C.c_uint32), u16p]
         L.acs_debug_pass_counts.argtypes = [P, C.POINTER(C.c_int64), C.c_int32]
         L.acs_debug_layout.argtypes = [P, C.POINTER(C.c_int64), C.c_int32]
         L.acs_bench_passes.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, dp]
@@ -806,7 +806,7 @@ def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas
     info = np.zeros(6, dtype=np.int64)
     args = (int(m), int(n), _ptr(rp, C.c_int64), _ptr(ci, C.c_int32), _ptr(va, C.c_double), int(which),
             int(width_limit), int(ctas))
-    rc = lib().acs_debug_cbsell(*args, _ptr(info, C.c_int64), None, None, None, None, None, None, None)
+    rc = lib().acs_debug_cbsell(*args, _ptr(info, C.c_int64), None, None, None, None, None, None, None, None)
     if rc != 0:
         raise AcsError(rc, "acs_debug_cbsell")
     rows, cols, width, nblocks, nsl, stored = (int(v) for v in info)
@@ -818,13 +818,14 @@ def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas
     ov = np.zeros(max(stored, 1), dtype=np.float32)
     cta = np.zeros(ctas + 1, dtype=np.int32)
     cend = np.zeros(stored // 1024 + 2, dtype=np.uint32)
+    ipos = np.zeros(items * 32, dtype=np.uint16)
     rc = lib().acs_debug_cbsell(*args, _ptr(info, C.c_int64), _ptr(perm, C.c_int32), _ptr(sptr, C.c_int32),
                                 _ptr(rowid, C.c_uint16), _ptr(oc, C.c_uint16), _ptr(ov, C.c_float),
-                                _ptr(cta, C.c_int32), _ptr(cend, C.c_uint32))
+                                _ptr(cta, C.c_int32), _ptr(cend, C.c_uint32), _ptr(ipos, C.c_uint16))
     if rc != 0:
         raise AcsError(rc, "acs_debug_cbsell")
     return dict(rows=rows, cols=cols, width=width, nblocks=nblocks, nsl=nsl, stored=stored, perm=perm,
-                sptr=sptr, rowid=rowid, col=oc[:stored], val=ov[:stored], cta_beg=cta, cend=cend)
+                sptr=sptr, rowid=rowid, col=oc[:stored], val=ov[:stored], cta_beg=cta, cend=cend, ipos=ipos)
 
 
 PASS_COUNTS = ("cg_A", "cg_At", "fp64_A", "fp64_At", "rescalings", "checks", "fp32_outer_A",

@@ -91,8 +91,10 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M, bool narrow = tr
 int upload_cb(Problem* P, const acs::host::HostCb& H, acs::CbMat& M) {
     int* sptr = nullptr; unsigned short* rowid = nullptr; unsigned short* col = nullptr;
     float* val = nullptr; int* cta = nullptr; float* part = nullptr; unsigned* cend = nullptr;
+    unsigned short* ipos = nullptr;
     const size_t tot = H.col.size();
     if (dalloc(P, &sptr, H.sptr.size()) || dalloc(P, &rowid, H.rowid.size()) || dalloc(P, &col, tot) ||
+        dalloc(P, &ipos, H.ipos.size()) ||
         dalloc(P, &val, tot) || dalloc(P, &cta, H.cta_beg.size()) || dalloc(P, &cend, H.cend.size()) ||
         dalloc(P, &part, (size_t)H.nblocks * H.nsl * 32))
         return ACS_ERR_OOM;
@@ -103,10 +105,12 @@ int upload_cb(Problem* P, const acs::host::HostCb& H, acs::CbMat& M) {
     rc |= upload(P, val, H.val.data(), tot);
     rc |= upload(P, cta, H.cta_beg.data(), H.cta_beg.size());
     rc |= upload(P, cend, H.cend.data(), H.cend.size());
+    rc |= upload(P, ipos, H.ipos.data(), H.ipos.size());
     if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
     M.nrows = H.nrows; M.ncols = H.ncols; M.width = H.width; M.nblocks = H.nblocks; M.nsl = H.nsl;
     M.ctas = (int)H.cta_beg.size() - 1;
     M.sptr = sptr; M.rowid = rowid; M.col = col; M.val = val; M.cta_beg = cta; M.part = part; M.cend = cend;
+    M.ipos = ipos;
     return ACS_SOLVED;
 }
 
@@ -287,8 +291,11 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         }
         P->padded_Acb = (long long)CA.col.size();
         P->padded_ATcb = (long long)CT.col.size();
-        // one block of the vector in a pass; a window of rows in a combine
-        P->cb_smem = (int)sizeof(float) * std::max(std::max(CA.width, CT.width), acs::kCbWindow);
+        // one block of the vector in a pass; in a combine, two tiles of up to
+        // kCbCombineMaxGroup blocks
+        const int g = std::min(std::max(CA.nblocks, CT.nblocks), acs::kCbCombineMaxGroup);
+        P->cb_smem = std::max((int)sizeof(float) * std::max(CA.width, CT.width), 2 * g * acs::kCbWindow * 6);
+        P->cb_smem = std::min(P->cb_smem, acs::cb_smem_limit());
         CA = acs::host::HostCb();
         CT = acs::host::HostCb();
     }
@@ -445,7 +452,7 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
 int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                      int32_t which, int32_t width_limit, int32_t ctas, int64_t* info, int32_t* perm,
                      int32_t* sptr, uint16_t* rowid, uint16_t* out_col, float* out_val, int32_t* cta_beg,
-                     uint32_t* cend) {
+                     uint32_t* cend, uint16_t* ipos) {
     if (!info || (which != 0 && which != 1) || width_limit < 4 || ctas <= 0 || m <= 0 || n <= 0)
         return ACS_ERR_ARG;
     return acs::host::no_throw([&]() -> int {
@@ -480,6 +487,7 @@ int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
         if (out_val) std::copy(C.val.begin(), C.val.end(), out_val);
         if (cta_beg) std::copy(C.cta_beg.begin(), C.cta_beg.end(), cta_beg);
         if (cend) std::copy(C.cend.begin(), C.cend.end(), cend);
+        if (ipos) std::copy(C.ipos.begin(), C.ipos.end(), ipos);
         return ACS_SOLVED;
     });
 }

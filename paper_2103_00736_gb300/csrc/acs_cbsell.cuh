@@ -18,7 +18,9 @@
 //     col = column - b * width (16 bits), val = the FP32 value;
 //     padding entries have col 0 and val 0; rowid 0xFFFF marks no row;
 //     every item has at least one chunk, and bit c % 32 of cend[c / 32]
-//     marks chunk c (in units of 32 entries) as the last of its item.
+//     marks chunk c (in units of 32 entries) as the last of its item;
+//     ipos[b * nsl * 32 + row] = the slot of the row within its window in
+//     block b (the inverse of rowid).
 //
 // A pass stages block b of the vector in shared memory and multiplies every
 // item of the block, writing one partial sum per row and block,
@@ -53,6 +55,7 @@ struct HostCb {
     raw_vector<float> val;
     std::vector<int> cta_beg;
     std::vector<unsigned> cend;
+    std::vector<unsigned short> ipos;      // [nblocks * nsl * 32]: slot of each row in its window
 };
 
 // Block width for ncols columns and a limit: the fewest blocks that respect
@@ -108,6 +111,7 @@ inline bool build_cbsell(int nrows, int ncols, int width, const std::vector<long
     const int nwin = (R + kCbWindow - 1) / kCbWindow;
     std::vector<int> pos((size_t)nb * R);
     H.rowid.assign((size_t)nitems * 32, kCbNoRow);
+    H.ipos.assign((size_t)nitems * 32, 0);
     std::vector<int> len((size_t)nitems, 0);
     parallel_for(threads, [&](int t) {
         std::vector<int> order;
@@ -122,6 +126,7 @@ inline bool build_cbsell(int nrows, int ncols, int width, const std::vector<long
             for (int k = 0; k < r1 - r0; ++k) {
                 const int r = order[k];
                 pos[(size_t)b * R + r] = k;
+                H.ipos[(size_t)b * nsl * 32 + (size_t)r] = (unsigned short)k;
                 const long long item = (long long)b * nsl + (long long)w * kCbSliceWin + k / 32;
                 H.rowid[(size_t)item * 32 + (k % 32)] = (unsigned short)(r - r0);
                 // the slice's longest row comes first; an item has at least

@@ -67,6 +67,9 @@ struct SyncShared {
     unsigned long long stage_bar;
     unsigned stage_phase;
     int cb_next;              // next run of the current segment to deal to a warp
+    // the combine phases' two tile slots: their mbarriers and phase parities
+    unsigned long long comb_bar[2];
+    unsigned comb_phase[2];
 };
 
 __device__ __forceinline__ SyncShared& sync_smem() {
@@ -440,17 +443,19 @@ __device__ __forceinline__ void cb_init() {
     SyncShared& S = sync_smem();
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.stage_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.comb_bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.comb_bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.stage_phase = 0u;
+        S.comb_phase[0] = S.comb_phase[1] = 0u;
     }
     __syncthreads();
 }
 
 // Bounded wait for the staging barrier's current phase (2 s, then the error
 // word records ACS_ERR_DEVICE_TIMEOUT; the next grid barrier ends the launch).
-__device__ __forceinline__ bool cb_wait(unsigned parity, int* err) {
-    SyncShared& S = sync_smem();
-    const unsigned bar = smem_u32(&S.stage_bar);
+__device__ __forceinline__ bool cb_wait_bar(unsigned long long* mbar, unsigned parity, int* err) {
+    const unsigned bar = smem_u32(mbar);
     unsigned done = 0;
     const unsigned long long t0 = gtimer();
     int spins = 0;
@@ -508,7 +513,7 @@ __device__ __forceinline__ void cb_stage(float* xs, const Src* __restrict__ x, i
         }
         for (int k = w4 + (int)threadIdx.x; k < w; k += blockDim.x) xs[k] = __ldcg(x + c0 + k);
         if (w4 > 0) {
-            cb_wait(parity, err);
+            cb_wait_bar(&S.stage_bar, parity, err);
             __syncthreads();                             // every thread has seen the phase
             if (threadIdx.x == 0) S.stage_phase = parity ^ 1u;
         }
@@ -709,56 +714,108 @@ __device__ __forceinline__ void cb_pass(const CbMat& M, const Src* __restrict__ 
     }
 }
 
+// Dynamic shared memory of the launch (bytes).
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// Blocks of one combine tile that fit two tile slots in `smem` bytes (at
+// least 1).
+__host__ __device__ __forceinline__ int cb_combine_group(int nblocks, unsigned smem) {
+    const unsigned per = (unsigned)kCbWindow * 6u;       // one block's sums and slot indices of a window
+    int g = (int)(smem / (2u * per));
+    if (g > nblocks) g = nblocks;
+    return g < 1 ? 1 : g;
+}
+
 // Adds up the partial sums of the last pass row by row, in block order, and
-// calls epi(row, sum) once for every row.  A CTA takes a window of kCbWindow
-// rows at a time: for each block it reads the window's slots (partial sums
-// and row ids, coalesced) and puts every sum at its row in shared memory
-// (within a block the slots of a window are a permutation of its rows, so
-// no two threads write one row; blocks are separated by a CTA barrier),
-// kCbGroup blocks' loads in flight at once.  Needs kCbWindow floats of
-// dynamic shared memory (free between passes).  Run by all threads of a
-// CTA of kThreads threads (the single-problem launch).
-constexpr int kCbGroup = 4;
+// calls epi(row, sum) once for every row.  A CTA takes windows of kCbWindow
+// rows (rank, rank + CTAs, ...); a tile is one window and a group of G
+// blocks: for each block of the group, the window's partial sums (slot
+// order) and the slot of each of its rows (ipos, row order) are copied into
+// one of two tile slots in shared memory by the bulk-copy engine while the
+// threads work on the previous tile.  Thread k owns rows k, k + blockDim, ...
+// of the window and adds their sums block after block in registers, reading
+// each at its slot.  Shared memory: the two slots (needs 24 KB for G = 1).
+// Run by all threads of the CTA, after cb_init in the launch.
+constexpr int kCbRowsPerThread = kCbWindow / kThreads;
 template <typename Epi>
-__device__ __forceinline__ void cb_combine(const CbMat& M, Epi epi) {
-    float* acc = acs_cb_smem;
+__device__ __forceinline__ void cb_combine(const CbMat& M, int* err, Epi epi) {
+    SyncShared& S = sync_smem();
     const int R = M.nrows, nb = M.nblocks;
     const size_t slab = (size_t)M.nsl * 32;              // slots of one block
     const int nwin = (R + kCbWindow - 1) / kCbWindow;
-    constexpr int kPer = kCbWindow / kThreads;           // slots per thread and block
-    for (int w = team_rank(); w < nwin; w += team_size()) {
-        const int r0 = w * kCbWindow;
-        const int rows = min(kCbWindow, R - r0);
-        const int nslots = (rows + 31) & ~31;
-        for (int b0 = 0; b0 < nb; b0 += kCbGroup) {
-            float v[kCbGroup][kPer];
-            unsigned r[kCbGroup][kPer];
+    const int rank = team_rank(), size = team_size();
+    if (rank >= nwin) return;                            // CTA-uniform
+    const int G = cb_combine_group(nb, dyn_smem_bytes());
+    const int ngroups = (nb + G - 1) / G;
+    const int T = ((nwin - 1 - rank) / size + 1) * ngroups;
+    char* slots = reinterpret_cast<char*>(acs_cb_smem);
+    const unsigned slot_bytes = (unsigned)G * kCbWindow * 6u;
+    // tile t: window rank + (t / ngroups) * size, blocks of group t % ngroups
+    auto issue = [&](int t) {                            // thread 0
+        const int w = rank + (t / ngroups) * size, g = t % ngroups;
+        const int r0 = w * kCbWindow, nslots = (min(kCbWindow, R - r0) + 31) & ~31;
+        const int b0 = g * G, gb = min(G, nb - b0);
+        char* sl = slots + (t & 1) * slot_bytes;
+        const unsigned bar = smem_u32(&S.comb_bar[t & 1]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((unsigned)(gb * nslots * 6))
+                     : "memory");
+        for (int k = 0; k < gb; ++k) {
+            const size_t src = (size_t)(b0 + k) * slab + (size_t)r0;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(sl + (size_t)k * kCbWindow * 4)),
+                "l"(M.part + src), "r"((unsigned)nslots * 4u), "r"(bar)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(sl + (size_t)G * kCbWindow * 4 + (size_t)k * kCbWindow * 2)),
+                "l"(M.ipos + src), "r"((unsigned)nslots * 2u), "r"(bar)
+                : "memory");
+        }
+    };
+    if (threadIdx.x == 0) {
+        // the partial sums were written by other CTAs before the grid barrier
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        issue(0);
+    }
+    float acc[kCbRowsPerThread];
+    for (int t = 0; t < T; ++t) {
+        // slot (t + 1) & 1 was last read in tile t - 1, which ended with a CTA barrier
+        if (threadIdx.x == 0 && t + 1 < T) issue(t + 1);
+        const int w = rank + (t / ngroups) * size, g = t % ngroups;
+        const int r0 = w * kCbWindow, rows = min(kCbWindow, R - r0);
+        const int b0 = g * G, gb = min(G, nb - b0);
+        const unsigned parity = S.comb_phase[t & 1];
+        cb_wait_bar(&S.comb_bar[t & 1], parity, err);
+        const float* sp = reinterpret_cast<const float*>(slots + (t & 1) * slot_bytes);
+        const unsigned short* si =
+            reinterpret_cast<const unsigned short*>(slots + (t & 1) * slot_bytes + (size_t)G * kCbWindow * 4);
 #pragma unroll
-            for (int g = 0; g < kCbGroup; ++g)
-#pragma unroll
-                for (int k = 0; k < kPer; ++k) {
-                    const int sl = (int)threadIdx.x + k * kThreads;
-                    const size_t idx = (size_t)(b0 + g) * slab + (size_t)r0 + sl;
-                    if (b0 + g < nb && sl < nslots) {
-                        r[g][k] = __ldcs(M.rowid + idx);
-                        v[g][k] = __ldcg(M.part + idx);
-                    } else {
-                        r[g][k] = kCbNoRow;
-                        v[g][k] = 0.f;
-                    }
+        for (int i = 0; i < kCbRowsPerThread; ++i) {
+            const int j = (int)threadIdx.x + i * kThreads;
+            float a = b0 == 0 ? 0.f : acc[i];
+            if (j < rows)
+                for (int k = 0; k < gb; ++k) {
+                    const float v = sp[k * kCbWindow + si[k * kCbWindow + j]];
+                    a = (b0 + k == 0) ? v : a + v;
                 }
+            acc[i] = a;
+        }
+        __syncthreads();                                 // the slot may be refilled
+        if (threadIdx.x == 0) S.comb_phase[t & 1] = parity ^ 1u;
+        if (g == ngroups - 1) {                          // the window is complete
 #pragma unroll
-            for (int g = 0; g < kCbGroup; ++g) {
-                if (b0 + g < nb) {                       // CTA-uniform
-#pragma unroll
-                    for (int k = 0; k < kPer; ++k)
-                        if (r[g][k] != kCbNoRow) acc[r[g][k]] = (b0 + g == 0) ? v[g][k] : acc[r[g][k]] + v[g][k];
-                    __syncthreads();
-                }
+            for (int i = 0; i < kCbRowsPerThread; ++i) {
+                const int j = (int)threadIdx.x + i * kThreads;
+                if (j < rows) epi(r0 + j, acc[i]);
             }
         }
-        for (int k = threadIdx.x; k < rows; k += blockDim.x) epi(r0 + k, acc[k]);
-        __syncthreads();                                 // acc is rewritten for the next window
     }
 }
 
@@ -1006,7 +1063,7 @@ __device__ __noinline__ void phase_rhs_cb(const IterParams<T>& P) {
 template <typename T>
 __device__ __noinline__ void phase_rhs_comb(const IterParams<T>& P) {
     double gam = 0.0;
-    cb_combine(P.Acb, [&](int i, float sum) { rhs_epi(P, i, (double)sum, gam); });
+    cb_combine(P.Acb, &P.ctl->err, [&](int i, float sum) { rhs_epi(P, i, (double)sum, gam); });
     const double v[1] = {gam};
     const int op[1] = {0};
     block_partials<1>(v, op, P.partials);
@@ -1047,7 +1104,7 @@ __device__ __noinline__ void phase_cg_At_cb(const IterParams<T>& P) {
 template <typename T>
 __device__ __noinline__ void phase_cg_tcomb(const IterParams<T>& P) {
     double delta = 0.0;
-    cb_combine(P.ATcb, [&](int j, float sum) {
+    cb_combine(P.ATcb, &P.ctl->err, [&](int j, float sum) {
         const T v = (T)sum;
         const T t = P.V.O2[j] * v;
         P.V.t[j] = t;
@@ -1085,7 +1142,7 @@ __device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, 
         V.u[i] = u;
         gam += (double)r * (double)u;
     };
-    if (CB) cb_combine(P.Acb, [&](int i, float sum) { step(i, (T)sum); });
+    if (CB) cb_combine(P.Acb, &P.ctl->err, [&](int i, float sum) { step(i, (T)sum); });
     else
         for (int i = global_tid(); i < P.m; i += global_threads()) step(i, V.au[i]);
     const double v[1] = {gam};
@@ -1148,7 +1205,7 @@ __device__ __noinline__ void phase_update_cb(const IterParams<T>& P) {
 template <typename T>
 __device__ __noinline__ void phase_update_comb(const IterParams<T>& P, bool want_xz) {
     double ds2 = 0.0, ss2 = 0.0;
-    cb_combine(P.ATcb, [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2); });
+    cb_combine(P.ATcb, &P.ctl->err, [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2); });
     update_partials(ds2, ss2, true, P.partials);
 }
 

@@ -105,6 +105,7 @@ struct SellMat {
 constexpr int kCbWindow = 2048;                 // rows sorted together by their count in a block
 constexpr int kCbSliceWin = kCbWindow / 32;     // slices per window
 constexpr unsigned short kCbNoRow = 0xFFFF;
+constexpr int kCbCombineMaxGroup = 7;           // blocks per tile of a combine phase
 struct CbMat {
     int nrows, ncols, width, nblocks, nsl;      // nsl = slices per block = ceil(nrows / 32)
     int ctas;                                   // CTAs the item ranges were dealt to
@@ -114,6 +115,7 @@ struct CbMat {
     const float* val;                           // [sptr[last]]
     const int* cta_beg;                         // [ctas + 1]
     const unsigned* cend;                       // item-end marks, one bit per chunk of 32 entries
+    const unsigned short* ipos;                 // [nblocks * nsl * 32] slot of each row in its window
     float* part;                                // [nblocks * nsl * 32] partial sums of the last pass,
                                                 //   in slot order (item * 32 + lane)
 };

@@ -27,10 +27,10 @@ from paper_2103_00736_gb300 import capi, instances as I  # noqa: E402
 SCHED = {"large_lp": dict(cond_first=300, cond_period=100, t=9.2),
          "socp": dict(cond_first=200, cond_period=100, t=1.7)}
 CB_KINDS = ("cb_At", "cb_tcomb", "cb_A", "cb_vec", "o32_rhs", "o32_rhs_comb", "o32_upd", "o32_upd_comb",
-            "cb_stage32", "cb_stage64", "cb_At_nogather", "cb_At_nostage",
-               "stream_At", "stream_At_val")
+            "cb_stage32", "cb_stage64")
 L2_KINDS = ("l2_At", "l2_A", "l2_vec")
 COMMON = ("fp64_rhs", "fp64_At", "barrier", "abs_K", "kkt")
+DIAG = ("cb_At_nogather", "cb_At_nostage", "stream_At", "stream_At_val")
 
 
 def main():
@@ -55,14 +55,14 @@ def main():
             lay = capi.acs_debug_layout(s.h)
             kinds = (CB_KINDS if lay["col_blocked"] else L2_KINDS) + COMMON
             if args.kinds:
-                kinds = tuple(k for k in args.kinds.split(",") if k in kinds)
+                kinds = tuple(k for k in args.kinds.split(",") if k in kinds + (DIAG if lay["col_blocked"] else ()))
             res = {k: capi.acs_bench_passes(s.h, k, args.reps) for k in kinds}
             if args.smem_sweep and lay["col_blocked"]:
                 for sm in (0, 196608):
                     for k in ("cb_At_nogather", "stream_At", "stream_At_val"):
                         res[f"{k}@smem{sm}"] = capi.acs_bench_passes(s.h, k, args.reps, sm)
             if args.smem_sweep and not lay["col_blocked"]:
-                for sm in (98304, 196608):
+                for sm in (65536, 98304, 131072, 163840, 196608):
                     for k in L2_KINDS + COMMON:
                         res[f"{k}@smem{sm}"] = capi.acs_bench_passes(s.h, k, args.reps, sm)
             out[f"width{w}"] = {"layout": lay, "us": res}

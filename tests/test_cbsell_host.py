@@ -12,7 +12,8 @@ Bit-exact bars (index and byte work):
     column) is the relabelled A, respectively A', entry for entry in each
     row's order, with FP32 values; padding is column 0, value 0; every item
     is as long as its longest row needs, and at least one chunk; the
-    item-end marks flag exactly the last chunk of every item;
+    item-end marks flag exactly the last chunk of every item; ipos is the
+    inverse of the row ids (the slot of every row in every block);
   * the items are dealt to the CTAs as contiguous ranges covering all items
     once, each range's work (chunks + 1 per item) within one item of an
     equal share.
@@ -114,6 +115,15 @@ def _check(S, rows, width_limit, ctas):
             assert cs[:k] == list(wc[sel]), (r, b)
             assert np.array_equal(np.array(vs[:k], np.float32), wv[sel].astype(np.float32)), (r, b)
             assert all(c == b * W for c in cs[k:]) and not any(vs[k:]), (r, b)   # padding: column 0, value 0
+    # ipos is the inverse of rowid: the slot of every row of a window in every block
+    ipos = S["ipos"]
+    for b in range(nb):
+        for q in range(nsl):
+            for lane in range(32):
+                rid = int(rowid[(b * nsl + q) * 32 + lane])
+                if rid != NO_ROW:
+                    r = (q // SLICES_PER_WINDOW) * WINDOW + rid
+                    assert ipos[b * nsl * 32 + r] == (q % SLICES_PER_WINDOW) * 32 + lane, (b, r)
     # item-end marks: exactly the last chunk of every item
     marks = np.unpackbits(S["cend"].view(np.uint8), bitorder="little").astype(bool)
     want = np.zeros(marks.size, bool)
