@@ -25,12 +25,17 @@ Readings (the paper is silent or ambiguous on these):
   * o is the same for every coordinate of one cone, so O is constant on each
     cone and O^{-1} K = K, abs_{O^{-1} K} = abs_K; O' A_cal = range((A O)').
   * o_j = 0, inf or nan (x_{h+1} = ||xbar|| or z_{h+1} = 0, e.g. a
-    coordinate with x_j = z_j = 0): such entries carry no scale, so the
-    exponent of step 11 is computed from the finite positive o only, and the
-    others take the limits of the rule under the cap: o = 0 the smallest
-    scale min(o)^alpha, o = inf the largest max(o)^alpha, o = nan the
-    geometric middle.  No finite positive o at all: O = I.  All finite o
-    equal: exponent 1.
+    coordinate with x_j = z_j = 0): a departure from the printed rule, not a
+    reading of it.  Evaluated as printed (IEEE, or MATLAB whose max and min
+    skip nan), an o of 0 or inf makes the log spread infinite, the exponent
+    0 and O = I: one degenerate coordinate switches the rescaling off for the
+    whole problem (conditioning_matrix_literal, rule="literal").  The oracle
+    instead lets such entries carry no scale: the exponent of step 11 is
+    computed from the finite positive o only, and the others take the
+    limits of the rule under the cap: o = 0 the smallest scale
+    min(o)^alpha, o = inf the largest max(o)^alpha, o = nan the geometric
+    middle.  No finite positive o at all: O = I.  All finite o equal:
+    exponent 1.
   * O is recomputed from the current x, z at each conditioning (not composed).
   * Steps 20-21 use p from the old s and the updated s, as printed.
   * The schedule L continues with its period up to max_iter.
@@ -102,6 +107,25 @@ def conditioning_exponent(o: np.ndarray, t: float) -> float:
     return min(1.0, t / spread)
 
 
+def conditioning_matrix_literal(x, z, n_orth, soc_dims, t):
+    """diag(O) of step 11 evaluated as printed in IEEE arithmetic, with max and
+    min ignoring nan (MATLAB's max/min): an o of 0 or inf makes
+    log max o - log min o infinite, so alpha = min(1, t / inf) = 0 and
+    O = |o|^0 = 1 everywhere (0^0 = inf^0 = nan^0 = 1): the rescaling is
+    switched off.  With only nan among the non-finite o, alpha > 0 and the
+    nan entries give O_j = nan (the printed rule is undefined there).  This
+    is not the rule the oracle uses (conditioning_matrix); it is kept to
+    show what the literal evaluation does."""
+    o = conditioning_vector(x, z, n_orth, soc_dims)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        lo = np.log(np.abs(o))
+        if np.all(np.isnan(lo)):
+            return np.full_like(o, np.nan), float("nan")
+        spread = float(np.nanmax(lo) - np.nanmin(lo))
+        alpha = min(1.0, t / spread) if spread > 0 else 1.0
+        return np.power(np.abs(o), alpha), alpha
+
+
 def conditioning_matrix(x, z, n_orth, soc_dims, t):
     """diag(O) of step 11: |o|^alpha, with the limits above for o in {0, inf, nan}."""
     o = conditioning_vector(x, z, n_orth, soc_dims)
@@ -136,9 +160,12 @@ class Result:
 def algorithm2(A, b, c, n_orth: int, soc_dims=(), mu: float = 1.0, t: float = 9.2,
                L: Schedule = LP_SCHEDULE, max_iter: int = 1000, tol: float = 1e-6,
                check_every: int = 1, x0=None, z0=None, keep_x: int = 0,
-               solver: str = "auto", on_iter=None) -> Result:
+               solver: str = "auto", on_iter=None, rule: str = "finite") -> Result:
     """Algorithm 2 in FP64.  Stops when every relative KKT residual (kkt.residuals)
-    is <= tol at a check, or after max_iter iterations (status 'max_iter')."""
+    is <= tol at a check, or after max_iter iterations (status 'max_iter').
+    rule: step 11 as the oracle reads it ("finite", conditioning_matrix) or
+    evaluated as printed ("literal", conditioning_matrix_literal; a nan O
+    ends the run with status 'breakdown')."""
     A = sp.csr_matrix(A, dtype=np.float64)
     m, n = A.shape
     soc_dims = np.asarray(soc_dims, dtype=np.int64)
@@ -156,7 +183,13 @@ def algorithm2(A, b, c, n_orth: int, soc_dims=(), mu: float = 1.0, t: float = 9.
     while l < max_iter:
         l += 1
         if l in L or l == 1:
-            O, alpha = conditioning_matrix(x, z, n_orth, soc_dims, t)        # steps 5-11
+            if rule == "literal":
+                O, alpha = conditioning_matrix_literal(x, z, n_orth, soc_dims, t)
+                if not np.all(np.isfinite(O)):
+                    out.status, out.iters = "breakdown", l
+                    return out
+            else:
+                O, alpha = conditioning_matrix(x, z, n_orth, soc_dims, t)    # steps 5-11
             sub = Subspace(A, O, solver=solver)                              # step 12
             c_hat = O * c
             d = sub.pinv_t(b) + 0.5 * mu * (sub.abs(c_hat) - c_hat)          # step 13

@@ -383,9 +383,10 @@ def test_bf16_storage_of_A():
     """BF16 storage of A (the FP32 correction CG reads 2-byte values): the
     FP64 residual of every refinement round still uses the FP64 values, so
     the end result meets the same bars.  The first iterates differ from the
-    oracle's by the BF16 model error (8 significant bits) that one correction
-    leaves: measured 7.2e-3 relative over the first 50 iterations on the
-    GB300, bound 1e-2 (FP32 storage: 1e-4)."""
+    oracle's because each correction is solved with the BF16 matrix; they are
+    compared with a reference that applies exactly that rounding in an exact
+    FP64 correction (tests/refinement_model.py, pinned to the oracle), at
+    the FP32 bar of 1e-4: what remains is the FP32 arithmetic of the CG."""
     inst = I.small_lp()
     kw = dict(projection=capi.PROJ_CG, a_storage=capi.STORE_BF16, **LP_SCHED)
     st, x, y, z, iters, res = _solve(inst, tol=2e-7, **kw)
@@ -393,15 +394,16 @@ def test_bf16_storage_of_A():
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
     assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
-    ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=alg.LP_SCHEDULE,
-                         max_iter=50, tol=0.0, keep_x=50)
+    import refinement_model as RM
+    A = inst.to_scipy()
+    ref = RM.refined_iterates(A, inst.b, inst.c, inst.n, [], iters=50, correction_values=RM.bf16_round(A.data))
     worst = 0.0
     for k in (1, 5, 20, 50):
         st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, cg_eta=1e-9, cg_tol=0.0, **kw)
-        xr = ref.x_history[k - 1]
+        xr = ref[k - 1]
         worst = max(worst, np.linalg.norm(x - xr) / np.linalg.norm(xr))
     print("BF16 storage: worst relative iterate error over 50 iterations", worst)
-    assert worst <= 1e-2
+    assert worst <= 1e-4
 
 
 @pytest.mark.slow
@@ -412,3 +414,26 @@ def test_bf16_storage_large_lp():
     ours = _kkt_of(inst, x, y, z)
     assert kkt.max_residual(ours) <= 1e-6, ours
     assert abs(ours["obj_p"] - inst.obj_star) <= 1e-6 * abs(inst.obj_star)
+
+
+def test_schedule_on_the_device():
+    """The device rescales at l = 1 and at the paper's {300, 400, ...} (LP,
+    Section V-A) or {200, 300, ...} (SOCP, Section V-C) and nowhere else:
+    nine, respectively ten, rescalings in 1000 iterations, and the iterates
+    at l = 299, 300, 301 match the oracle's (cached FP64 operator: exact
+    projections on both sides), which a rescaling one iteration early or
+    late would break."""
+    inst = I.small_lp()
+    for sched, L, count in ((dict(cond_first=300, cond_period=100), alg.LP_SCHEDULE, 9),
+                            (dict(cond_first=200, cond_period=100), alg.SOCP_SCHEDULE, 10)):
+        with capi.Solver(inst, projection=capi.PROJ_DENSE, precision=capi.PREC_FP64, **sched) as s:
+            s.solve(tol=0.0, max_iter=1000)
+            assert capi.acs_debug_pass_counts(s.h)["rescalings"] == count
+        first = sched["cond_first"]
+        ref = alg.algorithm2(inst.to_scipy(), inst.b, inst.c, inst.n, [], L=L, max_iter=first + 1, tol=0.0,
+                             keep_x=first + 1)
+        for k in (first - 1, first, first + 1):
+            st, x, y, z, iters, res = _solve(inst, tol=0.0, max_iter=k, projection=capi.PROJ_DENSE,
+                                             precision=capi.PREC_FP64, **sched)
+            xr = ref.x_history[k - 1]
+            assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr), (first, k, np.linalg.norm(x - xr))

@@ -239,6 +239,71 @@ def test_conditioning_rule():
     assert alg.conditioning_exponent(np.full(5, 3.0), 9.2) == 1.0
 
 
+def test_literal_step11_switches_rescaling_off():
+    """Step 11 evaluated as printed: an o of 0 or inf makes the log spread
+    infinite, the exponent 0 and O = I (0^0 = inf^0 = 1); with nan as the
+    only non-finite entry the exponent stays positive and O gets a nan.  On
+    an instance with an empty column (x_j -> 0, z_j -> c_j > 0, so o_j = 0 from
+    the second rescaling on) the literal rule therefore reproduces the run
+    with no rescaling at all, iterate for iterate, while the oracle's rule
+    keeps rescaling."""
+    rng = np.random.default_rng(21)
+    x = np.abs(rng.standard_normal(6)) + 0.1
+    z = np.abs(rng.standard_normal(6)) + 0.1
+    for bad_x, bad_z in ((0.0, 1.0), (1.0, 0.0)):            # o = 0, o = inf
+        x0, z0 = x.copy(), z.copy()
+        x0[2], z0[2] = bad_x, bad_z
+        O, a = alg.conditioning_matrix_literal(x0, z0, 6, [], 9.2)
+        assert a == 0.0 and np.all(O == 1.0)
+    x0, z0 = x.copy(), z.copy()
+    x0[2] = z0[2] = 0.0                                       # o = nan only
+    O, a = alg.conditioning_matrix_literal(x0, z0, 6, [], 9.2)
+    assert a > 0.0 and np.isnan(O[2]) and np.all(np.isfinite(np.delete(O, 2)))
+    # without non-finite o both rules agree
+    O1, a1 = alg.conditioning_matrix_literal(x, z, 6, [], 1.0)
+    O2, a2 = alg.conditioning_matrix(x, z, 6, [], 1.0)
+    assert a1 == a2 and np.allclose(O1, O2, rtol=1e-14)
+    # an empty column with c_j = 0.7
+    inst = I.small_lp()
+    n = inst.n + 1
+    A = sp.hstack([inst.to_scipy(), sp.csr_matrix((inst.m, 1))]).tocsr()
+    c = np.concatenate([inst.c, [0.7]])
+    lit = alg.algorithm2(A, inst.b, c, n, [], L=alg.LP_SCHEDULE, max_iter=420, tol=0.0, keep_x=420,
+                         rule="literal")
+    off = alg.algorithm2(A, inst.b, c, n, [], L=alg.NO_SCHEDULE, max_iter=420, tol=0.0, keep_x=420)
+    ours = alg.algorithm2(A, inst.b, c, n, [], L=alg.LP_SCHEDULE, max_iter=420, tol=0.0)
+    assert [a for _, _, a in lit.O_history] == [1.0, 0.0, 0.0]
+    for k in (299, 300, 301, 420):
+        np.testing.assert_allclose(lit.x_history[k - 1], off.x_history[k - 1], rtol=0, atol=1e-12)
+    assert [l for l, _, _ in ours.O_history] == [1, 300, 400]
+    assert all(0.0 < a < 1.0 for _, _, a in ours.O_history[1:])
+
+
+def test_schedule_sets_of_the_paper():
+    """The periodic part of L as the paper states it: {300, 400, ...} for its
+    LPs (Section V-A), {200, 300, ...} for its SOCPs (Section V-C), plus
+    l = 1 (step 4).  The sets are written out here for l <= 1000 and compared
+    with Schedule's membership test and with the iterations at which
+    algorithm2 actually rescales."""
+    lp = {1, 300, 400, 500, 600, 700, 800, 900, 1000}
+    socp = {1, 200, 300, 400, 500, 600, 700, 800, 900, 1000}
+    assert {l for l in range(1, 1001) if l in alg.LP_SCHEDULE} | {1} == lp
+    assert {l for l in range(1, 1001) if l in alg.SOCP_SCHEDULE} | {1} == socp
+    assert 1 not in alg.LP_SCHEDULE and 299 not in alg.LP_SCHEDULE and 301 not in alg.LP_SCHEDULE
+    assert [l for l in range(1, 60) if l in alg.Schedule(first=5, period=7)] == [5, 12, 19, 26, 33, 40, 47, 54]
+    assert [l for l in range(1, 60) if l in alg.Schedule(first=5)] == [5]
+    assert [l for l in range(1, 60) if l in alg.Schedule(explicit=(3, 9), first=50, period=4)] == [3, 9, 50, 54, 58]
+    # the iterations at which Algorithm 2 rescales, on a tiny LP run to l = 1000
+    rng = np.random.default_rng(3)
+    A = sp.csr_matrix(rng.standard_normal((3, 6)))
+    xs = np.abs(rng.standard_normal(6))
+    b = A @ xs
+    c = np.abs(rng.standard_normal(6)) + 0.5
+    for L, want in ((alg.LP_SCHEDULE, lp), (alg.SOCP_SCHEDULE, socp)):
+        r = alg.algorithm2(A, b, c, 6, [], L=L, max_iter=1000, tol=0.0, check_every=10 ** 9)
+        assert {l for l, _, _ in r.O_history} == want
+
+
 def test_recast_is_identity_when_O_unchanged():
     # step 14 applied with the O that produced x, z (steps 20-21) returns the same s
     inst = I.small_lp()
