@@ -77,25 +77,11 @@ WORKLOADS = {
                   settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
 }
 BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
-# Random 4-byte gathers from an L2-resident 4 MB vector on this GB300 (152 SMs),
-# every load path (.ca, .cg, .nc), measured by a standalone probe: 275e9/s.
-GATHER_PROBE_G_PER_S = 275.0
-
-
-# DRAM bytes of one launch of the persistent kernel, from one ncu capture
-# (profiles/iter_kernel_large_lp.md), valid only for the kernel source it was
-# taken from: reported as null once acs_device.cuh, acs_iter.cu or
-# acs_internal.cuh change.
-TRAFFIC_RECORD = {"workload": "large_lp", "source_sha16": "85288478835299f6", "bytes": 357.23e9}
-
-
-def kernel_source_sha16() -> str:
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("acs_device.cuh", "acs_iter.cu", "acs_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2103_00736_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def nproc() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def make_instance(name: str):
@@ -110,10 +96,23 @@ def make_instance(name: str):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic byte model (per pass; nnz = true nonzeros, FP32 CG, FP64 outer)
+# algorithmic bytes
 # ---------------------------------------------------------------------------
 
+def survey_bytes(m: int, n: int, nnz: int, iters: int, cg_iters: int, checks: int, conds: int) -> float:
+    """The hot path's algorithmic bytes of one solve by the fixed formula of
+    the scope table (FP32 values and int32 indices of A and A' stored, each
+    read once per pass): per outer iteration 16 nnz + 20 n + 12 m (the A and
+    A' passes, abs_K, the update), per CG iteration 16 nnz + 8 n + 20 m, per
+    KKT check 24 nnz (the FP64 pair of passes), per rescaling 8 nnz."""
+    return (iters * (16.0 * nnz + 20 * n + 12 * m) + cg_iters * (16.0 * nnz + 8 * n + 20 * m)
+            + checks * 24.0 * nnz + conds * 8.0 * nnz)
+
+
 def algorithmic_bytes(m: int, n: int, nnz: int, counters, iters: int) -> float:
+    """This implementation's own byte model: every pass it actually runs
+    (pass counters of the solve), with its FP64 outer passes at 12 bytes a
+    nonzero."""
     n_cg_A, n_cg_AT, n64_A, n64_AT, n_cond, n_chk = [int(v) for v in counters]
     b = 0.0
     b += n_cg_AT * (8.0 * nnz + 4 * m + 8 * n)          # t = O^2 A'u: val+col, u gathered, O2 in, t out
@@ -212,10 +211,13 @@ class ClockSampler:
 HBM_SPEC_GBS = 7900.0   # nominal HBM3e bandwidth of one GB300, for context beside the measured peak
 
 
-def roofline_entry(kernel: str, alg_bytes: float, launch_ms: float, traffic=None, **extra) -> dict:
+def roofline_entry(kernel: str, alg_bytes: float, launch_ms: float, traffic=None, own_bytes=None,
+                   **extra) -> dict:
     """The HBM roofline object of a kernel: algorithmic bytes per launch over the
     launch's device time, against the measured copy bandwidth (and, for context,
-    the nominal one); traffic = DRAM bytes per launch from an ncu capture, or None."""
+    the nominal one); traffic = DRAM bytes per launch from an ncu capture of the
+    same build, or None.  own_bytes: the implementation's own pass-count model,
+    reported beside (not in place of) alg_bytes."""
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -223,6 +225,9 @@ def roofline_entry(kernel: str, alg_bytes: float, launch_ms: float, traffic=None
            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
            "spec_peak": HBM_SPEC_GBS, "frac_of_spec": achieved / HBM_SPEC_GBS,
            "traffic_gbs": traffic / (launch_ms / 1e3) / 1e9 if traffic else None}
+    if own_bytes is not None:
+        own = own_bytes / (launch_ms / 1e3) / 1e9
+        out["own_model"] = {"bytes_per_launch": own_bytes, "achieved": own, "frac": own / peak}
     out.update(extra)
     return out
 
@@ -256,11 +261,12 @@ def cpu_sample(workload: str, iters: int) -> dict:
     A = inst.to_scipy()
     st = WORKLOADS[workload]["settings"]
     L = alg.Schedule(first=st["cond_first"], period=st["cond_period"])
+    dims = {"m": inst.m, "n": inst.n, "nnz": inst.nnz}
     if workload == "small_lp":
         t0 = time.perf_counter()
         r = alg.algorithm2(A, inst.b, inst.c, inst.n_orth, inst.soc_dims, mu=st["mu"], t=st["t"], L=L,
                            max_iter=MAX_ITER, tol=TOL, check_every=10)
-        return {"complete_s": time.perf_counter() - t0, "iters": r.iters, "status": r.status}
+        return {"complete_s": time.perf_counter() - t0, "iters": r.iters, "status": r.status, **dims}
     stamps = []
     t0 = time.perf_counter()
 
@@ -271,7 +277,7 @@ def cpu_sample(workload: str, iters: int) -> dict:
                    max_iter=1 + iters, tol=0.0, check_every=10 ** 9, on_iter=hook)
     first = stamps[0] - t0
     per_iter = (stamps[-1] - stamps[0]) / max(1, len(stamps) - 1)
-    return {"first_iter_s": first, "per_iter_s": per_iter, "iters": len(stamps)}
+    return {"first_iter_s": first, "per_iter_s": per_iter, "iters": len(stamps), **dims}
 
 
 def _stratified(sizes, k: int):
@@ -324,8 +330,12 @@ def _cpu_sample_serve(alg, iters: int) -> dict:
             "distinct": SERVE_DISTINCT}
 
 
-def run_cpu_sample_subprocess(workload: str, iters: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def run_cpu_sample_subprocess(workload: str, iters: int, threads: int = 1) -> dict:
+    """The oracle sample in a child process whose BLAS / OpenMP pools have
+    `threads` threads (the oracle's sparse products run on one core either way;
+    its dense factorisations and vector operations use the pool)."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
                         "--cpu-iters", str(iters)], capture_output=True, text=True, env=env, timeout=1800)
     for line in r.stdout.splitlines()[::-1]:
@@ -338,31 +348,42 @@ def oracle_baseline(workload: str, args, rank: int, world: int):
     """The cpu_baseline object of a bench line (rank 0 of a 1-GPU run only)."""
     if rank != 0 or world != 1 or args.no_cpu:
         return None
-    v, desc = oracle_solves_per_s(run_cpu_sample_subprocess(workload, args.cpu_iters), workload)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    return oracle_runs(workload, args.cpu_iters)
 
 
-def oracle_solves_per_s(sample: dict, workload: str) -> tuple[float, str]:
+def oracle_runs(workload: str, iters: int) -> dict:
+    """The oracle timed on one host thread and on all of them; the line's
+    value is the faster of the two, and both are listed."""
+    runs = []
+    for threads in sorted({1, nproc()}):
+        v, desc = oracle_solves_per_s(run_cpu_sample_subprocess(workload, iters, threads), workload, threads)
+        runs.append({"value": v, "cores": threads, "sample": desc})
+    best = max(runs, key=lambda r: r["value"])
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle",
+            "sample": best["sample"], "runs": runs, "host_cores": nproc()}
+
+
+def oracle_solves_per_s(sample: dict, workload: str, threads: int = 1) -> tuple[float, str]:
     if "members_s" in sample:
         return sample["solved"] / sample["members_s"], (
-            f"FP64 oracle, 1 thread: {sample['members']} of the {sample['count']} members, stratified by size "
+            f"FP64 oracle, {threads} thread(s): {sample['members']} of the {sample['count']} members, stratified by size "
             f"(m {sample['m_min']}..{sample['m_max']}), solved one after another to {TOL:g} KKT within "
             f"{BATCH_MAX_ITER} iterations each: {sample['solved']} solved in {sample['members_s']:.1f} s; "
             f"the batch's rate taken as the sample's")
     if "requests_s" in sample:
         return sample["requests"] / sample["requests_s"], (
-            f"FP64 oracle, 1 thread: {sample['requests']} of the {sample['distinct']} distinct requests, "
+            f"FP64 oracle, {threads} thread(s): {sample['requests']} of the {sample['distinct']} distinct requests, "
             f"stratified by size (m {sample['m_min']}..{sample['m_max']}); each one's first iterations timed "
             f"and extrapolated to the oracle's median count for its type ({ORACLE_ITERS_SERVE_LP} for LPs, "
             f"{ORACLE_ITERS_SERVE_SOC} with cones), every iteration costed like the sampled ones: "
             f"{sample['requests_s']:.1f} s for the sample, one request after another")
     if "complete_s" in sample:
-        return 1.0 / sample["complete_s"], (f"FP64 oracle, 1 thread: complete solve to {TOL:g} KKT, "
+        return 1.0 / sample["complete_s"], (f"FP64 oracle, {threads} thread(s): complete solve to {TOL:g} KKT, "
                                             f"{sample['iters']} iterations ({sample['status']}), "
                                             f"{sample['complete_s']:.2f} s")
     t = sample["per_iter_s"]
-    head = (f"FP64 oracle, 1 thread: first iteration {sample['first_iter_s']:.1f} s, "
-            f"{sample['iters'] - 1} more at {t:.2f} s each; ")
+    head = (f"FP64 oracle, {threads} thread(s), EXTRAPOLATED from {sample['iters']} timed iterations: "
+            f"first iteration {sample['first_iter_s']:.1f} s, {sample['iters'] - 1} more at {t:.2f} s each; ")
     if workload == "large_lp":
         n_it, n_pre, ratio = ORACLE_ITERS_LARGE_LP, ORACLE_PRE_COND_ITERS, ORACLE_LATE_COST_RATIO
         how = (f"extrapolated to the {n_it} iterations the oracle needs for this instance, the "
@@ -417,6 +438,42 @@ def solver_overrides(args) -> dict:
         out["precision"] = PRECISIONS[args.precision]
     if args.col_block is not None:
         out["col_block"] = args.col_block
+    return out
+
+
+SUB_TOL = 2e-7          # the batched and served records: relative objective error <= 1e-6 needs it
+
+
+def sub_records(args) -> dict:
+    """The batched and served forms at the accuracy bar, beside the large LP:
+    a 1024-member batch of the batched recipe (batched against the plain
+    single-problem form, size-stratified sample) and one saturation-rate
+    point of the served stream (served against plain, p50/p99)."""
+    import argparse as _ap
+    out = {}
+    b = _ap.Namespace(**vars(args))
+    b.batch_count, b.steps, b.warmup, b.tol, b.plain_sample = 1024, 2, 3, SUB_TOL, 12
+    b.no_e2e, b.no_cpu = True, True
+    L = batch_arm(b, emit=False)
+    out["batch"] = {"workload": "batch of 1024 (batched recipe: m log-uniform [50, 2000], n = 2.5 m, 2 %, "
+                                "a quarter sharing one 1000 x 2500 A)",
+                    "value": L["value"], "unit": UNIT, "ms_per_step": L["ms_per_step"], "steps": b.steps,
+                    "warmup": b.warmup, "tol": SUB_TOL, "members": L["config"]["members"],
+                    "solved": L["config"]["solved"], "plain": L["plain"],
+                    "batched_over_plain": L["batched_over_plain"],
+                    "accuracy_sampled_max": L["config"]["accuracy_sampled_max"],
+                    "mapping": L["config"]["mapping"], "cuda_graph": L["config"]["cuda_graph"],
+                    "roofline": L["roofline"], "clocks": L["clocks"]}
+    v = _ap.Namespace(**vars(args))
+    v.rates, v.serve_requests, v.serve_distinct, v.tol, v.no_cpu = "2000", 96, 48, SUB_TOL, True
+    L = serve_arm(v, emit=False)
+    pt = L["sweep"][0]
+    out["served"] = {"workload": "served stream at 2000 requests/s (saturation), 96 requests over 48 distinct "
+                                 "mixed LP/SOCP requests, m log-uniform [100, 1e5]",
+                     "value": pt["solves_per_s"], "unit": UNIT, "p50_ms": pt["p50_ms"], "p99_ms": pt["p99_ms"],
+                     "solved": pt["solved"], "requests": pt["requests"], "tol": SUB_TOL, "plain": L["plain"],
+                     "served_over_plain": L["served_over_plain"], "accuracy_max": L["config"]["accuracy_max"],
+                     "rounds": pt["rounds"], "clocks": L["clocks"]}
     return out
 
 
@@ -490,16 +547,17 @@ def gpu_arm(args) -> None:
 
     # roofline of the persistent iteration kernel (the only kernel of a solve
     # besides four small initialisation launches; its FP64 continuation
-    # launch returns at once unless the FP32 loop handed over)
-    alg_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
+    # launch returns at once unless the FP32 loop handed over): the scope
+    # table's byte formula, and beside it the implementation's own model
+    own_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
+    alg_bytes = survey_bytes(inst.m, inst.n, inst.nnz, iters, int(res[6]), int(counters[5]), int(counters[4]))
     # every stored entry of every matrix pass costs one random gather from an
     # L2-resident vector: the rate that actually bounds these passes
     n_cg_A, n_cg_AT, n64_A, n64_AT = (int(v) for v in counters[:4])
     gathers = float(n_cg_A + n64_A) * info["padded_A"] + float(n_cg_AT + n64_AT) * info["padded_AT"]
     traffic = args.traffic
-    if traffic is None and args.workload == TRAFFIC_RECORD["workload"] and tol > 0 \
-            and kernel_source_sha16() == TRAFFIC_RECORD["source_sha16"]:
-        traffic = TRAFFIC_RECORD["bytes"]
+    # the device's random-gather rate, measured now (4 MB vector, L2-resident)
+    gather_probe = capi.acs_bench_gather(1 << 20, 0, device=local)
 
     # end to end through the C ABI with host buffers, every step: upload,
     # solve, read back x, y, s
@@ -530,6 +588,8 @@ def gpu_arm(args) -> None:
     capi.acs_problem_destroy(h)
 
     cpu = oracle_baseline(args.workload, args, rank, world)
+    subs = sub_records(args) if (args.workload == "large_lp" and not args.no_sub and world == 1 and rank == 0
+                                 and tol > 0) else None
 
     if rank == 0:
         line = {
@@ -543,12 +603,15 @@ def gpu_arm(args) -> None:
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (A and A' in FP32+FP64 ~0.6 GB)"},
             "gather": {"achieved_g_per_s": gathers / (launch_ms / 1e3) / 1e9,
-                       "probe_g_per_s": GATHER_PROBE_G_PER_S,
-                       "frac": gathers / (launch_ms / 1e3) / 1e9 / GATHER_PROBE_G_PER_S,
+                       "probe_g_per_s": gather_probe / 1e9,
+                       "frac": gathers / (launch_ms / 1e3) / gather_probe,
                        "note": "matrix passes x stored entries / launch time, against random 4-byte "
-                               "gathers from an L2-resident vector measured by a standalone probe"},
-            "roofline": roofline_entry("iter_kernel<float>", alg_bytes, launch_ms, traffic,
-                                       step_ms_median=statistics.median(step_ms)),
+                               "gathers from an L2-resident 4 MB vector measured in this run "
+                               "(acs_bench_gather)"},
+            "roofline": roofline_entry("iter_kernel<float>", alg_bytes, launch_ms, traffic, own_bytes=own_bytes,
+                                       step_ms_median=statistics.median(step_ms),
+                                       bytes_formula="survey: iters*(16 nnz+20 n+12 m) + cg*(16 nnz+8 n+20 m)"
+                                                     " + checks*24 nnz + rescalings*8 nnz"),
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": 6 * args.steps,
@@ -558,6 +621,8 @@ def gpu_arm(args) -> None:
         }
         if phases is not None:
             line["phases_ms"] = phases
+        if subs:
+            line.update(subs)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -576,7 +641,7 @@ def member_bytes(m: int, n: int, nnz: int, c) -> float:
     return b
 
 
-def batch_arm(args) -> None:
+def batch_arm(args, emit: bool = True) -> dict:
     import numpy as np
     import torch
     from paper_2103_00736_gb300 import capi, instances as I
@@ -626,7 +691,7 @@ def batch_arm(args) -> None:
     ms_step = statistics.median(step_ms)
     value = solved / (ms_step / 1e3)
     # accuracy of a sample of solved members, from the problem data
-    idx = np.linspace(0, len(mem) - 1, 16).astype(int)
+    idx = np.linspace(0, len(mem) - 1, 64).astype(int)
     checked = []
     for i in idx:
         s_i, x, y, z, it_i, r_i = capi.acs_batch_get(h, int(i), mem[i].m, mem[i].n)
@@ -639,7 +704,7 @@ def batch_arm(args) -> None:
     # solve after another, extrapolated to the whole batch
     order = np.argsort([x.nnz for x in mem])
     sample = order[np.linspace(0, len(mem) - 1, args.plain_sample).astype(int)] if args.plain_sample > 0 else []
-    plain_ms, plain_solved = [], 0
+    plain_ms, plain_solved, plain_checked = [], 0, []
     for i in sample:
         x = mem[i]
         hs = capi.acs_problem_create(x.m, x.n, x.row_ptr, x.col, x.val, x.b, x.c, x.n_orth, x.soc_dims,
@@ -653,6 +718,9 @@ def batch_arm(args) -> None:
         torch.cuda.synchronize()
         plain_ms.append(a.elapsed_time(b2))
         plain_solved += capi.acs_get_residuals(hs)[0] == capi.SOLVED
+        st_p, xp, yp, zp, _, _ = capi.acs_get(hs, x.m, x.n)
+        if st_p == capi.SOLVED:
+            plain_checked.append(affine_residuals(x, xp, yp, zp))
         capi.acs_problem_destroy(hs)
     if len(sample):
         plain_total_ms = float(np.mean(plain_ms)) * len(mem)
@@ -693,6 +761,7 @@ def batch_arm(args) -> None:
                    "l2": "inputs larger than L2 (distinct matrices ~2.6 GB)"},
         "plain": {"value": plain_value, "unit": UNIT, "sample": int(len(sample)),
                   "sample_solved": int(plain_solved), "mean_ms": float(np.mean(plain_ms)),
+                  "accuracy_max": worst_of(plain_checked),
                   "how": "single-problem API, one member after another, size-stratified sample "
                          "extrapolated to all members"},
         "batched_over_plain": value / plain_value if plain_value > 0 else None,
@@ -700,11 +769,12 @@ def batch_arm(args) -> None:
         "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps,
         "cpu_baseline": oracle_baseline("batch", args, rank, world),
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def serve_arm(args) -> None:
+def serve_arm(args, emit: bool = True) -> dict:
     """Continuous batching under a Poisson stream: for each arrival rate, the
     stream's requests are submitted at their arrival times by client threads;
     latency runs from the scheduled arrival to the results in host memory."""
@@ -724,11 +794,15 @@ def serve_arm(args) -> None:
     # single-problem API (create, solve, read back), each with its schedule
     t0 = time.perf_counter()
     plain_ok = 0
+    plain_checked = []
     for r in reqs:
         sched = capi.SOCP_SCHEDULE if len(r.soc_dims) else capi.LP_SCHEDULE
         with capi.Solver(r, device=local, **sched) as sv:
-            plain_ok += sv.solve(tol=args.tol, max_iter=args.batch_max_iter) == capi.SOLVED
-            sv.get()
+            st_p = sv.solve(tol=args.tol, max_iter=args.batch_max_iter)
+            plain_ok += st_p == capi.SOLVED
+            _, xp, yp, zp, _, _ = sv.get()
+        if st_p == capi.SOLVED:
+            plain_checked.append(affine_residuals(r, xp, yp, zp))
     plain_s = time.perf_counter() - t0
     plain_value = plain_ok / plain_s
 
@@ -744,7 +818,7 @@ def serve_arm(args) -> None:
             warm_ok += st == capi.SOLVED
             if st == capi.SOLVED:
                 checked.append(affine_residuals(reqs[k], x, y, z))
-        accuracy = worst_of(checked)
+        accuracy_warmup = worst_of(checked)
         clocks.start()
         for ri, rate in enumerate(rates):
             n_req = args.serve_requests
@@ -776,6 +850,8 @@ def serve_arm(args) -> None:
                 S.wait(rid, 1200.0)
                 st, x, y, z, it, res, ms = S.result(rid)
                 ok += st == capi.SOLVED
+                if st == capi.SOLVED:
+                    checked.append(affine_residuals(reqs[k % len(reqs)], x, y, z))
                 lat.append(lag * 1e3 + ms)
                 done_at.append(arr[k] + lag + ms / 1e3)
             span = max(done_at) - arr[0]
@@ -787,6 +863,7 @@ def serve_arm(args) -> None:
                           "large_alone": int(after["large"] - before["large"]),
                           "mean_active": after["active_mean"], "pool_peak_bytes": int(after["pool_peak_bytes"])})
         clk = clocks.stop()
+    accuracy = worst_of(checked)
     best = max(table, key=lambda d: d["solves_per_s"])
     line = {
         "metric": METRIC, "value": best["solves_per_s"], "unit": UNIT, "n_gpus": world, "steps": len(rates),
@@ -799,6 +876,7 @@ def serve_arm(args) -> None:
                    "schedules": "LP: t=9.2, L={300,400,...}; with cones: t=1.7, L={200,300,...}"},
         "sweep": table,
         "plain": {"value": plain_value, "unit": UNIT, "solved": int(plain_ok), "requests": len(reqs),
+                  "accuracy_max": worst_of(plain_checked),
                   "how": "single-problem API, create+solve+read back, one request after another"},
         "served_over_plain": best["solves_per_s"] / plain_value if plain_value > 0 else None,
         "clocks": clk,
@@ -813,8 +891,9 @@ def serve_arm(args) -> None:
         "gpu_launches": int(sum(t["rounds"] + 6 * t["large_alone"] for t in table)),
         "cpu_baseline": oracle_baseline("serve", args, rank, world),
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def reference_arm(args) -> None:
@@ -822,14 +901,17 @@ def reference_arm(args) -> None:
     if rank != 0:
         return
     t0 = time.perf_counter()
-    sample = run_cpu_sample_subprocess(args.workload, max(1, args.steps))
-    v, desc = oracle_solves_per_s(sample, args.workload)
+    threads = nproc()
+    sample = run_cpu_sample_subprocess(args.workload, max(1, args.steps), threads)
+    v, desc = oracle_solves_per_s(sample, args.workload, threads)
+    cfg = {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "tol": TOL}
+    cfg.update({k: sample[k] for k in ("m", "n", "nnz") if k in sample})
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "tol": TOL},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": cfg,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t0,
     }
@@ -848,8 +930,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch from an ncu capture of the same kernel build")
-    ap.add_argument("--tol", type=float, default=TOL,
-                    help="KKT tolerance of a step (0 with --max-iter: a truncated solve, for profiling)")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="KKT tolerance of a step (0 with --max-iter: a truncated solve, for profiling); "
+                         f"default {TOL:g}, and {SUB_TOL:g} for the batch and serve workloads")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -868,7 +951,10 @@ def main():
     ap.add_argument("--col-block", type=int, default=None,
                     help="column-block width limit of the FP32 passes (-1: off; default: the library's)")
     ap.add_argument("--phases", action="store_true", help="add the per-phase device times of a warm-up solve")
+    ap.add_argument("--no-sub", action="store_true", help="leave out the batched and served records")
     args = ap.parse_args()
+    if args.tol is None:
+        args.tol = SUB_TOL if args.workload in ("batch", "serve") else TOL
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.workload, args.cpu_iters)), flush=True)
         return

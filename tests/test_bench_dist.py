@@ -106,7 +106,9 @@ def test_oracle_extrapolation_rules():
 
 
 def test_oracle_baseline_object():
-    """Only rank 0 of a 1-GPU run times the oracle; the object has the contract's keys."""
+    """Only rank 0 of a 1-GPU run times the oracle; the object has the
+    contract's keys, its value is the faster of the one-thread and the
+    all-cores run, and both runs are listed."""
     import argparse
     import bench
     a = argparse.Namespace(no_cpu=False, cpu_iters=2)
@@ -114,5 +116,10 @@ def test_oracle_baseline_object():
     assert bench.oracle_baseline("small_lp", a, 0, 2) is None
     assert bench.oracle_baseline("small_lp", argparse.Namespace(no_cpu=True, cpu_iters=2), 0, 1) is None
     b = bench.oracle_baseline("small_lp", a, 0, 1)
-    assert set(b) == {"value", "unit", "cores", "kind", "sample"}
-    assert b["value"] > 0 and b["cores"] == 1 and b["kind"] == "oracle" and "complete solve" in b["sample"]
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(b)
+    assert b["value"] > 0 and b["kind"] == "oracle" and "complete solve" in b["sample"]
+    runs = b["runs"]
+    assert [r["cores"] for r in runs] == sorted({1, bench.nproc()}) and b["host_cores"] == bench.nproc()
+    best = max(runs, key=lambda r: r["value"])
+    assert b["value"] == best["value"] and b["cores"] == best["cores"]
+    assert all(f"{r['cores']} thread(s)" in r["sample"] for r in runs)
