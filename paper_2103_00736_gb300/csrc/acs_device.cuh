@@ -1331,55 +1331,110 @@ __device__ __noinline__ void phase_dense_assemble(const IterParams<T>& P) {
     }
 }
 
-// Step k of the right-looking Cholesky factorisation (one team barrier per
-// step): scale column k-1 by its pivot, and update the trailing lower
-// triangle with column k: M_ij -= M_ik M_jk / M_kk for k < j <= i.  The two
-// touch disjoint columns.  The diagonal keeps the pivots d_k (L_kk = sqrt(d_k));
-// below it the columns hold L.  Row i belongs to the same warp at every
-// step; other rows are read past L1.
-// A pivot below 1e-13 of the row's original diagonal (jinv = 1 / diag M)
-// marks row k of A as linearly dependent on the rows before it (rank-
-// deficient A): the direction is dropped -- the pivot becomes +inf, so the
-// column scales to zero, nothing is eliminated with it, and row k of L^{-1}
-// is zero.  For a consistent right-hand side (b in range(A)) this solves the
-// remaining independent equations, which imply the dropped one.  Returns
-// false only for a pivot that is negative beyond rounding or not a number.
-constexpr int kColStage = 2048;   // column entries of a Cholesky step staged in shared memory
+// Pivot rule of the factorisation: a pivot below 1e-13 of the row's
+// original diagonal (jinv = 1 / diag M) marks row k of A as linearly
+// dependent on the rows before it (rank-deficient A): the direction is
+// dropped -- the pivot becomes +inf, its column of L is zero, nothing is
+// eliminated with it, and row k of L^{-1} is zero.  For a consistent
+// right-hand side (b in range(A)) this solves the remaining independent
+// equations, which imply the dropped one.  A pivot negative beyond rounding
+// or not a number fails the factorisation.
+// Blocked right-looking Cholesky: kCholB columns per step and two team
+// barriers per step (instead of one per column), so the trailing triangle is
+// read and rewritten once per kCholB columns.  The result has the layout of
+// the column-by-column version: the pivot d_k on the diagonal (+inf for a
+// dependent row), L below it.
+//   Step at column k0, block b = min(kCholB, m - k0):
+//   1. every CTA factors the diagonal block D = M[k0.., k0..] (b x b) in
+//      shared memory, column by column with the pivot rule above, so every
+//      CTA takes the same decisions without communicating; CTA 0 writes it
+//      back;
+//   2. every row i below the block is solved against it (warp per row):
+//      L_ik = (M_ik - sum_{t<k} L_it L_kt) s_k with s_k = 1/sqrt(d_k) (0 for
+//      a dependent row);
+//   -- team barrier --
+//   3. the trailing lower triangle is updated by the panel (warp per row i,
+//      lanes over the columns j <= i): M_ij -= sum_t L_it L_jt.
+//   -- team barrier --
+// Returns false (in every thread of the team) only for a pivot that is
+// negative beyond rounding or not a number.
+constexpr int kCholB = 16;
 
 template <typename T>
-__device__ __forceinline__ bool dense_chol_step(double* M, int m, int k, const T* jinv) {
-    // column k (rows k..m-1), read once per CTA into shared memory: every
-    // row's update needs it, and in row-major storage it is strided
-    __shared__ double colk[kColStage];
-    const bool staged = m <= kColStage;
-    const int lane = threadIdx.x & 31;
-    const double s = (k > 0) ? 1.0 / sqrt(__ldcg(M + (size_t)(k - 1) * m + (k - 1))) : 0.0;
-    if (staged && k < m) {
-        for (int j = k + (int)threadIdx.x; j < m; j += (int)blockDim.x) colk[j] = __ldcg(M + (size_t)j * m + k);
-        __syncthreads();
+__device__ __noinline__ bool dense_chol_panel(double* M, int m, int k0, const T* jinv) {
+    __shared__ double D[kCholB][kCholB];
+    __shared__ double sc[kCholB];
+    __shared__ int bad;
+    const int b = min(kCholB, m - k0);
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int r = e / b, c = e % b;
+        D[r][c] = r >= c ? __ldcg(M + (size_t)(k0 + r) * m + k0 + c) : 0.0;
     }
-    double inv = 0.0;
-    if (k < m) {
-        const double d = staged ? colk[k] : __ldcg(M + (size_t)k * m + k);
-        const double tau = 1e-13 / (double)__ldcg(jinv + k);
-        if (d != d || d < -1e3 * tau) return false;
-        const bool dep = !(d > tau) || d == INFINITY;
-        if (dep && team_rank() == 0 && threadIdx.x == 0) M[(size_t)k * m + k] = INFINITY;
-        inv = dep ? 0.0 : 1.0 / d;
-    }
-    for (int i = global_warp(); i < m; i += global_warps()) {
-        double* Mi = M + (size_t)i * m;
-        if (k < i && k < m && inv != 0.0) {
-            const double f = (staged ? colk[i] : __ldcg(Mi + k)) * inv;
-            if (staged)
-                for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, colk[j], Mi[j]);
-            else
-                for (int j = k + 1 + lane; j <= i; j += 32) Mi[j] = fma(-f, __ldcg(M + (size_t)j * m + k), Mi[j]);
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {                              // one warp factors the block
+        const int lane = threadIdx.x;
+        for (int k = 0; k < b; ++k) {
+            const double d = D[k][k];
+            const double tau = 1e-13 / (double)__ldcg(jinv + k0 + k);
+            const bool fail = d != d || d < -1e3 * tau;
+            const bool dep = !(d > tau) || d == INFINITY;
+            const double s = dep ? 0.0 : 1.0 / sqrt(d);
+            __syncwarp();
+            if (lane == 0) {
+                if (fail) bad = 1;
+                sc[k] = s;
+                D[k][k] = dep ? INFINITY : d;
+            }
+            if (lane > k && lane < b) D[lane][k] *= s;  // column k of L in the block
+            __syncwarp();
+            for (int i = k + 1 + lane; i < b; i += 32)   // rows below: update columns k+1 .. i
+                for (int j = k + 1; j <= i; ++j) D[i][j] = fma(-D[i][k], D[j][k], D[i][j]);
+            __syncwarp();
         }
-        if (k > 0 && i >= k && lane == 0) Mi[k - 1] *= s;
     }
-    if (staged) __syncthreads();      // colk is rewritten at the next step
+    __syncthreads();
+    if (bad) return false;                               // CTA-uniform (and team-uniform: same data)
+    if (team_rank() == 0)
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+            const int r = e / b, c = e % b;
+            if (r >= c) M[(size_t)(k0 + r) * m + k0 + c] = D[r][c];
+        }
+    // panel rows below the block, warp per row, lane k holds L_ik
+    const int lane = threadIdx.x & 31;
+    for (int i = k0 + b + global_warp(); i < m; i += global_warps()) {
+        double* Mi = M + (size_t)i * m + k0;
+        double x = lane < b ? __ldcg(Mi + lane) : 0.0;
+        for (int k = 0; k < b; ++k) {
+            const double xk = __shfl_sync(0xffffffffu, x, k) * sc[k];   // final L_ik
+            if (lane == k) x = xk;
+            if (lane > k && lane < b) x = fma(-xk, D[lane][k], x);
+        }
+        if (lane < b) Mi[lane] = x;
+    }
     return true;
+}
+
+// Step 3 of the blocked factorisation: M_ij -= sum_t L_it L_jt for
+// k0 + b <= j <= i < m, with L the panel just written.
+static __device__ __noinline__ void dense_chol_trailing(double* M, int m, int k0) {
+    const int b = min(kCholB, m - k0);
+    const int lane = threadIdx.x & 31;
+    for (int i = k0 + b + global_warp(); i < m; i += global_warps()) {
+        const double* Li = M + (size_t)i * m + k0;
+        double li[kCholB];
+#pragma unroll
+        for (int t = 0; t < kCholB; ++t) li[t] = t < b ? __ldcg(Li + t) : 0.0;
+        double* Mi = M + (size_t)i * m;
+        for (int j = k0 + b + lane; j <= i; j += 32) {
+            const double* Lj = M + (size_t)j * m + k0;
+            double acc = 0.0;
+#pragma unroll
+            for (int t = 0; t < kCholB; ++t)
+                if (t < b) acc = fma(li[t], __ldcg(Lj + t), acc);
+            Mi[j] -= acc;
+        }
+    }
 }
 
 // X = L^{-1} (column-major) by forward substitution, warp per column c:
@@ -1582,11 +1637,14 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 factor_ok = false;
                 phase_dense_assemble(P);
                 ACS_SYNC(PH_DENSE_FACTOR);
-                for (int k = 0; k <= P.m && dense; ++k) {
-                    if (!dense_chol_step(sync_smem().dM, P.m, k, P.V.jinv)) {
+                for (int k0 = 0; k0 < P.m && dense; k0 += kCholB) {
+                    if (!dense_chol_panel(sync_smem().dM, P.m, k0, P.V.jinv)) {
                         dense = false;
                         dense_failed = true;
                     }
+                    ACS_SYNC(PH_DENSE_FACTOR);
+                    if (!dense) break;
+                    dense_chol_trailing(sync_smem().dM, P.m, k0);
                     ACS_SYNC(PH_DENSE_FACTOR);
                 }
                 if (!ok) break;
