@@ -75,7 +75,13 @@ WORKLOADS = {
     "batch": dict(desc="4096 LPs in one persistent launch: m log-uniform [50,2000], n=2.5m, 2% density, "
                        "N(0,1); members 0..1023 share one 1000x2500 A",
                   settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
+    "dense_lp": dict(desc="dense LP of Section V-A: m=floor(0.8n), A U[-1,1], b=A|xdot|, xdot and c N(0,1)",
+                     settings=dict(cond_first=300, cond_period=100, t=9.2, mu=1.0)),
+    "dense_socp": dict(desc="dense SOCP of Section V-C: m=floor(0.8n), A U[-1,1], b=A abs_K(xdot), xdot and "
+                            "c U[0,1], Lorentz cones of size h",
+                       settings=dict(cond_first=200, cond_period=100, t=1.7, mu=1.0)),
 }
+DENSE_N = {"dense_lp": 10000, "dense_socp": 2900}
 BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
 def nproc() -> int:
     try:
@@ -84,8 +90,12 @@ def nproc() -> int:
         return os.cpu_count() or 1
 
 
-def make_instance(name: str):
+def make_instance(name: str, dense_n: int | None = None, cone_h: int = 10):
     from paper_2103_00736_gb300 import instances as I
+    if name == "dense_lp":
+        return I.dense_lp(dense_n or DENSE_N[name])
+    if name == "dense_socp":
+        return I.dense_socp(dense_n or DENSE_N[name], cone_h)
     if name == "large_lp":
         return I.large_lp()
     if name == "socp":
@@ -246,7 +256,7 @@ def measured_peak_hbm():
 # CPU oracle sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def cpu_sample(workload: str, iters: int) -> dict:
+def cpu_sample(workload: str, iters: int, dense_n: int | None = None, cone_h: int = 10) -> dict:
     """Time the FP64 oracle on the workload: the first iteration (includes the
     l = 1 conditioning, i.e. the factor/solve set-up) and `iters` further ones;
     the small LP is solved to completion instead (about a second); the batch
@@ -257,7 +267,7 @@ def cpu_sample(workload: str, iters: int) -> dict:
         return _cpu_sample_batch(alg, iters)
     if workload == "serve":
         return _cpu_sample_serve(alg, iters)
-    inst = make_instance(workload)
+    inst = make_instance(workload, dense_n, cone_h)
     A = inst.to_scipy()
     st = WORKLOADS[workload]["settings"]
     L = alg.Schedule(first=st["cond_first"], period=st["cond_period"])
@@ -330,40 +340,48 @@ def _cpu_sample_serve(alg, iters: int) -> dict:
             "distinct": SERVE_DISTINCT}
 
 
-def run_cpu_sample_subprocess(workload: str, iters: int, threads: int = 1) -> dict:
+def run_cpu_sample_subprocess(workload: str, iters: int, threads: int = 1, dense_n: int | None = None,
+                              cone_h: int = 10) -> dict:
     """The oracle sample in a child process whose BLAS / OpenMP pools have
     `threads` threads (the oracle's sparse products run on one core either way;
     its dense factorisations and vector operations use the pool)."""
     t = str(int(threads))
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
-                        "--cpu-iters", str(iters)], capture_output=True, text=True, env=env, timeout=1800)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload, "--cpu-iters",
+           str(iters), "--cone-h", str(cone_h)]
+    if dense_n:
+        cmd += ["--dense-n", str(dense_n)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     for line in r.stdout.splitlines()[::-1]:
         if line.startswith("{"):
             return json.loads(line)
     raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
 
 
-def oracle_baseline(workload: str, args, rank: int, world: int):
+def oracle_baseline(workload: str, args, rank: int, world: int, gpu_iters: int | None = None):
     """The cpu_baseline object of a bench line (rank 0 of a 1-GPU run only)."""
     if rank != 0 or world != 1 or args.no_cpu:
         return None
-    return oracle_runs(workload, args.cpu_iters)
+    return oracle_runs(workload, args.cpu_iters, getattr(args, "dense_n", None), getattr(args, "cone_h", 10),
+                       gpu_iters)
 
 
-def oracle_runs(workload: str, iters: int) -> dict:
+def oracle_runs(workload: str, iters: int, dense_n: int | None = None, cone_h: int = 10,
+                gpu_iters: int | None = None) -> dict:
     """The oracle timed on one host thread and on all of them; the line's
     value is the faster of the two, and both are listed."""
     runs = []
     for threads in sorted({1, nproc()}):
-        v, desc = oracle_solves_per_s(run_cpu_sample_subprocess(workload, iters, threads), workload, threads)
+        sample = run_cpu_sample_subprocess(workload, iters, threads, dense_n, cone_h)
+        v, desc = oracle_solves_per_s(sample, workload, threads, gpu_iters)
         runs.append({"value": v, "cores": threads, "sample": desc})
     best = max(runs, key=lambda r: r["value"])
     return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle",
             "sample": best["sample"], "runs": runs, "host_cores": nproc()}
 
 
-def oracle_solves_per_s(sample: dict, workload: str, threads: int = 1) -> tuple[float, str]:
+def oracle_solves_per_s(sample: dict, workload: str, threads: int = 1,
+                        gpu_iters: int | None = None) -> tuple[float, str]:
     if "members_s" in sample:
         return sample["solved"] / sample["members_s"], (
             f"FP64 oracle, {threads} thread(s): {sample['members']} of the {sample['count']} members, stratified by size "
@@ -393,6 +411,10 @@ def oracle_solves_per_s(sample: dict, workload: str, threads: int = 1) -> tuple[
         n_it, n_pre, ratio = GPU_ITERS_SOCP, SOCP_PRE_COND_ITERS, 1.0
         how = (f"extrapolated to the {n_it} iterations the GPU solve takes (the oracle has not been run "
                f"to completion on this instance), every iteration costed like the sampled ones")
+    elif workload in ("dense_lp", "dense_socp") and gpu_iters:
+        n_it, n_pre, ratio = int(gpu_iters), int(gpu_iters), 1.0
+        how = (f"extrapolated to the {n_it} iterations the GPU solve takes, every iteration costed like "
+               f"the sampled ones")
     else:
         raise ValueError(f"no CPU baseline for workload {workload}")
     t_solve = sample["first_iter_s"] + (n_pre - 1) * t + (n_it - n_pre) * ratio * t
@@ -489,7 +511,7 @@ def gpu_arm(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    inst = make_instance(args.workload)
+    inst = make_instance(args.workload, args.dense_n, args.cone_h)
     wl = WORKLOADS[args.workload]
     # a dedicated stream: the library launches on it and the events below time it
     stream = torch.cuda.Stream()
@@ -587,7 +609,7 @@ def gpu_arm(args) -> None:
     accuracy = affine_residuals(inst, xs, ys, zs)
     capi.acs_problem_destroy(h)
 
-    cpu = oracle_baseline(args.workload, args, rank, world)
+    cpu = oracle_baseline(args.workload, args, rank, world, iters)
     subs = sub_records(args) if (args.workload == "large_lp" and not args.no_sub and world == 1 and rank == 0
                                  and tol > 0) else None
 
@@ -902,7 +924,7 @@ def reference_arm(args) -> None:
         return
     t0 = time.perf_counter()
     threads = nproc()
-    sample = run_cpu_sample_subprocess(args.workload, max(1, args.steps), threads)
+    sample = run_cpu_sample_subprocess(args.workload, max(1, args.steps), threads, args.dense_n, args.cone_h)
     v, desc = oracle_solves_per_s(sample, args.workload, threads)
     cfg = {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "tol": TOL}
     cfg.update({k: sample[k] for k in ("m", "n", "nnz") if k in sample})
@@ -952,11 +974,13 @@ def main():
                     help="column-block width limit of the FP32 passes (-1: off; default: the library's)")
     ap.add_argument("--phases", action="store_true", help="add the per-phase device times of a warm-up solve")
     ap.add_argument("--no-sub", action="store_true", help="leave out the batched and served records")
+    ap.add_argument("--dense-n", type=int, default=None, help="n of the dense workloads")
+    ap.add_argument("--cone-h", type=int, default=10, help="Lorentz cone size of the dense SOCP")
     args = ap.parse_args()
     if args.tol is None:
         args.tol = SUB_TOL if args.workload in ("batch", "serve") else TOL
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.workload, args.cpu_iters)), flush=True)
+        print(json.dumps(cpu_sample(args.workload, args.cpu_iters, args.dense_n, args.cone_h)), flush=True)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

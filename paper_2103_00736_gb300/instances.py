@@ -26,7 +26,7 @@ import numpy as np
 SEED_BASE = 20210301
 
 # workload index used in the seed rule
-K_SMALL_LP, K_LARGE_LP, K_SOCP, K_BATCH, K_SERVE = 0, 1, 2, 3, 4
+K_SMALL_LP, K_LARGE_LP, K_SOCP, K_BATCH, K_SERVE, K_DENSE = 0, 1, 2, 3, 4, 5
 
 
 def seed_for(k: int, i: int = 0) -> int:
@@ -394,3 +394,69 @@ def paper_e2_lp(seed: int, m: int = 80, n: int = 100):
     row_ptr = np.arange(0, m * n + 1, n, dtype=np.int64)
     col = np.tile(np.arange(n, dtype=np.int32), m)
     return row_ptr, col, A.reshape(-1).copy(), A @ xdot, c
+
+
+def _dense_csr(A: np.ndarray):
+    m, n = A.shape
+    row_ptr = np.arange(0, m * n + 1, n, dtype=np.int64)
+    col = np.tile(np.arange(n, dtype=np.int32), m)
+    return row_ptr, col, A.reshape(-1)
+
+
+def _no_optimum(m: int, n: int):
+    nan = np.full(n, np.nan)
+    return nan, np.full(m, np.nan), nan.copy()
+
+
+def dense_lp(n: int, seed: int | None = None) -> Instance:
+    """Dense LP of the paper's LP experiments (Section V-A): m = floor(0.8 n),
+    A with i.i.d. entries U[-1,1], b = A |xdot| with xdot ~ N(0,1) i.i.d.,
+    c ~ N(0,1) i.i.d., K = R+^n (drawn in that order).  No planted optimum
+    (x_star, y_star, s_star are nan); A is stored as a CSR with full rows."""
+    rng = np.random.default_rng(seed_for(K_DENSE, n) if seed is None else seed)
+    m = (4 * n) // 5
+    A = rng.uniform(-1.0, 1.0, size=(m, n))
+    xdot = rng.standard_normal(n)
+    c = rng.standard_normal(n)
+    b = A @ np.abs(xdot)
+    row_ptr, col, val = _dense_csr(A)
+    xs, ys, ss = _no_optimum(m, n)
+    return Instance(m=m, n=n, row_ptr=row_ptr, col=col, val=val, b=b, c=c, n_orth=n,
+                    soc_dims=np.zeros(0, np.int32), x_star=xs, y_star=ys, s_star=ss,
+                    name=f"dense_lp_{n}", meta={"planted": False})
+
+
+def _lorentz_reflection(v: np.ndarray, h: int) -> np.ndarray:
+    """The paper's abs_K of Definition 1 on a product of Lorentz cones of size
+    h, needed by its SOCP recipe to form b (input generation only; neither
+    solver uses it): per cone (v1, vbar), t = ||vbar||: v if t <= v1, -v if
+    t <= -v1, else (t, (v1 / t) vbar)."""
+    V = v.reshape(-1, h).copy()
+    t = np.linalg.norm(V[:, 1:], axis=1)
+    v1 = V[:, 0].copy()
+    inside, polar = t <= v1, t <= -v1
+    mid = ~(inside | polar)
+    V[polar] = -V[polar]
+    V[mid, 0] = t[mid]
+    V[mid, 1:] *= (v1[mid] / t[mid])[:, None]
+    return V.reshape(-1)
+
+
+def dense_socp(n: int, h: int, seed: int | None = None) -> Instance:
+    """Dense SOCP of the paper's SOCP experiments (Section V-C): n a multiple of
+    h, m = floor(0.8 n), A i.i.d. U[-1,1], b = A abs_K(xdot) with xdot ~
+    U[0,1] i.i.d., c ~ U[0,1] i.i.d., K = (K_h)^(n/h), K_h the Lorentz cone
+    of size h.  No planted optimum."""
+    if n % h:
+        raise ValueError("n must be a multiple of the cone size h")
+    rng = np.random.default_rng(seed_for(K_DENSE, 1_000_000 + 100 * n + h) if seed is None else seed)
+    m = (4 * n) // 5
+    A = rng.uniform(-1.0, 1.0, size=(m, n))
+    xdot = rng.uniform(0.0, 1.0, size=n)
+    c = rng.uniform(0.0, 1.0, size=n)
+    b = A @ _lorentz_reflection(xdot, h)
+    row_ptr, col, val = _dense_csr(A)
+    xs, ys, ss = _no_optimum(m, n)
+    return Instance(m=m, n=n, row_ptr=row_ptr, col=col, val=val, b=b, c=c, n_orth=0,
+                    soc_dims=np.full(n // h, h, np.int32), x_star=xs, y_star=ys, s_star=ss,
+                    name=f"dense_socp_{n}_h{h}", meta={"planted": False})
