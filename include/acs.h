@@ -128,7 +128,24 @@ typedef struct {
                                 operator runs from the first iteration                         */
     double outer32_tol;      /* ACS_PREC_FP32: KKT level at which the outer products return
                                 to FP64; default 1e-5                                          */
+    int32_t splitting;       /* ACS_SPLIT_DR (default): the iteration of Algorithms 1-2,
+                                Douglas-Rachford splitting of f = indicator of K and
+                                g = c'x + indicator{Ax = b} (Section III-B);
+                                ACS_SPLIT_ADMM: the ADMM of Section III-B for the same f, g
+                                with penalty mu, run as Douglas-Rachford with the two proximal
+                                steps swapped on zeta = x1 + z_admm/mu (one projection solve an
+                                iteration, as for DR).  x is ADMM's x1 = proj_K(a) for the
+                                reflection a = 2 prox_g(zeta) - zeta, y the multiplier of
+                                Ax = b, s the state zeta, which starts where DR's s does:
+                                (1 - mu) e from x = z = e, for mu = 1 the textbook start
+                                x2 = z_admm = 0.  Needs L empty (cond_first = 0, no cond_list):
+                                ADMM's x = proj_K(a) and z = proj_K(-a)/mu are exactly
+                                complementary, so the ratio o of Algorithm 2 step 8 is 0, inf
+                                or nan on every coordinate and the rescaling has nothing to
+                                work with; other schedules give ACS_ERR_ARG                   */
 } acs_settings;
+
+enum { ACS_SPLIT_DR = 0, ACS_SPLIT_ADMM = 1 };
 
 enum { ACS_STORE_FP32 = 0, ACS_STORE_BF16 = 1 };
 

@@ -20,6 +20,7 @@ ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
 ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
 PREC_MIXED, PREC_FP32, PREC_FP64 = 0, 1, 2
 PROJ_AUTO, PROJ_CG, PROJ_DENSE = 0, 1, 2
+SPLIT_DR, SPLIT_ADMM = 0, 1
 STORE_FP32, STORE_BF16 = 0, 1
 
 _lib = None
@@ -49,6 +50,7 @@ class acs_settings(C.Structure):
         ("a_storage", C.c_int32),
         ("col_block", C.c_int32),
         ("outer32_tol", C.c_double),
+        ("splitting", C.c_int32),
     ]
 
 

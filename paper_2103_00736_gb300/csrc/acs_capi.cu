@@ -187,6 +187,7 @@ int acs_settings_default(acs_settings* s) {
     s->extrapolation = 0.0;
     s->col_block = -1;
     s->outer32_tol = 1e-5;
+    s->splitting = ACS_SPLIT_DR;
     return ACS_SOLVED;
 }
 

@@ -1003,6 +1003,14 @@ __device__ __noinline__ void phase_abs(const IterParams<T>& P, double theta) {
             if (theta != 0.0) X.w[i] = fma(theta, w - X.wp[i], w);
             X.wp[i] = w;
         }
+    if (P.admm) {                                       // ADMM form: the projection acts on s itself
+        for (int j = global_tid(); j < P.n; j += global_threads()) {
+            const double pj = X.s[j];
+            X.p[j] = pj;
+            X.g[j] = X.O[j] * (pj + extrap_q(X, j, theta, save));
+        }
+        return;
+    }
     for (int j = global_tid(); j < P.n_orth; j += global_threads()) {
         const double pj = fabs(X.s[j]);
         X.p[j] = pj;
@@ -1160,6 +1168,31 @@ __device__ __forceinline__ void update_epi(const IterParams<T>& P, int j, double
     const double qj = Oj * sum;
     P.X.q[j] = qj;
     if (!update) P.X.g[j] = Oj * (P.X.p[j] + qj);   // right-hand side input of a refinement round
+    if (update && P.admm) {
+        // ADMM form (Section III-B), as Douglas-Rachford splitting with the two
+        // proximal steps in the other order: p = s = zeta, q = A_hat' w with
+        // w = M^{-1}(b_tilde - A_hat zeta), so zeta - mu c_hat + q is the
+        // proximal point of g (x2) and a = 2 x2 - zeta its reflection;
+        // zeta <- (zeta + abs_K(a))/2, x1 = proj_K(a) = (a + abs_K(a))/2 and
+        // z = (abs_K(a) - a)/(2 mu), scaled back by O.  Lorentz-cone
+        // coordinates keep a in p for phase_admm_soc.
+        const double so = P.X.s[j];
+        const double a = (so - 2.0 * P.mu * P.X.chat[j]) + 2.0 * qj;
+        if (j >= P.n_orth) {
+            P.X.p[j] = a;
+            return;
+        }
+        const double aa = fabs(a);
+        const double sj = 0.5 * (so + aa);
+        P.X.s[j] = sj;
+        ds2 += (sj - so) * (sj - so);
+        ss2 += sj * sj;
+        if (want_xz) {
+            P.x[j] = Oj * (a + aa) * 0.5;
+            P.z[j] = (aa - a) / (2.0 * P.mu * Oj);
+        }
+        return;
+    }
     if (update) {
         const double pj = P.X.p[j];
         const double so = P.X.s[j];
@@ -1207,6 +1240,46 @@ __device__ __noinline__ void phase_update_comb(const IterParams<T>& P, bool want
     double ds2 = 0.0, ss2 = 0.0;
     cb_combine(P.ATcb, &P.ctl->err, [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2); });
     update_partials(ds2, ss2, true, P.partials);
+}
+
+// ADMM form, Lorentz cones: abs_K of the reflection a kept in p by
+// update_epi (the cone rule of phase_abs), then zeta <- (zeta + abs_K(a))/2,
+// x and z as for the orthant.  Partials ||s_new - s||^2, ||s_new||^2 of these
+// coordinates.
+template <typename T>
+__device__ __noinline__ void phase_admm_soc(const IterParams<T>& P, bool want_xz) {
+    double ds2 = 0.0, ss2 = 0.0;
+    const Outer& X = P.X;
+    const int lane = threadIdx.x & 31;
+    for (int cI = global_warp(); cI < P.n_soc; cI += global_warps()) {
+        const int a0 = __ldg(P.soc_off + cI), e = __ldg(P.soc_off + cI + 1);
+        double tt = 0.0;
+        for (int j = a0 + 1 + lane; j < e; j += 32) tt = fma(X.p[j], X.p[j], tt);
+        tt = warp_sum(tt);
+        const double t = sqrt(tt);
+        const double v1 = X.p[a0];
+        double ftail, head;
+        if (t <= v1) { ftail = 1.0; head = v1; }
+        else if (t <= -v1) { ftail = -1.0; head = -v1; }
+        else { ftail = v1 / t; head = t; }
+        const double Oc = X.O[a0];
+        for (int j = a0 + lane; j < e; j += 32) {
+            const double a = X.p[j];
+            const double aa = (j == a0) ? head : ftail * a;
+            const double so = X.s[j];
+            const double sj = 0.5 * (so + aa);
+            X.s[j] = sj;
+            ds2 += (sj - so) * (sj - so);
+            ss2 += sj * sj;
+            if (want_xz) {
+                P.x[j] = Oc * (a + aa) * 0.5;
+                P.z[j] = (aa - a) / (2.0 * P.mu * Oc);
+            }
+        }
+    }
+    const double v[2] = {ds2, ss2};
+    const int op[2] = {0, 0};
+    block_partials<2>(v, op, P.partials);
 }
 
 // FP64 residual partials: ||Ax - b||^2, ||A'y + z - c||^2 (y = w/mu), c'x, b'y,
@@ -1786,6 +1859,15 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             double d2[3];
             const int op[3] = {0, 0, 1};
             grid_combine<3>(P.partials, op, d2);
+            if (P.admm && P.n_soc > 0) {                        // the cones' share of the update
+                phase_admm_soc(P, want_xz);
+                ACS_SYNC(PH_UPDATE);
+                double e2[2];
+                const int op2[2] = {0, 0};
+                grid_combine<2>(P.partials, op2, e2);
+                d2[0] += e2[0];
+                d2[1] += e2[1];
+            }
             const double ds_new = sqrt(d2[0]);
             snorm = sqrt(d2[1]);
             over = d2[2] > 0.0;

@@ -161,6 +161,8 @@ inline bool valid_settings(const acs_settings& set) {
            (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP32 ||
             set.precision == ACS_PREC_FP64) &&
            set.col_block >= -1 && set.outer32_tol >= 0 &&
+           (set.splitting == ACS_SPLIT_DR ||
+            (set.splitting == ACS_SPLIT_ADMM && set.cond_first == 0 && set.n_cond_list == 0)) &&
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&
            set.dense_max_m >= 0 && set.dense_max_m <= kDenseLimit && set.dense_switch_max_m >= 0 &&
            set.dense_switch_max_m <= kDenseLimit && set.dense_switch_cg >= 0 &&

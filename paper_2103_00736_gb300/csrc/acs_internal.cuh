@@ -159,6 +159,7 @@ struct IterParams {
                                                       // (FP32 loop of the single-problem launch only)
     int outer32;                                      // FP32 outer passes (rhs, update) until the
     double outer32_tol;                               //   KKT residuals reach outer32_tol
+    int admm;                                         // ADMM form of the splitting (Section III-B)
 };
 
 struct Problem {

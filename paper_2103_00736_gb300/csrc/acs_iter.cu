@@ -222,6 +222,7 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.dense = P->dense;
     Q.switch_budget = acs::host::switch_budget(P->set, P->m, P->padded_A);
     Q.extrap = P->set.extrapolation;
+    Q.admm = P->set.splitting == ACS_SPLIT_ADMM ? 1 : 0;
     Q.dM = P->dM;
     Q.dX = P->dX;
     if (sizeof(T) == 4) {                 // column-blocked passes: FP32 loop only

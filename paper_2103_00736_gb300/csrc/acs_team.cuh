@@ -339,6 +339,7 @@ IterParams<T> member_params(const acs_settings& set, const int* d_cond_list, int
     Q.dense = M.dense;
     Q.switch_budget = host::switch_budget(set, M.m, M.nnz);
     Q.extrap = set.extrapolation;
+    Q.admm = set.splitting == ACS_SPLIT_ADMM ? 1 : 0;
     Q.dM = Q.dX = nullptr;                    // team scratch, set by the kernel
     return Q;
 }

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(capi):
 def test_settings_defaults(capi):
     s = capi.acs_settings_default()
     assert s.mu == 1.0 and s.t == 9.2 and s.cond_first == 300 and s.cond_period == 100
-    assert s.check_every == 10 and s.precision == capi.PREC_MIXED
+    assert s.check_every == 10 and s.precision == capi.PREC_MIXED and s.splitting == capi.SPLIT_DR
     assert capi.acs_status_string(0) == "solved"
     assert "CSR" in capi.acs_status_string(capi.ERR_CSR)
 
@@ -136,7 +136,8 @@ def test_settings_of_the_projection_are_validated(capi):
     from paper_2103_00736_gb300 import instances as I
     inst = I.bernoulli_lp(21, 6, 15, density=0.3)
     for kw in (dict(projection=7), dict(dense_max_m=5000), dict(a_storage=3), dict(extrapolation=-0.5),
-               dict(dense_switch_cg=-1)):
+               dict(dense_switch_cg=-1), dict(splitting=2), dict(splitting=-1),
+               dict(splitting=1), dict(splitting=1, cond_first=0, cond_list=[5])):
         with pytest.raises(capi.AcsError) as e:
             capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
                                     inst.n_orth, inst.soc_dims, capi.acs_settings_default(**kw))
