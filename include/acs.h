@@ -40,6 +40,8 @@ extern "C" {
 enum {
     ACS_SOLVED = 0,          /* all relative KKT residuals <= tol                   */
     ACS_MAX_ITER = 1,        /* iteration limit reached; results/residuals valid    */
+    ACS_POLISH_KEPT = 2,     /* acs_polish: the polished point was not better; the
+                                iterate is kept unchanged                           */
     ACS_ERR_ARG = -1,        /* bad argument (NULL pointer, size <= 0, bad setting) */
     ACS_ERR_CSR = -2,        /* malformed CSR: row_ptr not monotone, col out of
                                 range or unsorted/duplicate within a row, empty row */
@@ -217,10 +219,42 @@ int acs_get(acs_problem* p, double* x, double* y, double* s, int32_t* iters, dou
  * x = z = e (Algorithm 2 step 14 keeps progress across rescalings the same
  * way); a state taken after l iterations and resumed reproduces the
  * uninterrupted run.  All pointers are host pointers owned by the caller.
+ * acs_get_state returns ACS_ERR_ARG after acs_polish until the next solve.
  */
 int acs_get_state(acs_problem* p, double* s_dr, double* O, double* w, int32_t* l, double* step);
 int acs_set_state(acs_problem* p, const double* s_dr, const double* O, const double* w, int32_t l,
                   const double* step);
+
+/*
+ * LP crossover polish of the last solve's iterate (K = R+^n only; not in the
+ * paper, whose solver stops on its KKT test: an active-set alternative to
+ * iterating on).  With B = {j : x_j > z_j}, the support of a strictly
+ * complementary optimum:
+ *   x~ = the orthogonal projection of x onto {u : u_j = 0 off B, A u = b}
+ *      = x_B + A_B'(A_B A_B')^+ (b - A_B x_B) on B, 0 elsewhere;
+ *   y~ = the least change of y with A_B' y~ = c_B in the metric of
+ *        J = diag(A_B A_B') (J_ii = 1 on rows with no entry in B);
+ *   z~ = c - A' y~.
+ * At a nondegenerate vertex these are the vertex and its dual whatever x and
+ * y were.  Both solves run on the device in FP64: Jacobi-preconditioned CG
+ * from zero on M = A_B A_B' (the projection solve's phases with O the
+ * indicator of B), in up to `rounds` (1..8) refinement rounds of at most
+ * cg_max_iter iterations, each from a fresh FP64 residual.  The polished
+ * point replaces the iterate (acs_get then returns it and residuals[0..5]
+ * are its own; the solve's status and iteration count stay) only if its
+ * largest relative KKT residual is below the iterate's.
+ * Returns ACS_SOLVED (replaced) or ACS_POLISH_KEPT (kept); ACS_ERR_ARG
+ * before any solve, after a failed one, with Lorentz cones of size >= 2 or
+ * rounds outside 1..8; ACS_ERR_OOM (the polish's buffers, 2n + 2m + 16
+ * doubles, are allocated at the first call), ACS_ERR_CUDA,
+ * ACS_ERR_DEVICE_TIMEOUT, ACS_ERR_NUMERICAL.  info (host, may be NULL):
+ * info[6] = {|B|, CG iterations of the x solve, of the y solve, largest
+ * residual before, after, 1 if replaced}.  x, y, z are kept intact when the
+ * polish is not taken, but the rest of the iteration state is used as
+ * scratch: acs_get_state fails until the next acs_solve, which starts from
+ * x = z = e (or from acs_set_state).  Blocks until done.
+ */
+int acs_polish(acs_problem* p, int32_t rounds, double* info);
 
 /* Release every device buffer of the handle.  NULL is ignored. */
 void acs_problem_destroy(acs_problem* p);

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libacs.so")
 
-SOLVED, MAX_ITER = 0, 1
+SOLVED, MAX_ITER, POLISH_KEPT = 0, 1, 2
 ERR_ARG, ERR_CSR, ERR_CONES, ERR_OOM, ERR_FACTOR = -1, -2, -3, -4, -5
 ERR_DEVICE_TIMEOUT, ERR_NUMERICAL, ERR_CUDA, ERR_LIMIT = -6, -7, -8, -9
 PREC_MIXED, PREC_FP32, PREC_FP64 = 0, 1, 2
@@ -100,6 +100,7 @@ def lib():
         L.acs_get.argtypes = [P, dp, dp, dp, ip, dp]
         L.acs_get_state.argtypes = [P, dp, dp, dp, ip, dp]
         L.acs_set_state.argtypes = [P, dp, dp, dp, C.c_int32, dp]
+        L.acs_polish.argtypes = [P, C.c_int32, dp]
         L.acs_problem_destroy.argtypes = [P]
         L.acs_problem_destroy.restype = None
         L.acs_status_string.argtypes = [C.c_int]
@@ -273,6 +274,17 @@ def acs_get_state(h, m: int, n: int):
     return s, O, w, l.value, step
 
 
+def acs_polish(h, rounds: int = 3):
+    """LP crossover polish of the last solve's iterate: (status, info[6]) with
+    status SOLVED (replaced) or POLISH_KEPT, info = {|B|, CG iterations of the
+    x and y solves, largest residual before, after, 1 if replaced}."""
+    info = np.zeros(6)
+    rc = lib().acs_polish(C.c_void_p(h), int(rounds), _ptr(info, C.c_double))
+    if rc < 0:
+        raise AcsError(rc, "acs_polish")
+    return rc, info
+
+
 def acs_set_state(h, s, O, w, l: int, step=None):
     s = np.ascontiguousarray(s, dtype=np.float64)
     O = np.ascontiguousarray(O, dtype=np.float64)
@@ -375,6 +387,9 @@ class Solver:
 
     def get(self):
         return acs_get(self.h, self.m, self.n)
+
+    def polish(self, rounds: int = 3):
+        return acs_polish(self.h, rounds)
 
     def residuals(self):
         return acs_get_residuals(self.h)

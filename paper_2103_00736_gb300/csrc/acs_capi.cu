@@ -195,6 +195,7 @@ const char* acs_status_string(int st) {
     switch (st) {
         case ACS_SOLVED: return "solved";
         case ACS_MAX_ITER: return "iteration limit reached";
+        case ACS_POLISH_KEPT: return "polish not better: iterate kept";
         case ACS_ERR_ARG: return "invalid argument";
         case ACS_ERR_CSR: return "malformed CSR matrix";
         case ACS_ERR_CONES: return "invalid cone sizes";
@@ -551,9 +552,51 @@ int acs_problem_info(acs_problem* h, int32_t* out8) {
     return ACS_SOLVED;
 }
 
+int acs_polish(acs_problem* h, int32_t rounds, double* info) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || rounds < 1 || rounds > 8 || P->n_soc > 0 || P->solves == 0) return ACS_ERR_ARG;
+    const int st = acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);   // waits for the solve
+    if (st < 0) return st == ACS_ERR_CUDA ? st : ACS_ERR_ARG;
+    double before = 0.0;
+    for (int i = 0; i < 4; ++i) before = fmax(before, P->ctl_host->res[i]);
+    int rc = acs::launch_polish(P, rounds);
+    if (rc != ACS_SOLVED) return rc;
+    P->state_clobbered = true;
+    double h16[16];
+    int err = 0;
+    if (cudaMemcpyAsync(h16, P->pres, sizeof(h16), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &P->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (err != 0) return err;
+    if (h16[11] != 1.0) return ACS_ERR_NUMERICAL;
+    double after = 0.0;
+    for (int i = 0; i < 4; ++i) after = fmax(after, h16[i]);
+    const bool take = after < before;                       // NaN compares false: kept
+    if (take) {
+        cudaStream_t s = P->stream;
+        if (cudaMemcpyAsync(P->x, P->px, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(P->z, P->pz, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(P->X.w, P->pw, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(&P->ctl->res[0], P->pres, sizeof(double) * 6, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ACS_ERR_CUDA;
+    }
+    if (info) {
+        info[0] = h16[8];
+        info[1] = h16[9];
+        info[2] = h16[10];
+        info[3] = before;
+        info[4] = after;
+        info[5] = take ? 1.0 : 0.0;
+    }
+    return take ? ACS_SOLVED : ACS_POLISH_KEPT;
+}
+
 int acs_get_state(acs_problem* h, double* s_dr, double* O, double* w, int32_t* l, double* step) {
     Problem* P = reinterpret_cast<Problem*>(h);
-    if (!P) return ACS_ERR_ARG;
+    if (!P || P->state_clobbered) return ACS_ERR_ARG;
     if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
     acs::Control C;

@@ -193,6 +193,9 @@ struct Problem {
     Control* ctl_host = nullptr;         // pinned mirror
     int grid32 = 0, grid64 = 0;
     bool warm = false;                   // acs_set_state called
+    long long solves = 0;                // acs_solve_async calls
+    bool state_clobbered = false;        // a polish overwrote the iteration state
+    double *px = nullptr, *pw = nullptr, *pz = nullptr, *pwork = nullptr, *pres = nullptr;   // polish (lazy)
     int warm_l = 0;
     double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 0.3;
     int last_status = ACS_MAX_ITER;
@@ -206,6 +209,9 @@ struct Problem {
 
 // launches (acs_iter.cu)
 int launch_solve(Problem* P, double tol, int max_iter);
+// LP crossover polish of the current iterate into px, pw, pz; pres[0..5] its
+// residuals, pres[8..11] {|B|, CG iterations x, y, 1 = completed}.
+int launch_polish(Problem* P, int rounds);
 int occupancy_grid(Problem* P);
 int cb_smem_limit();
 int pass_bench(Problem* P, int kind, int reps, int smem_bytes, double* us);

@@ -141,9 +141,25 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(const __grid_constant
     solve_loop<T>(P, status0);
 }
 
+// LP crossover polish of the current iterate (FP64; see polish_loop).
+__global__ void __launch_bounds__(kThreads, 1) polish_kernel(const __grid_constant__ IterParams<double> P,
+                                                             const __grid_constant__ IterParams<double> Q,
+                                                             const PolishOut out, int rounds) {
+    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, nullptr, nullptr);
+    sync_init(P.ctl->bar_gen);
+    polish_loop(P, Q, out, rounds);
+}
+
 // ---------------------------------------------------------------------------
 // small setup kernels used by the solve
 // ---------------------------------------------------------------------------
+
+// the grid barrier's counters, restarted for a launch outside a solve
+__global__ void reset_barrier(Control* ctl) {
+    ctl->bar_count = 0;
+    ctl->bar_gen = 0;
+    ctl->bar_count64 = 0;
+}
 
 __global__ void init_zero_kernel(double* x, double* z, double* w, double* q, int n, int m) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -323,6 +339,46 @@ int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent) {
     return ACS_SOLVED;
 }
 
+int launch_polish(Problem* P, int rounds) {
+    cudaStream_t st = P->stream;
+    const int n = P->n, m = P->m;
+    if (!P->px) {
+        void* a[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t sz[5] = {sizeof(double) * n, sizeof(double) * m, sizeof(double) * n, sizeof(double) * m,
+                              sizeof(double) * 16};
+        for (int k = 0; k < 5; ++k) {
+            if (cudaMalloc(&a[k], sz[k]) != cudaSuccess) {
+                for (int q = 0; q < k; ++q) cudaFree(a[q]);
+                return ACS_ERR_OOM;
+            }
+        }
+        for (int k = 0; k < 5; ++k) P->allocations.push_back(a[k]);
+        P->px = (double*)a[0];
+        P->pw = (double*)a[1];
+        P->pz = (double*)a[2];
+        P->pwork = (double*)a[3];
+        P->pres = (double*)a[4];
+    }
+    if (cudaMemcpyAsync(P->pw, P->X.w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(P->pres, 0, sizeof(double) * 16, st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    reset_barrier<<<1, 1, 0, st>>>(P->ctl);
+    if (cudaGetLastError() != cudaSuccess) return ACS_ERR_CUDA;
+    IterParams<double> Q = make_params<double>(P, 0.0, 1, P->V64);
+    Q.dense = 0;
+    Q.X.w = P->pwork;                     // the solves' w: the iterate's w stays
+    IterParams<double> Qk = Q;
+    Qk.x = P->px;
+    Qk.z = P->pz;
+    Qk.X.w = P->pw;
+    PolishOut out{P->px, P->pw, P->pz, P->pres, P->pres + 8};
+    void* args[] = {(void*)&Q, (void*)&Qk, (void*)&out, (void*)&rounds};
+    if (cudaLaunchCooperativeKernel((const void*)polish_kernel, dim3(P->grid64), dim3(kThreads), args, 0, st) !=
+        cudaSuccess)
+        return ACS_ERR_CUDA;
+    return ACS_SOLVED;
+}
+
 int launch_solve(Problem* P, double tol, int max_iter) {
     cudaStream_t st = P->stream;
     const int n = P->n, m = P->m;
@@ -355,6 +411,8 @@ int launch_solve(Problem* P, double tol, int max_iter) {
     }
     if (P->ev_launch[1]) cudaEventRecord(P->ev_launch[1], st);
     P->warm = false;
+    P->state_clobbered = false;
+    ++P->solves;
     if (e != cudaSuccess) {
         fprintf(stderr, "acs: cooperative launch failed: %s\n", cudaGetErrorString(e));
         return ACS_ERR_CUDA;

@@ -144,6 +144,13 @@ def test_settings_of_the_projection_are_validated(capi):
         assert e.value.code == capi.ERR_ARG, kw
 
 
+def test_polish_rejects_a_null_handle(capi):
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_polish(None)
+    assert e.value.code == capi.ERR_ARG
+    assert capi.acs_status_string(capi.POLISH_KEPT).startswith("polish")
+
+
 def test_missing_library_fails_loudly(capi, monkeypatch, tmp_path):
     """No CPU fallback: without the CUDA library every entry point raises."""
     monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libacs.so"))

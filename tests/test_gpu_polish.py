@@ -1,0 +1,167 @@
+"""GPU: the LP crossover polish (acs_polish) through the C ABI against the
+oracle's polish (oracle/crossover.py) applied to the same iterate.
+
+Tolerances: the oracle solves the two projections with dense least squares,
+the device with FP64 Jacobi-PCG refinement rounds; both are accurate to a
+few ulps times cond(A_B A_B') of the support's columns, so x~, y~, z~ are
+compared at 1e-9 relative (1e-8 on the row-scaled planted LP, whose rows
+span four decades) and the residuals of an accepted polish at 1e-11.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2103_00736_gb300 import capi, instances as I, studies  # noqa: E402
+from oracle import crossover as X, kkt, vertex  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")))
+
+
+def _solve_then_polish(inst, tol, rounds=3, **kw):
+    with capi.Solver(inst, **kw) as s:
+        st = s.solve(tol=tol, max_iter=20000)
+        _, x, y, z, iters, res = s.get()
+        pst, info = s.polish(rounds)
+        _, xp, yp, zp, iters2, res2 = s.get()
+    assert iters2 == iters
+    return (st, x, y, z, res), (pst, info, xp, yp, zp, res2)
+
+
+def _close(a, b, rtol):
+    assert np.linalg.norm(a - b) <= rtol * (1.0 + np.linalg.norm(b)), np.abs(a - b).max()
+
+
+def _dense_inst(A, b, c):
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    csr = sp.csr_matrix(A)
+    nan_n, nan_m = np.full(n, np.nan), np.full(m, np.nan)
+    return I.Instance(m=m, n=n, row_ptr=csr.indptr.astype(np.int64), col=csr.indices.astype(np.int32),
+                      val=csr.data.astype(np.float64), b=np.asarray(b, float), c=np.asarray(c, float),
+                      n_orth=n, soc_dims=np.zeros(0, np.int32), x_star=nan_n, y_star=nan_m, s_star=nan_n,
+                      name="dense")
+
+
+def test_worked_example_vertex():
+    """From a 1e-3 iterate the polish lands on the enumerated vertex and the
+    dual of its basis; the oracle's polish of the same iterate agrees."""
+    A, b, c = np.array(GOLD["A"]), np.array(GOLD["b"]), np.array(GOLD["c"])
+    inst = _dense_inst(A, b, c)
+    (st, x, y, z, res), (pst, info, xp, yp, zp, res2) = _solve_then_polish(inst, 1e-3)
+    assert pst == capi.SOLVED and info[5] == 1.0 and info[0] == 3
+    xs = vertex.solve_lp(A, b, c)[0]
+    _close(xp, xs, 1e-10)
+    xo, yo, zo, _ = X.polish(A, b, c, x, y, z)
+    _close(xp, xo, 1e-9)
+    _close(yp, yo, 1e-9)
+    _close(zp, zo, 1e-9)
+    assert max(res2[:4]) <= 1e-11
+    ours = kkt.residuals(sp.csr_matrix(A), b, c, xp, yp, zp, 5, [])
+    assert kkt.max_residual(ours) <= 1e-11
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_section_iv_a_lps(k):
+    """Dense 80 x 100 LPs of Section IV-A's recipe (nondegenerate vertices)."""
+    rp, col, val, b, c = studies.e2_instance(k)
+    A = sp.csr_matrix((val, col, rp), shape=(80, 100)).toarray()
+    inst = _dense_inst(A, b, c)
+    (st, x, y, z, res), (pst, info, xp, yp, zp, res2) = _solve_then_polish(inst, 1e-4)
+    xo, yo, zo, accept_o, before, after = X.polish_if_better(A, b, c, x, y, z)
+    assert (pst == capi.SOLVED) == accept_o
+    assert pst == capi.SOLVED
+    _close(xp, xo, 1e-9)
+    _close(yp, yo, 1e-9)
+    _close(zp, zo, 1e-9)
+    assert max(res2[:4]) <= 1e-11 and abs(max(res2[:4]) - kkt.max_residual(after)) <= 1e-11
+
+
+def test_degenerate_planted_lp():
+    """The small planted LP (|supp x*| = 150 < m = 200): y~ is fixed only up to
+    null(A_B'), where both sides take the J-metric least change."""
+    inst = I.small_lp()
+    A = inst.to_scipy()
+    (st, x, y, z, res), (pst, info, xp, yp, zp, res2) = _solve_then_polish(
+        inst, 1e-6, cond_first=300, cond_period=100)
+    xo, yo, zo, accept_o, before, after = X.polish_if_better(A, inst.b, inst.c, x, y, z)
+    assert info[0] == 150
+    assert (pst == capi.SOLVED) == accept_o, (info, kkt.max_residual(before), kkt.max_residual(after))
+    if accept_o:
+        _close(xp, xo, 1e-9)
+        _close(yp, yo, 1e-9)
+        _close(zp, zo, 1e-9)
+        assert abs(inst.c @ xp - inst.obj_star) <= 1e-10 * abs(inst.obj_star)
+
+
+def test_planted_sparse_lp_with_row_scaling():
+    """large_lp's recipe at 1 % (m = 2000, n = 10000, rows over four decades,
+    |supp x*| = 3000 > m: y* unique, x~ the projection onto the face)."""
+    inst = I.large_lp(scale=0.01)
+    A = inst.to_scipy()
+    (st, x, y, z, res), (pst, info, xp, yp, zp, res2) = _solve_then_polish(inst, 1e-4)
+    xo, yo, zo, accept_o, before, after = X.polish_if_better(A, inst.b, inst.c, x, y, z)
+    assert pst == capi.SOLVED and accept_o
+    _close(xp, xo, 1e-8)
+    _close(yp, yo, 1e-8)
+    _close(zp, zo, 1e-8)
+    assert max(res2[:4]) <= 1e-10
+    assert abs(inst.c @ xp - inst.obj_star) <= 1e-9 * abs(inst.obj_star)
+
+
+def test_large_lp_full_size():
+    """m = 2e5, n = 1e6, nnz = 1e7 from a 1e-4 iterate: the polished point's
+    residuals, re-evaluated by the oracle's FP64 residual function, and the
+    planted objective."""
+    inst = I.large_lp()
+    A = inst.to_scipy()
+    (st, x, y, z, res), (pst, info, xp, yp, zp, res2) = _solve_then_polish(inst, 1e-4)
+    print("polish", info, res2[:4])
+    assert pst == capi.SOLVED
+    ours = kkt.residuals(A, inst.b, inst.c, xp, yp, zp, inst.n, [])
+    assert kkt.max_residual(ours) <= 1e-9, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-9 * abs(inst.obj_star)
+
+
+def test_worse_polish_keeps_the_iterate():
+    """Six iterations of the worked example: the support guess holds column 1,
+    which is not in the optimal basis; the polished point is worse (the
+    oracle's: 0.327 against 0.069) and the iterate stays as it was."""
+    A, b, c = np.array(GOLD["A"]), np.array(GOLD["b"]), np.array(GOLD["c"])
+    inst = _dense_inst(A, b, c)
+    with capi.Solver(inst) as s:
+        s.solve(tol=0.0, max_iter=6)
+        _, x, y, z, _, res = s.get()
+        pst, info = s.polish()
+        _, x2, y2, z2, _, res2 = s.get()
+        with pytest.raises(capi.AcsError):                      # state used as scratch
+            capi.acs_get_state(s.h, 3, 5)
+    _, _, _, accept_o, before, after = X.polish_if_better(A, b, c, x, y, z)
+    assert pst == capi.POLISH_KEPT and not accept_o
+    assert (x2 == x).all() and (y2 == y).all() and (z2 == z).all() and (res2 == res).all()
+
+
+def test_polish_arguments_and_a_later_solve():
+    inst = I.socp(scale=0.001)
+    with capi.Solver(inst) as s:
+        with pytest.raises(capi.AcsError):                      # before any solve; and not an LP
+            s.polish()
+    lp = I.small_lp()
+    with capi.Solver(lp, cond_first=300, cond_period=100) as s:
+        with pytest.raises(capi.AcsError):
+            s.polish()                                          # no solve yet
+        s.solve(tol=1e-6, max_iter=20000)
+        _, x1, *_ = s.get()
+        with pytest.raises(capi.AcsError):
+            s.polish(rounds=9)
+        s.polish()
+        s.solve(tol=1e-6, max_iter=20000)                       # starts from x = z = e again
+        _, x2, *_ = s.get()
+        capi.acs_get_state(s.h, lp.m, lp.n)                     # the state is valid again
+    np.testing.assert_array_equal(x1, x2)
