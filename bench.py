@@ -82,6 +82,10 @@ WORKLOADS = {
                        settings=dict(cond_first=200, cond_period=100, t=1.7, mu=1.0)),
 }
 DENSE_N = {"dense_lp": 10000, "dense_socp": 2900}
+# LP crossover polish inside the solve (setting polish_tol): on for the sparse
+# LPs, whose supports settle early; off for the dense LP, whose polish systems
+# (square A_B of m = 8000 > 4096, CG) do not converge, and for cones
+POLISH_TOL = {"large_lp": 1e-2, "small_lp": 1e-2}
 BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
 def nproc() -> int:
     try:
@@ -453,9 +457,28 @@ def dist_info():
 PRECISIONS = {"mixed": 0, "fp32": 1, "fp64": 2}
 
 
+def polish_tol(args) -> float:
+    if args.no_polish:
+        return 0.0
+    if args.polish_tol is not None:
+        return args.polish_tol
+    return POLISH_TOL.get(args.workload, 0.0)
+
+
+def polish_bytes(m: int, n: int, nnz: int, corrections: int, attempts: int) -> float:
+    """Algorithmic bytes of the crossover polishes of one solve: per CG
+    iteration an FP64 pass over A' and one over A (12 bytes a nonzero, the
+    vectors once) and the vector step; per polish about 14 further FP64 passes
+    (support, Jacobi, the rounds' residuals and q refreshes, z_y, z, KKT)."""
+    per_cg = 2 * (12.0 * nnz) + 16.0 * (m + n) + 56.0 * m
+    per_pass = 12.0 * nnz + 16.0 * (m + n)
+    return corrections * per_cg + attempts * 14 * per_pass
+
+
 def solver_overrides(args) -> dict:
-    """Settings chosen on the command line (precision mode, column blocks)."""
-    out = {}
+    """Settings chosen on the command line (precision mode, column blocks,
+    crossover polish)."""
+    out = {"polish_tol": polish_tol(args)}
     if args.precision is not None:
         out["precision"] = PRECISIONS[args.precision]
     if args.col_block is not None:
@@ -525,9 +548,14 @@ def gpu_arm(args) -> None:
 
     tol, max_iter = args.tol, args.max_iter
     expect = capi.SOLVED if tol > 0 else capi.MAX_ITER
+    ptol = polish_tol(args)
+    polished = ptol > tol and inst.n_orth == inst.n
 
     def solve_checked():
-        capi.acs_solve_async(h, tol, max_iter)
+        if polished:            # blocking: the host decides between segments and polishes
+            capi.acs_solve(h, tol, max_iter)
+        else:
+            capi.acs_solve_async(h, tol, max_iter)
 
     for _ in range(args.warmup):
         solve_checked()
@@ -561,9 +589,14 @@ def gpu_arm(args) -> None:
     elapsed_ms = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launch_ms = capi.acs_last_launch_ms(h)
+    polish_ms = capi.acs_last_polish_ms(h) if polished else 0.0
     st, iters, res = capi.acs_get_residuals(h)
     if st != expect:
         raise RuntimeError(f"timed solve did not converge: {capi.acs_status_string(st)}")
+    counters = capi.acs_debug_counters(h)
+    passes = capi.acs_debug_pass_counts(h)
+    _, xs, ys, zs, _, _ = capi.acs_get(h, inst.m, inst.n)
+    accuracy = affine_residuals(inst, xs, ys, zs)            # of the timed solve's point
     elapsed_ms = max_over_ranks(elapsed_ms, pg, "cuda")
     value = replica_throughput(world, args.steps, elapsed_ms / 1e3)
 
@@ -581,6 +614,34 @@ def gpu_arm(args) -> None:
     # the device's random-gather rate, measured now (4 MB vector, L2-resident)
     gather_probe = capi.acs_bench_gather(1 << 20, 0, device=local)
 
+    plain = None
+    if polished:
+        # the same handle without the polish (acs_solve_async iterates to tol):
+        # Algorithm 2 alone, timed the same way
+        for _ in range(2):
+            capi.acs_solve_async(h, tol, max_iter)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            capi.acs_solve_async(h, tol, max_iter)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pst, piters, pres = capi.acs_get_residuals(h)
+        if pst != expect:
+            raise RuntimeError(f"plain solve did not converge: {capi.acs_status_string(pst)}")
+        plain_ms = max_over_ranks(p0.elapsed_time(p1), pg, "cuda")
+        pc = capi.acs_debug_counters(h)
+        plaunch = capi.acs_last_launch_ms(h)
+        pbytes = survey_bytes(inst.m, inst.n, inst.nnz, piters, int(pres[6]), int(pc[5]), int(pc[4]))
+        plain = {"what": "Algorithm 2 alone (no polish), same handle and instance",
+                 "value": replica_throughput(world, args.steps, plain_ms / 1e3), "unit": UNIT,
+                 "ms_per_step": plain_ms / args.steps, "iterations": piters, "cg_iterations": int(pres[6]),
+                 "residual_max": float(max(pres[:4])),
+                 "roofline": roofline_entry("iter_kernel<float>", pbytes, plaunch, None,
+                                            own_bytes=algorithmic_bytes(inst.m, inst.n, inst.nnz, pc, piters))}
+
     # end to end through the C ABI with host buffers, every step: upload,
     # solve, read back x, y, s
     e2e = None
@@ -591,7 +652,8 @@ def gpu_arm(args) -> None:
             t0 = time.perf_counter()
             h2 = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b,
                                          inst.c, inst.n_orth, inst.soc_dims,
-                                         capi.acs_settings_default(device=local, **wl["settings"]))
+                                         capi.acs_settings_default(device=local, **wl["settings"],
+                                                                   **solver_overrides(args)))
             st2 = capi.acs_solve(h2, TOL, MAX_ITER)
             out = capi.acs_get(h2, inst.m, inst.n)
             capi.acs_problem_destroy(h2)
@@ -605,8 +667,6 @@ def gpu_arm(args) -> None:
         t_e2e = max_over_ranks(t_e2e, pg, "cuda")
         e2e = {"value": replica_throughput(world, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-    _, xs, ys, zs, _, _ = capi.acs_get(h, inst.m, inst.n)
-    accuracy = affine_residuals(inst, xs, ys, zs)
     capi.acs_problem_destroy(h)
 
     cpu = oracle_baseline(args.workload, args, rank, world, iters)
@@ -636,13 +696,31 @@ def gpu_arm(args) -> None:
                                                      " + checks*24 nnz + rescalings*8 nnz"),
             "clocks": clk,
             "e2e": e2e,
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": (6 * (1 + max(passes.get("polish_attempts", 0) - passes.get("polish_taken", 0), 0))
+                             + 2 * passes.get("polish_attempts", 0)) * args.steps,
             "cpu_baseline": cpu,
             "layout": layout,
             "passes": passes,
         }
         if phases is not None:
             line["phases_ms"] = phases
+        if polished:
+            line["config"]["polish_tol"] = ptol
+            line["polish"] = {
+                "what": "LP crossover polish inside the solve: iterate to every KKT residual <= polish_tol, "
+                        "polish (support x > z, FP64 projections of x and y), stop if the polished point "
+                        "meets tol, else resume",
+                "attempts": passes["polish_attempts"], "taken": passes["polish_taken"],
+                "cg_iterations": passes["polish_corrections"], "factored": passes["polish_factored"],
+                "iteration_launch_ms": launch_ms, "polish_ms": polish_ms,
+                "roofline": roofline_entry("polish_kernel", polish_bytes(inst.m, inst.n, inst.nnz,
+                                                                         passes["polish_corrections"],
+                                                                         passes["polish_attempts"]),
+                                           polish_ms, None,
+                                           bytes_formula="per CG iteration 24 nnz + 16 (m+n) + 56 m, "
+                                                         "per polish 14 x (12 nnz + 16 (m+n))")
+                if polish_ms > 0 else None}
+            line["no_polish"] = plain
         if subs:
             line.update(subs)
         print(json.dumps(line), flush=True)
@@ -976,6 +1054,10 @@ def main():
     ap.add_argument("--no-sub", action="store_true", help="leave out the batched and served records")
     ap.add_argument("--dense-n", type=int, default=None, help="n of the dense workloads")
     ap.add_argument("--cone-h", type=int, default=10, help="Lorentz cone size of the dense SOCP")
+    ap.add_argument("--polish-tol", type=float, default=None,
+                    help="LP crossover polish level inside the solve (default per workload: large_lp and "
+                         "small_lp 1e-2, else off)")
+    ap.add_argument("--no-polish", action="store_true", help="Algorithm 2 alone (no crossover polish)")
     args = ap.parse_args()
     if args.tol is None:
         args.tol = SUB_TOL if args.workload in ("batch", "serve") else TOL

@@ -145,6 +145,16 @@ typedef struct {
                                 complementary, so the ratio o of Algorithm 2 step 8 is 0, inf
                                 or nan on every coordinate and the rescaling has nothing to
                                 work with; other schedules give ACS_ERR_ARG                   */
+    double polish_tol;       /* LP crossover polish inside acs_solve (K = R+^n; see acs_polish):
+                                0 (default) = off.  With polish_tol > tol, acs_solve iterates
+                                until every KKT residual is <= polish_tol and polishes; if the
+                                polished point meets tol the solve ends there (ACS_SOLVED),
+                                else the iteration resumes from its state (the polish restores
+                                the scaling) and the polish is tried again at a ten times
+                                lower level, until the iteration itself reaches tol.  Only the
+                                blocking acs_solve does this; acs_solve_async and the batched
+                                and served forms ignore it.  Problems with Lorentz cones of
+                                size >= 2 and polish_tol > 0 are rejected (ACS_ERR_ARG)        */
 } acs_settings;
 
 enum { ACS_SPLIT_DR = 0, ACS_SPLIT_ADMM = 1 };
@@ -236,20 +246,27 @@ int acs_set_state(acs_problem* p, const double* s_dr, const double* O, const dou
  *        J = diag(A_B A_B') (J_ii = 1 on rows with no entry in B);
  *   z~ = c - A' y~.
  * At a nondegenerate vertex these are the vertex and its dual whatever x and
- * y were.  Both solves run on the device in FP64: Jacobi-preconditioned CG
- * from zero on M = A_B A_B' (the projection solve's phases with O the
- * indicator of B), in up to `rounds` (1..8) refinement rounds of at most
- * cg_max_iter iterations, each from a fresh FP64 residual.  The polished
+ * y were.  When |B| < m, y~ is fixed only up to null(A_B'): the CG path takes
+ * the least change in the J-metric, the factored path the solution with no
+ * component along the pivots it drops; both satisfy A_B' y~ = c_B.  Both solves run on the device in FP64, in up to `rounds` (1..8)
+ * refinement rounds, each from a fresh FP64 residual: for m <= 4096,
+ * M = A_B A_B' is assembled and factored once (the cached operator's
+ * phases with O the indicator of B; a dependent row is dropped) and each
+ * round applies its inverse factor; above that, or if the factorisation
+ * fails, each round is a Jacobi-preconditioned CG from zero of at most
+ * cg_max_iter iterations, down to the residual's rounding floor.  The polished
  * point replaces the iterate (acs_get then returns it and residuals[0..5]
  * are its own; the solve's status and iteration count stay) only if its
  * largest relative KKT residual is below the iterate's.
  * Returns ACS_SOLVED (replaced) or ACS_POLISH_KEPT (kept); ACS_ERR_ARG
  * before any solve, after a failed one, with Lorentz cones of size >= 2 or
  * rounds outside 1..8; ACS_ERR_OOM (the polish's buffers, 2n + 2m + 16
- * doubles, are allocated at the first call), ACS_ERR_CUDA,
+ * doubles and, for m <= 4096 on a handle without the cached operator,
+ * 2 m^2, are allocated at the first call), ACS_ERR_CUDA,
  * ACS_ERR_DEVICE_TIMEOUT, ACS_ERR_NUMERICAL.  info (host, may be NULL):
- * info[6] = {|B|, CG iterations of the x solve, of the y solve, largest
- * residual before, after, 1 if replaced}.  x, y, z are kept intact when the
+ * info[7] = {|B|, CG iterations (factored M: corrections) of the x solve,
+ * of the y solve, largest residual before, after, 1 if replaced, 1 if M was
+ * factored}.  x, y, z are kept intact when the
  * polish is not taken, but the rest of the iteration state is used as
  * scratch: acs_get_state fails until the next acs_solve, which starts from
  * x = z = e (or from acs_set_state).  Blocks until done.
@@ -269,8 +286,12 @@ const char* acs_status_string(int status);
  * CTAs of the FP32 launch, CTAs of the FP64 launch, threads per CTA}. */
 int acs_debug_counters(acs_problem* p, long long* out6);
 /* Device time (ms) of the last persistent iteration launch, from CUDA events
- * recorded on the handle's stream around that launch; waits for it. */
+ * recorded on the handle's stream around that launch; waits for it.  After an
+ * acs_solve with polish_tol: the sum over its iteration launches.
+ * acs_last_polish_ms: device time of the polish launches of the last solve
+ * with polish_tol, or of the acs_polish calls since the last solve. */
 int acs_last_launch_ms(acs_problem* p, double* ms);
+int acs_last_polish_ms(acs_problem* p, double* ms);
 /* Time of each phase of the persistent kernel in the last solve (ms, from
  * the device's global timer, barrier wait included) and how often it ran, in
  * the order: rescale-o, rescale-apply, b_tilde, q-refresh, abs_K, CG-rhs,
@@ -338,7 +359,11 @@ int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
  * passes, FP64 A passes, FP64 A' passes, rescalings, KKT checks, FP32 outer
  * A passes, FP32 outer A' passes, iteration at which the FP32 outer passes
  * ended (0 = never ran or did not end), iterations, CG iterations, iteration
- * of the FP32-to-FP64 CG hand-over}; n >= 12.  Waits for queued work.
+ * of the FP32-to-FP64 CG hand-over}; n >= 12; with n >= 16 also {polishes
+ * tried, polishes taken, their CG iterations (factored M: corrections), polishes
+ * that factored M} of the last solve with polish_tol (or of acs_polish calls
+ * since).  Counters of a polished solve add up all its segments.  Waits for
+ * queued work.
  * acs_debug_layout: out[10] = {column-blocked layout in use, blocks of A,
  * width, stored entries, blocks of A', width, stored entries, dynamic shared
  * memory of the FP32 launch (bytes), stored entries of the sliced-ELLPACK A

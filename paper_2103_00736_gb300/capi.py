@@ -51,6 +51,7 @@ class acs_settings(C.Structure):
         ("col_block", C.c_int32),
         ("outer32_tol", C.c_double),
         ("splitting", C.c_int32),
+        ("polish_tol", C.c_double),
     ]
 
 
@@ -101,6 +102,7 @@ def lib():
         L.acs_get_state.argtypes = [P, dp, dp, dp, ip, dp]
         L.acs_set_state.argtypes = [P, dp, dp, dp, C.c_int32, dp]
         L.acs_polish.argtypes = [P, C.c_int32, dp]
+        L.acs_last_polish_ms.argtypes = [P, dp]
         L.acs_problem_destroy.argtypes = [P]
         L.acs_problem_destroy.restype = None
         L.acs_status_string.argtypes = [C.c_int]
@@ -276,9 +278,10 @@ def acs_get_state(h, m: int, n: int):
 
 def acs_polish(h, rounds: int = 3):
     """LP crossover polish of the last solve's iterate: (status, info[6]) with
-    status SOLVED (replaced) or POLISH_KEPT, info = {|B|, CG iterations of the
-    x and y solves, largest residual before, after, 1 if replaced}."""
-    info = np.zeros(6)
+    status SOLVED (replaced) or POLISH_KEPT, info = {|B|, CG iterations (or
+    exact corrections) of the x and y solves, largest residual before, after,
+    1 if replaced, 1 if M = A_B A_B' was factored}."""
+    info = np.zeros(7)
     rc = lib().acs_polish(C.c_void_p(h), int(rounds), _ptr(info, C.c_double))
     if rc < 0:
         raise AcsError(rc, "acs_polish")
@@ -347,6 +350,14 @@ def acs_last_launch_ms(h) -> float:
     rc = lib().acs_last_launch_ms(C.c_void_p(h), C.byref(ms))
     if rc != 0:
         raise AcsError(rc, "acs_last_launch_ms")
+    return ms.value
+
+
+def acs_last_polish_ms(h) -> float:
+    ms = C.c_double()
+    rc = lib().acs_last_polish_ms(C.c_void_p(h), C.byref(ms))
+    if rc != 0:
+        raise AcsError(rc, "acs_last_polish_ms")
     return ms.value
 
 
@@ -846,7 +857,8 @@ def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas
 
 
 PASS_COUNTS = ("cg_A", "cg_At", "fp64_A", "fp64_At", "rescalings", "checks", "fp32_outer_A",
-               "fp32_outer_At", "outer32_end", "iterations", "cg_iterations", "cg_switch_at")
+               "fp32_outer_At", "outer32_end", "iterations", "cg_iterations", "cg_switch_at",
+               "polish_attempts", "polish_taken", "polish_corrections", "polish_factored")
 
 
 def acs_debug_pass_counts(h) -> dict:

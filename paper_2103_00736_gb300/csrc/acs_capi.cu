@@ -150,12 +150,156 @@ void free_all(Problem* P) {
     P->allocations.clear();
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
     P->ctl_host = nullptr;
+    for (auto& ev : P->ev_polish) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+    }
     for (auto& ev : P->ev_launch) {
         if (ev) cudaEventDestroy(ev);
         ev = nullptr;
     }
     if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
     P->stream = nullptr;
+}
+
+// One crossover polish of the current iterate (LP; the iteration state other
+// than s, w, x, z is used as scratch).  info7 as documented for acs_polish.
+// Returns ACS_SOLVED (the polished point replaced x, y, z and the residual
+// record) or ACS_POLISH_KEPT, or an error.  Reads the iterate's residuals
+// from ctl_host (filled by acs_get).
+int polish_once(Problem* P, int rounds, double* info7) {
+    double before = 0.0;
+    for (int i = 0; i < 4; ++i) before = fmax(before, P->ctl_host->res[i]);
+    cudaEventRecord(P->ev_polish[0], P->stream);
+    int rc = acs::launch_polish(P, rounds);
+    if (rc != ACS_SOLVED) return rc;
+    cudaEventRecord(P->ev_polish[1], P->stream);
+    double h16[16];
+    int err = 0;
+    if (cudaMemcpyAsync(h16, P->pres, sizeof(h16), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &P->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if (err != 0) return err;
+    if (h16[11] != 1.0) return ACS_ERR_NUMERICAL;
+    {
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, P->ev_polish[0], P->ev_polish[1]) != cudaSuccess) return ACS_ERR_CUDA;
+        P->polish_ms += (double)f;
+    }
+    double after = 0.0;
+    for (int i = 0; i < 4; ++i) after = fmax(after, h16[i]);
+    const bool take = after < before;                       // NaN compares false: kept
+    if (take) {
+        cudaStream_t s = P->stream;
+        if (cudaMemcpyAsync(P->x, P->px, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(P->z, P->pz, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(P->X.w, P->pw, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(&P->ctl->res[0], P->pres, sizeof(double) * 6, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ACS_ERR_CUDA;
+        for (int i = 0; i < 6; ++i) P->ctl_host->res[i] = h16[i];
+    }
+    info7[0] = h16[8];
+    info7[1] = h16[9];
+    info7[2] = h16[10];
+    info7[3] = before;
+    info7[4] = after;
+    info7[5] = take ? 1.0 : 0.0;
+    info7[6] = h16[12];
+    ++P->pol.attempts;
+    P->pol.taken += take ? 1 : 0;
+    P->pol.corrections += (long long)(h16[9] + h16[10]);
+    P->pol.factored += h16[12] == 1.0 ? 1 : 0;
+    return take ? ACS_SOLVED : ACS_POLISH_KEPT;
+}
+
+// Counters of a solve run in segments, added up on the host.
+void add_counters(acs::Control& acc, const acs::Control& c) {
+    acc.cg_iters += c.cg_iters;
+    acc.n_cg_A += c.n_cg_A; acc.n_cg_AT += c.n_cg_AT; acc.n_64_A += c.n_64_A; acc.n_64_AT += c.n_64_AT;
+    acc.n_cond += c.n_cond; acc.n_checks += c.n_checks;
+    acc.n_dense_solve += c.n_dense_solve; acc.n_dense_factor += c.n_dense_factor;
+    acc.n_32_A += c.n_32_A; acc.n_32_AT += c.n_32_AT;
+    for (int i = 0; i < acs::PH_COUNT; ++i) {
+        acc.phase_ns[i] += c.phase_ns[i];
+        acc.phase_n[i] += c.phase_n[i];
+    }
+}
+
+// acs_solve with polish_tol > tol (LP): iterate until every residual is <=
+// the current polish level, polish; done if the polished point meets tol,
+// else restore the scaling, resume the iteration from its state (as
+// acs_set_state does) and try again at a level ten times lower; the last
+// segment runs to tol without a polish.
+int solve_polished(Problem* P, double tol, int max_iter) {
+    double level = P->set.polish_tol;
+    acs::Control acc{};
+    P->pol = acs::PolishStats{};
+    P->seg_ms = P->polish_ms = 0.0;
+    P->polished_solve = true;
+    const int n = P->n;
+    if (!P->psaveO && dalloc(P, &P->psaveO, (size_t)n)) return ACS_ERR_OOM;
+    if (!P->psaveW && dalloc(P, &P->psaveW, (size_t)P->m)) return ACS_ERR_OOM;
+    int st = ACS_ERR_CUDA;
+    for (;;) {
+        const double target = fmax(tol, level);
+        int rc = acs::launch_solve(P, target, max_iter);
+        if (rc != ACS_SOLVED) return rc;
+        if (cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(acs::Control), cudaMemcpyDeviceToHost, P->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(P->stream) != cudaSuccess)
+            return ACS_ERR_CUDA;
+        add_counters(acc, *P->ctl_host);
+        {
+            float f = 0.f;
+            if (cudaEventElapsedTime(&f, P->ev_launch[0], P->ev_launch[1]) != cudaSuccess) return ACS_ERR_CUDA;
+            P->seg_ms += (double)f;
+        }
+        st = P->ctl_host->status;
+        if (st == acs::ST_RUNNING || st == acs::ST_SWITCH) st = ACS_ERR_CUDA;
+        if (st != ACS_SOLVED || target <= tol) break;
+        const acs::Control seg = *P->ctl_host;
+        if (cudaMemcpyAsync(P->psaveO, P->X.O, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(P->psaveW, P->X.w, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, P->stream) !=
+                cudaSuccess)
+            return ACS_ERR_CUDA;
+        double info[7];
+        rc = polish_once(P, 3, info);
+        P->state_clobbered = true;                           // until the next segment starts
+        if (rc < 0) return rc;
+        if (rc == ACS_SOLVED && info[4] <= tol) break;       // polished to tol: st = ACS_SOLVED
+        // resume: the scaling and the multiplier back (a polished point that
+        // was better but not good enough replaced w), the iteration state as
+        // it was; x and z are rewritten before anything reads them again
+        if (cudaMemcpyAsync(P->X.O, P->psaveO, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(P->X.w, P->psaveW, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, P->stream) !=
+                cudaSuccess)
+            return ACS_ERR_CUDA;
+        P->warm = true;
+        P->warm_l = seg.l;
+        P->warm_ds = seg.ds;
+        P->warm_snorm = seg.snorm;
+        P->warm_eta = seg.eta;
+        level *= 0.1;
+    }
+    // the whole solve's counters in the device record (acs_get, the debug getters)
+    acs::Control fin;
+    if (cudaMemcpy(&fin, P->ctl, sizeof(fin), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_ERR_CUDA;
+    fin.cg_iters = acc.cg_iters;
+    fin.n_cg_A = acc.n_cg_A; fin.n_cg_AT = acc.n_cg_AT; fin.n_64_A = acc.n_64_A; fin.n_64_AT = acc.n_64_AT;
+    fin.n_cond = acc.n_cond; fin.n_checks = acc.n_checks;
+    fin.n_dense_solve = acc.n_dense_solve; fin.n_dense_factor = acc.n_dense_factor;
+    fin.n_32_A = acc.n_32_A; fin.n_32_AT = acc.n_32_AT;
+    for (int i = 0; i < acs::PH_COUNT; ++i) {
+        fin.phase_ns[i] = acc.phase_ns[i];
+        fin.phase_n[i] = acc.phase_n[i];
+    }
+    if (cudaMemcpy(P->ctl, &fin, sizeof(fin), cudaMemcpyHostToDevice) != cudaSuccess) return ACS_ERR_CUDA;
+    return st;
 }
 
 }  // namespace
@@ -188,6 +332,7 @@ int acs_settings_default(acs_settings* s) {
     s->col_block = -1;
     s->outer32_tol = 1e-5;
     s->splitting = ACS_SPLIT_DR;
+    s->polish_tol = 0.0;
     return ACS_SOLVED;
 }
 
@@ -224,6 +369,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     const int vrc = acs::host::no_throw(
         [&] { return acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims); });
     if (vrc != ACS_SOLVED) return vrc;
+    if (set.polish_tol > 0 && n_soc > 0) return ACS_ERR_ARG;     // the polish is for LPs
     const int nnz = (int)row_ptr[m];
     Problem* P = new (std::nothrow) Problem();
     if (!P) return ACS_ERR_OOM;
@@ -320,7 +466,8 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         dalloc(P, &P->release, 32) || dalloc(P, &P->bcast, acs::kMaxRed) ||
         dalloc(P, &P->ctl, 1)) { free_all(P); delete P; return ACS_ERR_OOM; }
     if (cudaMallocHost(&P->ctl_host, sizeof(acs::Control)) != cudaSuccess) { free_all(P); delete P; return ACS_ERR_OOM; }
-    if (cudaEventCreate(&P->ev_launch[0]) != cudaSuccess || cudaEventCreate(&P->ev_launch[1]) != cudaSuccess) {
+    if (cudaEventCreate(&P->ev_launch[0]) != cudaSuccess || cudaEventCreate(&P->ev_launch[1]) != cudaSuccess ||
+        cudaEventCreate(&P->ev_polish[0]) != cudaSuccess || cudaEventCreate(&P->ev_polish[1]) != cudaSuccess) {
         free_all(P); delete P; return ACS_ERR_CUDA;
     }
     rc = 0;
@@ -341,11 +488,21 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
 int acs_solve_async(acs_problem* h, double tol, int32_t max_iter) {
     Problem* P = reinterpret_cast<Problem*>(h);
     if (!P || !(tol >= 0) || max_iter < 0) return ACS_ERR_ARG;
+    P->pol = acs::PolishStats{};
+    P->polished_solve = false;
+    P->polish_ms = 0.0;
     if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
     return acs::launch_solve(P, tol, max_iter);
 }
 
 int acs_solve(acs_problem* h, double tol, int32_t max_iter) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (P && P->set.polish_tol > tol && tol >= 0 && max_iter >= 0) {
+        if (cudaSetDevice(P->device) != cudaSuccess) return ACS_ERR_CUDA;
+        const int rc = solve_polished(P, tol, max_iter);
+        if (rc < 0) return rc;
+        return acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);
+    }
     int rc = acs_solve_async(h, tol, max_iter);
     if (rc != ACS_SOLVED) return rc;
     return acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -505,7 +662,9 @@ int acs_debug_pass_counts(acs_problem* h, int64_t* out, int32_t n) {
     out[0] = C.n_cg_A; out[1] = C.n_cg_AT; out[2] = C.n_64_A; out[3] = C.n_64_AT;
     out[4] = C.n_cond; out[5] = C.n_checks; out[6] = C.n_32_A; out[7] = C.n_32_AT;
     out[8] = C.outer32_end; out[9] = C.l; out[10] = C.cg_iters; out[11] = C.switched_at;
-    return 12;
+    if (n < 16) return 12;
+    out[12] = P->pol.attempts; out[13] = P->pol.taken; out[14] = P->pol.corrections; out[15] = P->pol.factored;
+    return 16;
 }
 
 int acs_bench_passes(acs_problem* h, int32_t kind, int32_t reps, int32_t smem_bytes, double* us_per_rep) {
@@ -534,11 +693,22 @@ int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out) {
 int acs_last_launch_ms(acs_problem* h, double* ms) {
     Problem* P = reinterpret_cast<Problem*>(h);
     if (!P || !ms) return ACS_ERR_ARG;
+    if (P->polished_solve) {
+        *ms = P->seg_ms;
+        return ACS_SOLVED;
+    }
     float f = 0.f;
     if (cudaEventSynchronize(P->ev_launch[1]) != cudaSuccess ||
         cudaEventElapsedTime(&f, P->ev_launch[0], P->ev_launch[1]) != cudaSuccess)
         return ACS_ERR_CUDA;
     *ms = (double)f;
+    return ACS_SOLVED;
+}
+
+int acs_last_polish_ms(acs_problem* h, double* ms) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !ms) return ACS_ERR_ARG;
+    *ms = P->polish_ms;
     return ACS_SOLVED;
 }
 
@@ -557,41 +727,11 @@ int acs_polish(acs_problem* h, int32_t rounds, double* info) {
     if (!P || rounds < 1 || rounds > 8 || P->n_soc > 0 || P->solves == 0) return ACS_ERR_ARG;
     const int st = acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);   // waits for the solve
     if (st < 0) return st == ACS_ERR_CUDA ? st : ACS_ERR_ARG;
-    double before = 0.0;
-    for (int i = 0; i < 4; ++i) before = fmax(before, P->ctl_host->res[i]);
-    int rc = acs::launch_polish(P, rounds);
-    if (rc != ACS_SOLVED) return rc;
+    double local[7];
+    const int rc = polish_once(P, rounds, info ? info : local);
+    if (rc < 0) return rc;
     P->state_clobbered = true;
-    double h16[16];
-    int err = 0;
-    if (cudaMemcpyAsync(h16, P->pres, sizeof(h16), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
-        cudaMemcpyAsync(&err, &P->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
-        cudaStreamSynchronize(P->stream) != cudaSuccess)
-        return ACS_ERR_CUDA;
-    if (err != 0) return err;
-    if (h16[11] != 1.0) return ACS_ERR_NUMERICAL;
-    double after = 0.0;
-    for (int i = 0; i < 4; ++i) after = fmax(after, h16[i]);
-    const bool take = after < before;                       // NaN compares false: kept
-    if (take) {
-        cudaStream_t s = P->stream;
-        if (cudaMemcpyAsync(P->x, P->px, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(P->z, P->pz, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(P->X.w, P->pw, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(&P->ctl->res[0], P->pres, sizeof(double) * 6, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return ACS_ERR_CUDA;
-    }
-    if (info) {
-        info[0] = h16[8];
-        info[1] = h16[9];
-        info[2] = h16[10];
-        info[3] = before;
-        info[4] = after;
-        info[5] = take ? 1.0 : 0.0;
-    }
-    return take ? ACS_SOLVED : ACS_POLISH_KEPT;
+    return rc;
 }
 
 int acs_get_state(acs_problem* h, double* s_dr, double* O, double* w, int32_t* l, double* step) {

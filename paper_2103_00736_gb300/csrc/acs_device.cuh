@@ -1282,230 +1282,6 @@ __device__ __noinline__ void phase_admm_soc(const IterParams<T>& P, bool want_xz
     block_partials<2>(v, op, P.partials);
 }
 
-// ---------------------------------------------------------------------------
-// LP crossover polish (FP64; the entry point is acs_polish).  Support
-// B = {j : x_j > z_j}; O holds the indicator of B, so that the projection-
-// solve phases work with M = A O^2 A' = A_B A_B' unchanged:
-//   x~ = O (p + q), p = O x, q = O A'w, w solving M w = b - A O p (refinement
-//        rounds of phase_rhs / CG / phase_update from w = 0);
-//   y~ = y + d, d solving M d = A O (O z_y), z_y = c - A'y (the same rounds
-//        with b_tilde = 0 and p = -O z_y), a Jacobi-preconditioned CG from
-//        zero: the least change of y in the metric J = diag(M);
-//   z~ = c - A'y~.
-// ---------------------------------------------------------------------------
-
-constexpr int kPolishWindow = 100;   // CG iterations over which the residual must halve
-
-struct PolishOut {
-    double* px;      // [n] polished x
-    double* pw;      // [m] on entry the iterate's w = mu y; on exit mu y~
-                     //     (the solves accumulate in P.X.w, a scratch vector)
-    double* pz;      // [n] polished z
-    double* res;     // [6] residuals of the polished point (as ctl->res) ...
-    double* info;    // [4] |B|, CG iterations of the x and y solves, 1 = completed
-};
-
-// O = indicator of B, p = O x, q = 0, g = O (p + q), w = 0, and the count |B|.
-static __device__ __noinline__ void phase_polish_init(const IterParams<double>& P) {
-    double nb = 0.0;
-    for (int j = global_tid(); j < P.n; j += global_threads()) {
-        const double o = P.x[j] > P.z[j] ? 1.0 : 0.0;
-        nb += o;
-        P.X.O[j] = o;
-        P.V.O2[j] = o;
-        const double pj = o * P.x[j];
-        P.X.p[j] = pj;
-        P.X.q[j] = 0.0;
-        P.X.g[j] = pj;
-    }
-    for (int i = global_tid(); i < P.m; i += global_threads()) P.X.w[i] = 0.0;
-    const double v[1] = {nb};
-    const int op[1] = {0};
-    block_partials<1>(v, op, P.partials);
-}
-
-// b_tilde = b and J^{-1} = 1 / diag(A_B A_B') (1 on rows without an entry in B).
-static __device__ __noinline__ void phase_polish_jacobi(const IterParams<double>& P) {
-    const double* O = P.X.O;
-    auto g1 = [](int) { return 0.0; };
-    auto g2 = [O](int j) { return O[j]; };
-    auto epi = [&](int i, double, double s2) {
-        P.X.btil[i] = P.b[i];
-        P.V.jinv[i] = s2 > 0.0 ? 1.0 / s2 : 1.0;
-    };
-    sell_rows2(P.A, g1, g2, epi);
-}
-
-// After the x solve: px = g (= x~); z_y = c - A'(w_iter / mu) into pz; the
-// y solve's start p = -O z_y, q = 0, g = O p, w = 0, b_tilde = 0.
-static __device__ __noinline__ void phase_polish_ystart(const IterParams<double>& P, const PolishOut& out) {
-    const double* pw = out.pw;
-    const double inv_mu = 1.0 / P.mu;
-    auto gather = [pw, inv_mu](int i) { return pw[i] * inv_mu; };
-    auto epi = [&](int j, double sum) {
-        const double o = P.X.O[j];
-        out.px[j] = P.X.g[j];
-        const double zj = P.c[j] - sum;
-        out.pz[j] = zj;
-        const double pj = -o * zj;
-        P.X.p[j] = pj;
-        P.X.q[j] = 0.0;
-        P.X.g[j] = o * pj;
-    };
-    sell_rows<double>(P.AT, gather, epi);
-    for (int i = global_tid(); i < P.m; i += global_threads()) {
-        P.X.w[i] = 0.0;
-        P.X.btil[i] = 0.0;
-    }
-}
-
-// z~ = c - A'(pw / mu).
-static __device__ __noinline__ void phase_polish_z(const IterParams<double>& P, const PolishOut& out) {
-    const double* pw = out.pw;
-    const double inv_mu = 1.0 / P.mu;
-    auto gather = [pw, inv_mu](int i) { return pw[i] * inv_mu; };
-    auto epi = [&](int j, double sum) { out.pz[j] = P.c[j] - sum; };
-    sell_rows<double>(P.AT, gather, epi);
-}
-
-// The projection residual r0 = b_tilde - A g with its rounding floor: the
-// partials are r0' J^{-1} r0 and sum_i J^{-1}_i (b_tilde_i^2 + (A g)_i^2).
-static __device__ __noinline__ void phase_polish_rhs(const IterParams<double>& P) {
-    double gam = 0.0, fl = 0.0;
-    const double* g = P.X.g;
-    auto gather = [g](int j) { return g[j]; };
-    auto epi = [&](int i, double sum) {
-        rhs_epi(P, i, sum, gam);
-        const double bt = P.X.btil[i];
-        fl += P.V.jinv[i] * (bt * bt + sum * sum);
-    };
-    sell_rows<double>(P.A, gather, epi);
-    const double v[2] = {gam, fl};
-    const int op[2] = {0, 0};
-    block_partials<2>(v, op, P.partials);
-}
-
-// M w = b_tilde - A g by FP64 refinement rounds (FP64 residual, Jacobi-PCG
-// correction to 1e-13 of the round's residual, the residual's rounding
-// floor 64 eps (sum J^{-1}(b_tilde^2 + (Ag)^2))^{1/2} with eps = 2^-52, or
-// cg_max iterations),
-// until the residual is at that floor, stops falling tenfold a round, or
-// `rounds` rounds have run; then q = O A'w and g = O (p + q) for the final w.
-// When |B| < m, M is singular and the rounding of b_tilde - A g leaves a
-// part outside range(M) that no correction removes: the floor ends the
-// solve there instead of letting CG drift on it.  Returns false on a failed
-// barrier or a non-finite residual.
-static __device__ bool polish_solve(const IterParams<double>& P, int rounds, long long& cg_total) {
-    double gam_last = INFINITY;
-    for (int round = 0; round < rounds; ++round) {
-        if (round > 0) {
-            phase_update(P, false, false);
-            if (!grid_sync(&P.ctl->err)) return false;
-        }
-        phase_polish_rhs(P);
-        if (!grid_sync(&P.ctl->err)) return false;
-        double gam, floor_r;
-        {
-            double t2[2];
-            const int op[2] = {0, 0};
-            grid_combine<2>(P.partials, op, t2);
-            gam = t2[0];
-            floor_r = 64.0 * 0x1p-52 * sqrt(fmax(t2[1], 0.0));
-        }
-        if (!isfinite(gam) || !isfinite(floor_r)) return false;
-        if (!(sqrt(fmax(gam, 0.0)) > floor_r) || (round > 0 && gam > 0.01 * gam_last)) break;
-        gam_last = gam;
-        const double thr = fmax(1e-13 * sqrt(gam), floor_r);
-        double gam_prev = 1.0, alpha_prev = 1.0;
-        // and, should the floor underestimate that part, the round ends
-        // when the smallest residual so far has not halved in kPolishWindow
-        // iterations
-        double best = gam, best_ref = gam;
-        int k = 0;
-        while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
-            double dl[1];
-            const int op1[1] = {0};
-            phase_cg_At(P);
-            if (!grid_sync(&P.ctl->err)) return false;
-            phase_cg_A(P);
-            if (!grid_sync(&P.ctl->err)) return false;
-            grid_combine<1>(P.partials, op1, dl);
-            const double beta = (k == 0) ? 0.0 : gam / gam_prev;
-            const double denom = dl[0] - ((k == 0) ? 0.0 : beta * gam / alpha_prev);
-            if (!(denom > 0.0)) break;                  // attainable accuracy reached
-            const double alpha = gam / denom;
-            phase_cg_vec<double, false>(P, alpha, beta);
-            if (!grid_sync(&P.ctl->err)) return false;
-            double gn[1];
-            grid_combine<1>(P.partials, op1, gn);
-            gam_prev = gam;
-            alpha_prev = alpha;
-            gam = gn[0];
-            ++k;
-            if (!isfinite(gam)) return false;
-            best = fmin(best, gam);
-            if (k % kPolishWindow == 0) {
-                if (best > 0.5 * best_ref) break;
-                best_ref = best;
-            }
-        }
-        cg_total += k;
-    }
-    phase_update(P, false, false);
-    return grid_sync(&P.ctl->err);
-}
-
-template <typename T>
-__device__ __noinline__ void phase_kkt(const IterParams<T>& P);
-
-// The whole polish; Q is P with x = px, z = pz, w = pw (its KKT residuals).
-static __device__ __noinline__ void polish_loop(const IterParams<double>& P, const IterParams<double>& Q,
-                                         const PolishOut& out, int rounds) {
-    const bool owner = blockIdx.x == 0 && threadIdx.x == 0;
-    long long cg_x = 0, cg_y = 0;
-    double nb[1] = {0.0};
-    bool ok = false;
-    do {
-        phase_polish_init(P);
-        if (!grid_sync(&P.ctl->err)) break;
-        {
-            const int op[1] = {0};
-            grid_combine<1>(P.partials, op, nb);
-        }
-        phase_polish_jacobi(P);
-        if (!grid_sync(&P.ctl->err)) break;
-        if (!polish_solve(P, rounds, cg_x)) break;             // x~ = g
-        phase_polish_ystart(P, out);
-        if (!grid_sync(&P.ctl->err)) break;
-        if (!polish_solve(P, rounds, cg_y)) break;             // d = w
-        for (int i = global_tid(); i < P.m; i += global_threads()) out.pw[i] += P.mu * P.X.w[i];
-        if (!grid_sync(&P.ctl->err)) break;
-        phase_polish_z(P, out);
-        if (!grid_sync(&P.ctl->err)) break;
-        phase_kkt(Q);
-        if (!grid_sync(&P.ctl->err)) break;
-        double r8[8];
-        const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        grid_combine<8>(P.partials, op, r8);
-        if (owner) {
-            out.res[0] = sqrt(r8[0]) / (1.0 + P.bnorm);
-            out.res[1] = sqrt(r8[1]) / (1.0 + P.cnorm);
-            out.res[2] = fabs(r8[2] - r8[3]) / (1.0 + fabs(r8[2]) + fabs(r8[3]));
-            out.res[3] = fmax(sqrt(r8[4]), sqrt(r8[5])) / (1.0 + fmax(sqrt(r8[6]), sqrt(r8[7])));
-            out.res[4] = r8[2];
-            out.res[5] = r8[3];
-        }
-        ok = true;
-    } while (false);
-    if (owner) {
-        out.info[0] = nb[0];
-        out.info[1] = (double)cg_x;
-        out.info[2] = (double)cg_y;
-        out.info[3] = ok ? 1.0 : 0.0;
-        P.ctl->bar_gen = sync_smem().gen;
-    }
-}
-
 // FP64 residual partials: ||Ax - b||^2, ||A'y + z - c||^2 (y = w/mu), c'x, b'y,
 // dist(x,K)^2, dist(z,K)^2, ||x||^2, ||z||^2.
 __device__ __forceinline__ double soc_dist2(double v1, double t) {
@@ -1797,6 +1573,266 @@ __device__ __noinline__ void phase_dense_x(const IterParams<T>& P) {
         if (i < m) a0 = fma(__ldcg(Xc + i), (double)__ldcg(y + i), a0);
         const double acc = warp_sum(a0 + a1);
         if (lane == 0) P.X.w[c] += acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LP crossover polish (FP64; the entry point is acs_polish).  Support
+// B = {j : x_j > z_j}; O holds the indicator of B, so that the projection-
+// solve phases work with M = A O^2 A' = A_B A_B' unchanged:
+//   x~ = O (p + q), p = O x, q = O A'w, w solving M w = b - A O p (refinement
+//        rounds of phase_rhs / CG / phase_update from w = 0);
+//   y~ = y + d, d solving M d = A O (O z_y), z_y = c - A'y (the same rounds
+//        with b_tilde = 0 and p = -O z_y), a Jacobi-preconditioned CG from
+//        zero: the least change of y in the metric J = diag(M);
+//   z~ = c - A'y~.
+// ---------------------------------------------------------------------------
+
+constexpr int kPolishWindow = 100;   // CG iterations over which the residual must halve
+
+struct PolishOut {
+    double* px;      // [n] polished x
+    double* pw;      // [m] on entry the iterate's w = mu y; on exit mu y~
+                     //     (the solves accumulate in P.X.w, a scratch vector)
+    double* pz;      // [n] polished z
+    double* res;     // [6] residuals of the polished point (as ctl->res) ...
+    double* info;    // [5] |B|, CG iterations (dense: corrections) of the x and y
+                     //     solves, 1 = completed, 1 = the factored M was used
+};
+
+// O = indicator of B, p = O x, q = 0, g = O (p + q), w = 0, and the count |B|.
+static __device__ __noinline__ void phase_polish_init(const IterParams<double>& P) {
+    double nb = 0.0;
+    for (int j = global_tid(); j < P.n; j += global_threads()) {
+        const double o = P.x[j] > P.z[j] ? 1.0 : 0.0;
+        nb += o;
+        P.X.O[j] = o;
+        P.V.O2[j] = o;
+        const double pj = o * P.x[j];
+        P.X.p[j] = pj;
+        P.X.q[j] = 0.0;
+        P.X.g[j] = pj;
+        P.X.chat[j] = fabs(pj);                       // magnitudes behind the residual's rounding
+    }
+    for (int i = global_tid(); i < P.m; i += global_threads()) P.X.w[i] = 0.0;
+    const double v[1] = {nb};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
+// b_tilde = b and J^{-1} = 1 / diag(A_B A_B') (1 on rows without an entry in B).
+static __device__ __noinline__ void phase_polish_jacobi(const IterParams<double>& P) {
+    const double* O = P.X.O;
+    auto g1 = [](int) { return 0.0; };
+    auto g2 = [O](int j) { return O[j]; };
+    auto epi = [&](int i, double, double s2) {
+        P.X.btil[i] = P.b[i];
+        P.V.jinv[i] = s2 > 0.0 ? 1.0 / s2 : 1.0;
+    };
+    sell_rows2(P.A, g1, g2, epi);
+}
+
+// After the x solve: px = g (= x~); z_y = c - A'(w_iter / mu) into pz; the
+// y solve's start p = -O z_y, q = 0, g = O p, w = 0, b_tilde = 0.
+static __device__ __noinline__ void phase_polish_ystart(const IterParams<double>& P, const PolishOut& out) {
+    const double* pw = out.pw;
+    const double inv_mu = 1.0 / P.mu;
+    auto gather = [pw, inv_mu](int i) { return pw[i] * inv_mu; };
+    auto epi = [&](int j, double sum) {
+        const double o = P.X.O[j];
+        out.px[j] = P.X.g[j];
+        const double zj = P.c[j] - sum;
+        out.pz[j] = zj;
+        const double pj = -o * zj;
+        P.X.p[j] = pj;
+        P.X.q[j] = 0.0;
+        P.X.g[j] = o * pj;
+        P.X.chat[j] = o * (fabs(P.c[j]) + fabs(sum));
+    };
+    sell_rows<double>(P.AT, gather, epi);
+    for (int i = global_tid(); i < P.m; i += global_threads()) {
+        P.X.w[i] = 0.0;
+        P.X.btil[i] = 0.0;
+    }
+}
+
+// z~ = c - A'(pw / mu).
+static __device__ __noinline__ void phase_polish_z(const IterParams<double>& P, const PolishOut& out) {
+    const double* pw = out.pw;
+    const double inv_mu = 1.0 / P.mu;
+    auto gather = [pw, inv_mu](int i) { return pw[i] * inv_mu; };
+    auto epi = [&](int j, double sum) { out.pz[j] = P.c[j] - sum; };
+    sell_rows<double>(P.AT, gather, epi);
+}
+
+// The projection residual r0 = b_tilde - A g with its rounding floor: the
+// partials are r0' J^{-1} r0 and sum_i J^{-1}_i (b_tilde_i^2 + sum_j A_ij^2
+// h_j^2), h (in c_hat) the magnitudes whose rounding the residual carries
+// (|x_B| for the x solve, |c_B| + |A_B'y| for the y solve).
+static __device__ __noinline__ void phase_polish_rhs(const IterParams<double>& P) {
+    double gam = 0.0, fl = 0.0;
+    const double* g = P.X.g;
+    const double* h = P.X.chat;
+    auto g1 = [g](int j) { return g[j]; };
+    auto g2 = [h](int j) { return h[j] * h[j]; };
+    auto epi = [&](int i, double sum, double s2) {
+        rhs_epi(P, i, sum, gam);
+        const double bt = P.X.btil[i];
+        fl += P.V.jinv[i] * (bt * bt + s2);
+    };
+    sell_rows2(P.A, g1, g2, epi);
+    const double v[2] = {gam, fl};
+    const int op[2] = {0, 0};
+    block_partials<2>(v, op, P.partials);
+}
+
+// M w = b_tilde - A g by FP64 refinement rounds (FP64 residual, Jacobi-PCG
+// correction to 1e-13 of the round's residual, the residual's rounding
+// floor 64 eps (sum J^{-1}(b_tilde^2 + (Ag)^2))^{1/2} with eps = 2^-52, or
+// cg_max iterations),
+// until the residual is at that floor, stops falling tenfold a round, or
+// `rounds` rounds have run; then q = O A'w and g = O (p + q) for the final w.
+// When |B| < m, M is singular and the rounding of b_tilde - A g leaves a
+// part outside range(M) that no correction removes: the floor ends the
+// solve there instead of letting CG drift on it.  Returns false on a failed
+// barrier or a non-finite residual.
+static __device__ bool polish_solve(const IterParams<double>& P, int rounds, bool dense, long long& cg_total) {
+    double gam_last = INFINITY;
+    for (int round = 0; round < rounds; ++round) {
+        if (round > 0) {
+            phase_update(P, false, false);
+            if (!grid_sync(&P.ctl->err)) return false;
+        }
+        phase_polish_rhs(P);
+        if (!grid_sync(&P.ctl->err)) return false;
+        double gam, floor_r;
+        {
+            double t2[2];
+            const int op[2] = {0, 0};
+            grid_combine<2>(P.partials, op, t2);
+            gam = t2[0];
+            floor_r = 64.0 * 0x1p-52 * sqrt(fmax(t2[1], 0.0));
+        }
+        if (!isfinite(gam) || !isfinite(floor_r)) return false;
+        if (!(sqrt(fmax(gam, 0.0)) > floor_r) || (round > 0 && gam > 0.01 * gam_last)) break;
+        gam_last = gam;
+        if (dense) {                                   // one exact correction: dw = X'(X r0)
+            phase_dense_y(P);
+            if (!grid_sync(&P.ctl->err)) return false;
+            phase_dense_x(P);
+            if (!grid_sync(&P.ctl->err)) return false;
+            ++cg_total;
+            continue;
+        }
+        const double thr = fmax(1e-13 * sqrt(gam), floor_r);
+        double gam_prev = 1.0, alpha_prev = 1.0;
+        // and, should the floor underestimate that part, the round ends
+        // when the smallest residual so far has not halved in kPolishWindow
+        // iterations
+        double best = gam, best_ref = gam;
+        int k = 0;
+        while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
+            double dl[1];
+            const int op1[1] = {0};
+            phase_cg_At(P);
+            if (!grid_sync(&P.ctl->err)) return false;
+            phase_cg_A(P);
+            if (!grid_sync(&P.ctl->err)) return false;
+            grid_combine<1>(P.partials, op1, dl);
+            const double beta = (k == 0) ? 0.0 : gam / gam_prev;
+            const double denom = dl[0] - ((k == 0) ? 0.0 : beta * gam / alpha_prev);
+            if (!(denom > 0.0)) break;                  // attainable accuracy reached
+            const double alpha = gam / denom;
+            phase_cg_vec<double, false>(P, alpha, beta);
+            if (!grid_sync(&P.ctl->err)) return false;
+            double gn[1];
+            grid_combine<1>(P.partials, op1, gn);
+            gam_prev = gam;
+            alpha_prev = alpha;
+            gam = gn[0];
+            ++k;
+            if (!isfinite(gam)) return false;
+            best = fmin(best, gam);
+            if (k % kPolishWindow == 0) {
+                if (best > 0.5 * best_ref) break;
+                best_ref = best;
+            }
+        }
+        cg_total += k;
+    }
+    phase_update(P, false, false);
+    return grid_sync(&P.ctl->err);
+}
+
+// The whole polish; Q is P with x = px, z = pz, w = pw (its KKT residuals).
+static __device__ __noinline__ void polish_loop(const IterParams<double>& P, const IterParams<double>& Q,
+                                         const PolishOut& out, int rounds) {
+    const bool owner = blockIdx.x == 0 && threadIdx.x == 0;
+    long long cg_x = 0, cg_y = 0;
+    double nb[1] = {0.0};
+    bool ok = false;
+    // with scratch for it, M = A_B A_B' is factored once (the cached
+    // operator's phases with O the indicator of B) and both solves apply
+    // L^{-1}; a failed factorisation falls back to CG
+    bool dense = sync_smem().dM != nullptr;
+    double used_dense = 0.0;
+    do {
+        phase_polish_init(P);
+        if (!grid_sync(&P.ctl->err)) break;
+        {
+            const int op[1] = {0};
+            grid_combine<1>(P.partials, op, nb);
+        }
+        phase_polish_jacobi(P);
+        if (!grid_sync(&P.ctl->err)) break;
+        if (dense) {
+            phase_dense_assemble(P);
+            if (!grid_sync(&P.ctl->err)) break;
+            bool fine = true;
+            for (int k0 = 0; k0 < P.m; k0 += kCholB) {
+                if (!dense_chol_panel(sync_smem().dM, P.m, k0, P.V.jinv)) dense = false;
+                if (!(fine = grid_sync(&P.ctl->err))) break;
+                if (!dense) break;
+                dense_chol_trailing(sync_smem().dM, P.m, k0);
+                if (!(fine = grid_sync(&P.ctl->err))) break;
+            }
+            if (!fine) break;
+            if (dense) {
+                phase_dense_inverse(P);
+                if (!grid_sync(&P.ctl->err)) break;
+                used_dense = 1.0;
+            }
+        }
+        if (!polish_solve(P, rounds, dense, cg_x)) break;      // x~ = g
+        phase_polish_ystart(P, out);
+        if (!grid_sync(&P.ctl->err)) break;
+        if (!polish_solve(P, rounds, dense, cg_y)) break;      // d = w
+        for (int i = global_tid(); i < P.m; i += global_threads()) out.pw[i] += P.mu * P.X.w[i];
+        if (!grid_sync(&P.ctl->err)) break;
+        phase_polish_z(P, out);
+        if (!grid_sync(&P.ctl->err)) break;
+        phase_kkt(Q);
+        if (!grid_sync(&P.ctl->err)) break;
+        double r8[8];
+        const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        grid_combine<8>(P.partials, op, r8);
+        if (owner) {
+            out.res[0] = sqrt(r8[0]) / (1.0 + P.bnorm);
+            out.res[1] = sqrt(r8[1]) / (1.0 + P.cnorm);
+            out.res[2] = fabs(r8[2] - r8[3]) / (1.0 + fabs(r8[2]) + fabs(r8[3]));
+            out.res[3] = fmax(sqrt(r8[4]), sqrt(r8[5])) / (1.0 + fmax(sqrt(r8[6]), sqrt(r8[7])));
+            out.res[4] = r8[2];
+            out.res[5] = r8[3];
+        }
+        ok = true;
+    } while (false);
+    if (owner) {
+        out.info[0] = nb[0];
+        out.info[1] = (double)cg_x;
+        out.info[2] = (double)cg_y;
+        out.info[3] = ok ? 1.0 : 0.0;
+        out.info[4] = used_dense;
+        P.ctl->bar_gen = sync_smem().gen;
     }
 }
 

@@ -160,7 +160,7 @@ inline bool valid_settings(const acs_settings& set) {
            set.n_cond_list >= 0 && !(set.n_cond_list > 0 && !set.cond_list) &&
            (set.precision == ACS_PREC_MIXED || set.precision == ACS_PREC_FP32 ||
             set.precision == ACS_PREC_FP64) &&
-           set.col_block >= -1 && set.outer32_tol >= 0 &&
+           set.col_block >= -1 && set.outer32_tol >= 0 && set.polish_tol >= 0 &&
            (set.splitting == ACS_SPLIT_DR ||
             (set.splitting == ACS_SPLIT_ADMM && set.cond_first == 0 && set.n_cond_list == 0)) &&
            (set.projection == ACS_PROJ_AUTO || set.projection == ACS_PROJ_CG || set.projection == ACS_PROJ_DENSE) &&

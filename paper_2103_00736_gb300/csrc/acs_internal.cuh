@@ -162,6 +162,10 @@ struct IterParams {
     int admm;                                         // ADMM form of the splitting (Section III-B)
 };
 
+struct PolishStats {
+    long long attempts = 0, taken = 0, corrections = 0, factored = 0;
+};
+
 struct Problem {
     int m = 0, n = 0, nnz = 0, n_orth = 0, n_soc = 0;
     int device = 0;
@@ -196,6 +200,10 @@ struct Problem {
     long long solves = 0;                // acs_solve_async calls
     bool state_clobbered = false;        // a polish overwrote the iteration state
     double *px = nullptr, *pw = nullptr, *pz = nullptr, *pwork = nullptr, *pres = nullptr;   // polish (lazy)
+    double *pdM = nullptr, *pdX = nullptr;   // polish's factored A_B A_B' when the handle has no scratch
+    double* psaveO = nullptr;                 // the scaling O and the multiplier w kept across a
+    double* psaveW = nullptr;                 //   polish of a polished solve
+    PolishStats pol;                          // polish attempts of the last solve (or acs_polish calls)
     int warm_l = 0;
     double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 0.3;
     int last_status = ACS_MAX_ITER;
@@ -205,6 +213,10 @@ struct Problem {
     int cb_smem = 0;                     // dynamic shared memory of the FP32 launch (bytes)
     std::vector<void*> allocations;
     cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch
+    cudaEvent_t ev_polish[2] = {nullptr, nullptr};   // bracket the last polish launch
+    double seg_ms = 0.0;                     // a polished solve: its iteration launches' device time
+    double polish_ms = 0.0;                  // ... and its polish launches' (or the last acs_polish's)
+    bool polished_solve = false;             // the last acs_solve ran with polish_tol
 };
 
 // launches (acs_iter.cu)

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(const __grid_constant
 __global__ void __launch_bounds__(kThreads, 1) polish_kernel(const __grid_constant__ IterParams<double> P,
                                                              const __grid_constant__ IterParams<double> Q,
                                                              const PolishOut out, int rounds) {
-    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, nullptr, nullptr);
+    team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, P.dM, P.dX);
     sync_init(P.ctl->bar_gen);
     polish_loop(P, Q, out, rounds);
 }
@@ -359,6 +359,22 @@ int launch_polish(Problem* P, int rounds) {
         P->pwork = (double*)a[3];
         P->pres = (double*)a[4];
     }
+    // the factored M = A_B A_B' (m <= kDenseLimit): the handle's cached-
+    // operator scratch, else the polish's own
+    double *dM = P->dM, *dX = P->dX;
+    if (!dM && m <= host::kDenseLimit) {
+        if (!P->pdM) {
+            void *a = nullptr, *b = nullptr;
+            if (cudaMalloc(&a, sizeof(double) * (size_t)m * m) != cudaSuccess) return ACS_ERR_OOM;
+            if (cudaMalloc(&b, sizeof(double) * (size_t)m * m) != cudaSuccess) { cudaFree(a); return ACS_ERR_OOM; }
+            P->allocations.push_back(a);
+            P->allocations.push_back(b);
+            P->pdM = (double*)a;
+            P->pdX = (double*)b;
+        }
+        dM = P->pdM;
+        dX = P->pdX;
+    }
     if (cudaMemcpyAsync(P->pw, P->X.w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(P->pres, 0, sizeof(double) * 16, st) != cudaSuccess)
         return ACS_ERR_CUDA;
@@ -367,6 +383,8 @@ int launch_polish(Problem* P, int rounds) {
     IterParams<double> Q = make_params<double>(P, 0.0, 1, P->V64);
     Q.dense = 0;
     Q.X.w = P->pwork;                     // the solves' w: the iterate's w stays
+    Q.dM = dM;
+    Q.dX = dX;
     IterParams<double> Qk = Q;
     Qk.x = P->px;
     Qk.z = P->pz;
