@@ -94,14 +94,14 @@ def nproc() -> int:
         return os.cpu_count() or 1
 
 
-def make_instance(name: str, dense_n: int | None = None, cone_h: int = 10):
+def make_instance(name: str, dense_n: int | None = None, cone_h: int = 10, lp_scale: float = 1.0):
     from paper_2103_00736_gb300 import instances as I
     if name == "dense_lp":
         return I.dense_lp(dense_n or DENSE_N[name])
     if name == "dense_socp":
         return I.dense_socp(dense_n or DENSE_N[name], cone_h)
     if name == "large_lp":
-        return I.large_lp()
+        return I.large_lp(scale=lp_scale)
     if name == "socp":
         return I.socp()
     if name == "small_lp":
@@ -534,7 +534,7 @@ def gpu_arm(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    inst = make_instance(args.workload, args.dense_n, args.cone_h)
+    inst = make_instance(args.workload, args.dense_n, args.cone_h, args.lp_scale)
     wl = WORKLOADS[args.workload]
     # a dedicated stream: the library launches on it and the events below time it
     stream = torch.cuda.Stream()
@@ -1058,6 +1058,8 @@ def main():
                     help="LP crossover polish level inside the solve (default per workload: large_lp and "
                          "small_lp 1e-2, else off)")
     ap.add_argument("--no-polish", action="store_true", help="Algorithm 2 alone (no crossover polish)")
+    ap.add_argument("--lp-scale", type=float, default=1.0,
+                    help="size of the large LP relative to m = 2e5, n = 1e6 (smaller cases for profiling)")
     args = ap.parse_args()
     if args.tol is None:
         args.tol = SUB_TOL if args.workload in ("batch", "serve") else TOL

@@ -151,7 +151,10 @@ typedef struct {
                                 polished point meets tol the solve ends there (ACS_SOLVED),
                                 else the iteration resumes from its state (the polish restores
                                 the scaling) and the polish is tried again at a ten times
-                                lower level, until the iteration itself reaches tol.  Only the
+                                lower level, until the iteration itself reaches tol.  These
+                                polishes need only meet tol: their solves stop at 1e-3 tol /
+                                polish_tol of their first residual (acs_polish itself goes
+                                down to the rounding floor).  Only the
                                 blocking acs_solve does this; acs_solve_async and the batched
                                 and served forms ignore it.  Problems with Lorentz cones of
                                 size >= 2 and polish_tol > 0 are rejected (ACS_ERR_ARG)        */

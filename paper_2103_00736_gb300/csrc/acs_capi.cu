@@ -167,11 +167,11 @@ void free_all(Problem* P) {
 // Returns ACS_SOLVED (the polished point replaced x, y, z and the residual
 // record) or ACS_POLISH_KEPT, or an error.  Reads the iterate's residuals
 // from ctl_host (filled by acs_get).
-int polish_once(Problem* P, int rounds, double* info7) {
+int polish_once(Problem* P, int rounds, double rel, double* info7) {
     double before = 0.0;
     for (int i = 0; i < 4; ++i) before = fmax(before, P->ctl_host->res[i]);
     cudaEventRecord(P->ev_polish[0], P->stream);
-    int rc = acs::launch_polish(P, rounds);
+    int rc = acs::launch_polish(P, rounds, rel);
     if (rc != ACS_SOLVED) return rc;
     cudaEventRecord(P->ev_polish[1], P->stream);
     double h16[16];
@@ -266,8 +266,10 @@ int solve_polished(Problem* P, double tol, int max_iter) {
             cudaMemcpyAsync(P->psaveW, P->X.w, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, P->stream) !=
                 cudaSuccess)
             return ACS_ERR_CUDA;
+        // the polished point need only meet tol: its solves stop at 1e-3 tol /
+        // polish_tol of their first residual (the iterate's, about polish_tol)
         double info[7];
-        rc = polish_once(P, 3, info);
+        rc = polish_once(P, 3, fmax(1e-13, 1e-3 * tol / P->set.polish_tol), info);
         P->state_clobbered = true;                           // until the next segment starts
         if (rc < 0) return rc;
         if (rc == ACS_SOLVED && info[4] <= tol) break;       // polished to tol: st = ACS_SOLVED
@@ -728,7 +730,7 @@ int acs_polish(acs_problem* h, int32_t rounds, double* info) {
     const int st = acs_get(h, nullptr, nullptr, nullptr, nullptr, nullptr);   // waits for the solve
     if (st < 0) return st == ACS_ERR_CUDA ? st : ACS_ERR_ARG;
     double local[7];
-    const int rc = polish_once(P, rounds, info ? info : local);
+    const int rc = polish_once(P, rounds, 1e-13, info ? info : local);
     if (rc < 0) return rc;
     P->state_clobbered = true;
     return rc;

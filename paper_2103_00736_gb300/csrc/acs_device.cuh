@@ -1688,16 +1688,18 @@ static __device__ __noinline__ void phase_polish_rhs(const IterParams<double>& P
 
 // M w = b_tilde - A g by FP64 refinement rounds (FP64 residual, Jacobi-PCG
 // correction to 1e-13 of the round's residual, the residual's rounding
-// floor 64 eps (sum J^{-1}(b_tilde^2 + (Ag)^2))^{1/2} with eps = 2^-52, or
-// cg_max iterations),
-// until the residual is at that floor, stops falling tenfold a round, or
+// floor 64 eps (sum J^{-1}(b_tilde^2 + (Ag)^2))^{1/2} with eps = 2^-52, the
+// target rel times the first residual, or cg_max iterations), until the
+// residual is at that floor or target, stops falling tenfold a round, or
 // `rounds` rounds have run; then q = O A'w and g = O (p + q) for the final w.
+// (Residuals in the J^{-1}-norm.)
 // When |B| < m, M is singular and the rounding of b_tilde - A g leaves a
 // part outside range(M) that no correction removes: the floor ends the
 // solve there instead of letting CG drift on it.  Returns false on a failed
 // barrier or a non-finite residual.
-static __device__ bool polish_solve(const IterParams<double>& P, int rounds, bool dense, long long& cg_total) {
-    double gam_last = INFINITY;
+static __device__ bool polish_solve(const IterParams<double>& P, int rounds, double rel, bool dense,
+                                    long long& cg_total) {
+    double gam_last = INFINITY, target = 0.0;
     for (int round = 0; round < rounds; ++round) {
         if (round > 0) {
             phase_update(P, false, false);
@@ -1714,6 +1716,8 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, boo
             floor_r = 64.0 * 0x1p-52 * sqrt(fmax(t2[1], 0.0));
         }
         if (!isfinite(gam) || !isfinite(floor_r)) return false;
+        if (round == 0) target = rel * sqrt(fmax(gam, 0.0));
+        floor_r = fmax(floor_r, target);
         if (!(sqrt(fmax(gam, 0.0)) > floor_r) || (round > 0 && gam > 0.01 * gam_last)) break;
         gam_last = gam;
         if (dense) {                                   // one exact correction: dw = X'(X r0)
@@ -1766,7 +1770,7 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, boo
 
 // The whole polish; Q is P with x = px, z = pz, w = pw (its KKT residuals).
 static __device__ __noinline__ void polish_loop(const IterParams<double>& P, const IterParams<double>& Q,
-                                         const PolishOut& out, int rounds) {
+                                         const PolishOut& out, int rounds, double rel) {
     const bool owner = blockIdx.x == 0 && threadIdx.x == 0;
     long long cg_x = 0, cg_y = 0;
     double nb[1] = {0.0};
@@ -1803,10 +1807,10 @@ static __device__ __noinline__ void polish_loop(const IterParams<double>& P, con
                 used_dense = 1.0;
             }
         }
-        if (!polish_solve(P, rounds, dense, cg_x)) break;      // x~ = g
+        if (!polish_solve(P, rounds, rel, dense, cg_x)) break; // x~ = g
         phase_polish_ystart(P, out);
         if (!grid_sync(&P.ctl->err)) break;
-        if (!polish_solve(P, rounds, dense, cg_y)) break;      // d = w
+        if (!polish_solve(P, rounds, rel, dense, cg_y)) break; // d = w
         for (int i = global_tid(); i < P.m; i += global_threads()) out.pw[i] += P.mu * P.X.w[i];
         if (!grid_sync(&P.ctl->err)) break;
         phase_polish_z(P, out);

@@ -222,8 +222,10 @@ struct Problem {
 // launches (acs_iter.cu)
 int launch_solve(Problem* P, double tol, int max_iter);
 // LP crossover polish of the current iterate into px, pw, pz; pres[0..5] its
-// residuals, pres[8..11] {|B|, CG iterations x, y, 1 = completed}.
-int launch_polish(Problem* P, int rounds);
+// residuals, pres[8..12] {|B|, CG iterations x, y, 1 = completed, 1 =
+// factored}.  rel: the solves stop at rel times their first residual (or at
+// its rounding floor).
+int launch_polish(Problem* P, int rounds, double rel);
 int occupancy_grid(Problem* P);
 int cb_smem_limit();
 int pass_bench(Problem* P, int kind, int reps, int smem_bytes, double* us);

@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(const __grid_constant
 // LP crossover polish of the current iterate (FP64; see polish_loop).
 __global__ void __launch_bounds__(kThreads, 1) polish_kernel(const __grid_constant__ IterParams<double> P,
                                                              const __grid_constant__ IterParams<double> Q,
-                                                             const PolishOut out, int rounds) {
+                                                             const PolishOut out, int rounds, double rel) {
     team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, P.dM, P.dX);
     sync_init(P.ctl->bar_gen);
-    polish_loop(P, Q, out, rounds);
+    polish_loop(P, Q, out, rounds, rel);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,7 +339,7 @@ int barrier_probe(Problem* P, int n, double* ns_per_barrier, int absent) {
     return ACS_SOLVED;
 }
 
-int launch_polish(Problem* P, int rounds) {
+int launch_polish(Problem* P, int rounds, double rel) {
     cudaStream_t st = P->stream;
     const int n = P->n, m = P->m;
     if (!P->px) {
@@ -390,7 +390,7 @@ int launch_polish(Problem* P, int rounds) {
     Qk.z = P->pz;
     Qk.X.w = P->pw;
     PolishOut out{P->px, P->pw, P->pz, P->pres, P->pres + 8};
-    void* args[] = {(void*)&Q, (void*)&Qk, (void*)&out, (void*)&rounds};
+    void* args[] = {(void*)&Q, (void*)&Qk, (void*)&out, (void*)&rounds, (void*)&rel};
     if (cudaLaunchCooperativeKernel((const void*)polish_kernel, dim3(P->grid64), dim3(kThreads), args, 0, st) !=
         cudaSuccess)
         return ACS_ERR_CUDA;

@@ -173,9 +173,10 @@ def test_polish_arguments_and_a_later_solve():
 
 
 def test_polished_solve_of_the_large_lp():
-    """polish_tol = 1e-2: the solve stops after the first polish (taken, every
-    residual far below 1e-6), well before the plain iteration would; the
-    oracle's FP64 residual function and the planted objective agree."""
+    """polish_tol = 1e-2: the solve stops after the first polish (taken, its
+    solves stopped at 1e-7 of their first residual), well before the plain
+    iteration would; the oracle's FP64 residual function and the planted
+    objective agree, with a tenfold margin on the 1e-6 bar."""
     inst = I.large_lp()
     with capi.Solver(inst, polish_tol=1e-2) as s:
         st = s.solve(tol=1e-6, max_iter=20000)
@@ -184,8 +185,8 @@ def test_polished_solve_of_the_large_lp():
     assert st == capi.SOLVED
     assert pc["polish_attempts"] == 1 and pc["polish_taken"] == 1 and iters < 390
     ours = kkt.residuals(inst.to_scipy(), inst.b, inst.c, x, y, z, inst.n, [])
-    assert kkt.max_residual(ours) <= 1e-9, ours
-    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-9 * abs(inst.obj_star)
+    assert kkt.max_residual(ours) <= 1e-7, ours
+    assert abs(ours["obj_p"] - inst.obj_star) <= 1e-7 * abs(inst.obj_star)
 
 
 def test_polished_solve_resumes_the_iteration():
@@ -211,6 +212,6 @@ def test_polished_solve_resumes_the_iteration():
     assert st == capi.SOLVED and pc["polish_taken"] >= 1 and pc["polish_attempts"] == 3
     assert pc["polish_factored"] == 3 and iters == it4
     ours = kkt.residuals(inst.to_scipy(), inst.b, inst.c, x, y, z, inst.n, [])
-    assert kkt.max_residual(ours) <= 1e-12, ours
+    assert kkt.max_residual(ours) <= 1e-9, ours
     assert st2 == capi.SOLVED and it2 == it3
     np.testing.assert_allclose(x2, x3, rtol=0, atol=1e-12)
