@@ -141,3 +141,24 @@ def test_section_iii_a_study_on_the_gpu():
         assert ac <= 10
         for name in ("none", "sk", "ruiz"):
             assert out["table"][f"{p}/{name}"]["iterations_to"]["1e-06"] >= 5 * ac
+
+
+def test_admm_iterates_on_a_socp_with_many_cones():
+    """The ADMM cone phase on the scaled C3 recipe (orthant plus Lorentz cones
+    of 3..64 coordinates, multi-lane cones): the device's x after k
+    iterations against the oracle's ADMM from x2 = z = 0 (the cached FP64
+    operator on the device, m = 150; the oracle's QR projection)."""
+    inst = I.socp(scale=0.001)
+    A = inst.to_scipy().toarray()
+    ref = B.admm(A, inst.b, inst.c, inst.n_orth, list(inst.soc_dims), iters=31)
+    s = capi.acs_settings_default(splitting=capi.SPLIT_ADMM, cond_first=0, precision=capi.PREC_FP64)
+    h = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b, inst.c,
+                                inst.n_orth, inst.soc_dims, s)
+    try:
+        for k in (1, 2, 7, 30):
+            st = capi.acs_solve(h, 0.0, k)
+            _, x, _, _, _, _ = capi.acs_get(h, inst.m, inst.n)
+            assert st == capi.MAX_ITER
+            assert np.linalg.norm(x - ref[k]) <= 1e-9 * (1.0 + np.linalg.norm(ref[k])), k
+    finally:
+        capi.acs_problem_destroy(h)
