@@ -94,8 +94,12 @@ typedef struct {
     int32_t device;          /* CUDA device ordinal; default 0                                 */
     int32_t projection;      /* how the projection onto range((A O)') is applied:
                                 ACS_PROJ_AUTO (default): the cached operator when
-                                m <= dense_max_m, else CG; ACS_PROJ_CG; ACS_PROJ_DENSE: the
-                                cached operator whenever m <= 4096.  The cached operator is
+                                m <= dense_max_m, else CG with the switch below (for every
+                                m <= 16384 when every row of A holds every column, nnz = m n);
+                                ACS_PROJ_CG;
+                                ACS_PROJ_DENSE: the cached operator whenever m <= 4096 (16384
+                                with full rows, whose M is assembled by a tiled FP64 product).
+                                The cached operator is
                                 the FP64 Cholesky factor of M = (A O)(A O)', formed at every
                                 rescaling, with L^{-1} kept so that each iteration's solve is
                                 exact up to rounding (two dense products); a factorisation
@@ -301,8 +305,10 @@ int acs_last_polish_ms(acs_problem* p, double* ms);
  * CG A' pass, CG A pass, CG vector step, update, KKT, cached-operator
  * factorisation, cached-operator correction, and for the column-blocked
  * passes the three phases that add up their partial sums: t = O^2 A'u of
- * the CG, the projection residual and the update of the FP32 outer passes.
- * n >= 16.  Returns the number of phases written or an error. */
+ * the CG, the projection residual and the update of the FP32 outer passes,
+ * then the cached operator's assembly of M and its inverse factor (the
+ * factorisation entry covers the Cholesky steps).  n >= 18.  Returns the
+ * number of phases written or an error. */
 int acs_debug_phase_times(acs_problem* p, double* ms, long long* count, int32_t n);
 /* Mean time (ns) of one grid-wide reduce-and-barrier of the persistent
  * kernel's launch shape, over n back-to-back barriers. */
@@ -537,7 +543,7 @@ int acs_batch_counters(acs_batch* b, long long* out);
 int acs_batch_member_ms(acs_batch* b, double* ms);
 
 /* Per-phase device times (ms) and counts of member i's last solve, or summed
- * over all members for i = -1, in the order of acs_debug_phase_times; n >= 16.
+ * over all members for i = -1, in the order of acs_debug_phase_times; n >= 18.
  * Returns the number of phases written or an error. */
 int acs_batch_phase_ms(acs_batch* b, int32_t i, double* ms, long long* count, int32_t n);
 

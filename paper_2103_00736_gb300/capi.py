@@ -317,14 +317,14 @@ def acs_debug_counters(h) -> np.ndarray:
 
 PHASES = ("rescale_o", "rescale_apply", "b_tilde", "q_refresh", "abs_K", "cg_rhs", "cg_At",
           "cg_A", "cg_vec", "update", "kkt", "dense_factor", "dense_solve", "cg_tcomb", "rhs_comb",
-          "update_comb")
+          "update_comb", "dense_assemble", "dense_inverse")
 
 
 def acs_debug_phase_times(h) -> dict:
-    ms = np.zeros(16)
-    cnt = np.zeros(16, dtype=np.int64)
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
     rc = lib().acs_debug_phase_times(C.c_void_p(h), _ptr(ms, C.c_double),
-                                     cnt.ctypes.data_as(C.POINTER(C.c_longlong)), 16)
+                                     cnt.ctypes.data_as(C.POINTER(C.c_longlong)), len(PHASES))
     if rc < 0:
         raise AcsError(rc, "acs_debug_phase_times")
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PHASES)}
@@ -560,10 +560,10 @@ def acs_batch_member_ms(h, count: int) -> np.ndarray:
 
 def acs_batch_phase_ms(h, i: int = -1) -> dict:
     """{phase: (ms, count)} of member i's last solve, or summed over members (i = -1)."""
-    ms = np.zeros(16)
-    cnt = np.zeros(16, dtype=np.int64)
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
     rc = lib().acs_batch_phase_ms(C.c_void_p(h), int(i), _ptr(ms, C.c_double),
-                                  cnt.ctypes.data_as(C.POINTER(C.c_longlong)), 16)
+                                  cnt.ctypes.data_as(C.POINTER(C.c_longlong)), len(PHASES))
     if rc < 0:
         raise AcsError(rc, "acs_batch_phase_ms")
     return {k: (float(ms[j]), int(cnt[j])) for j, k in enumerate(PHASES)}

@@ -392,7 +392,8 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     const long long warps = (long long)P->grid32 * acs::kThreads / 32;
     acs::host::HostProblem H;
     acs::host::HostTranspose HT_csr;
-    P->dense = acs::host::dense_mode(set, m);
+    P->full_rows = (long long)nnz == (long long)m * (long long)n;
+    P->dense = acs::host::dense_mode(set, m, P->full_rows);
     const bool cb = cb_wanted(set, P->dense);
     const int brc = acs::host::no_throw([&] {
         return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H,

@@ -1368,8 +1368,79 @@ __device__ __noinline__ void phase_kkt(const IterParams<T>& P) {
 // M = A O^2 A' (lower triangle), from row i of A and the columns of A it
 // touches (rows of A'): M_ik = sum_j O_j^2 a_ij a_kj.  Warp per row i, the
 // lanes over the entries of one column j at a time, in a fixed order.
+// Entry j of row i of a matrix whose rows are full (every column present,
+// in order), from its sliced-ELLPACK image: slice i / (32/g), lane group
+// i % (32/g), chunk j / g.
+__device__ __forceinline__ double sell_full_entry(const SellMat& A, int i, int j) {
+    const int g = A.g, h = 32 / g;
+    return __ldg(A.v64 + __ldg(A.sptr + i / h) + 32 * (j / g) + (i % h) * g + (j % g));
+}
+
+// M = A O^2 A' for full rows (the dense workloads): 64 x 64 tiles of the lower
+// triangle dealt to the team's CTAs, each the sum over j in increasing order
+// of 64 x 8 slabs of its two row blocks staged in shared memory (the first
+// scaled by O_j^2); thread (ty, tx) of the 32 x 32 threads owns rows
+// {ty, ty + 32} and columns {tx, tx + 32} of the tile.  FP64 throughout (the
+// FP64 pipe bounds it: about two FP64 multiply-adds per clock per SM here, so
+// the slabs stay small and leave L1 its carve-out).
+constexpr int kSyrkT = 64, kSyrkK = 8;
+
+template <typename T>
+__device__ __noinline__ void phase_dense_syrk(const IterParams<T>& P) {
+    __shared__ double Ai[kSyrkT][kSyrkK + 1];
+    __shared__ double Ak[kSyrkT][kSyrkK + 1];
+    double* M = sync_smem().dM;
+    const int m = P.m, n = P.n;
+    const int mt = (m + kSyrkT - 1) / kSyrkT;
+    const long long ntile = (long long)mt * (mt + 1) / 2;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (long long t = team_rank(); t < ntile; t += team_size()) {
+        // lower-triangular tile (bi, bk), bk <= bi, t = bi (bi + 1) / 2 + bk
+        int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        while ((long long)bi * (bi + 1) / 2 > t) --bi;
+        const int bk = (int)(t - (long long)bi * (bi + 1) / 2);
+        const int i0 = bi * kSyrkT, k0 = bk * kSyrkT;
+        double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+        for (int j0 = 0; j0 < n; j0 += kSyrkK) {
+            for (int e = threadIdx.x; e < kSyrkT * kSyrkK; e += blockDim.x) {
+                const int r = e / kSyrkK, c = e % kSyrkK, j = j0 + c;
+                double vi = 0.0, vk = 0.0;
+                if (j < n) {
+                    const double o = P.X.O[j];
+                    if (i0 + r < m) vi = sell_full_entry(P.A, i0 + r, j) * (o * o);
+                    if (k0 + r < m) vk = sell_full_entry(P.A, k0 + r, j);
+                }
+                Ai[r][c] = vi;
+                Ak[r][c] = vk;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int c = 0; c < kSyrkK; ++c) {
+                const double x0 = Ai[ty][c], x1 = Ai[ty + 32][c];
+                const double y0 = Ak[tx][c], y1 = Ak[tx + 32][c];
+                a00 = fma(x0, y0, a00);
+                a01 = fma(x0, y1, a01);
+                a10 = fma(x1, y0, a10);
+                a11 = fma(x1, y1, a11);
+            }
+            __syncthreads();
+        }
+        const double acc[2][2] = {{a00, a01}, {a10, a11}};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const int i = i0 + ty + 32 * a, k = k0 + tx + 32 * b;
+                if (i < m && k <= i) M[(size_t)i * m + k] = acc[a][b];
+            }
+    }
+}
+
 template <typename T>
 __device__ __noinline__ void phase_dense_assemble(const IterParams<T>& P) {
+    if (P.full_rows && blockDim.x == 1024) {            // dense rows: tiled product
+        phase_dense_syrk(P);
+        return;
+    }
     double* M = sync_smem().dM;
     const int m = P.m;
     const int lane = threadIdx.x & 31;
@@ -1973,7 +2044,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 factor_kept = false;
                 factor_ok = false;
                 phase_dense_assemble(P);
-                ACS_SYNC(PH_DENSE_FACTOR);
+                ACS_SYNC(PH_DENSE_ASSEMBLE);
                 for (int k0 = 0; k0 < P.m && dense; k0 += kCholB) {
                     if (!dense_chol_panel(sync_smem().dM, P.m, k0, P.V.jinv)) {
                         dense = false;
@@ -1987,7 +2058,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 if (!ok) break;
                 if (dense) {
                     phase_dense_inverse(P);
-                    ACS_SYNC(PH_DENSE_FACTOR);
+                    ACS_SYNC(PH_DENSE_INVERSE);
                     ++nfactor;
                     factor_ok = true;
                 }

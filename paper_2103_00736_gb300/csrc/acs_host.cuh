@@ -152,6 +152,7 @@ inline int validate(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t*
 }
 
 constexpr int kDenseLimit = 4096;   // largest m for the cached dense projection operator
+constexpr int kDenseRowsLimit = 16384;   // ... when every row of A is full (tiled assembly of M)
 
 // Settings checks shared by every entry point that takes acs_settings.
 inline bool valid_settings(const acs_settings& set) {
@@ -184,18 +185,29 @@ inline unsigned short to_bf16(double v) {
 // cached operator ((2/3) m^3 FP64 flops against 2 sparse passes over nnz
 // stored entries per CG iteration; the factor 0.3 is measured on this GPU:
 // one factorisation of an m = 1000, 5e4-nonzero M costs ~5700 CG iterations),
-// and at least 8 * dense_switch_cg.
-inline long long switch_budget(const acs_settings& set, int m, long long nnz) {
-    const double f = 0.3 * (double)m * (double)m * (double)m / (double)(nnz > 0 ? nnz : 1);
+// and at least 8 * dense_switch_cg.  Full rows (nnz = m n): the tiled
+// assembly adds m^2 n / 2 multiply-adds, and the factor is 1.0 instead,
+// m^2 / n CG iterations (measured: one factorisation takes 109 ms at m = 2320,
+// n = 2900 against 60 us a CG iteration, 1.73 s at m = 8000, n = 1e4 against
+// 0.35 ms).
+inline long long switch_budget(const acs_settings& set, int m, long long nnz, bool full_rows = false) {
+    const double k = full_rows ? 1.0 : 0.3;
+    const double f = k * (double)m * (double)m * (double)m / (double)(nnz > 0 ? nnz : 1);
     return std::max((long long)8 * set.dense_switch_cg, (long long)f);
 }
 
 // How a problem with m constraints applies the projection: 0 = CG only,
 // 1 = the cached dense operator from the first iteration, 2 = CG, switching
 // to the cached operator if CG stalls.
-inline int dense_mode(const acs_settings& set, int m) {
-    if (set.projection == ACS_PROJ_DENSE) return m <= kDenseLimit ? 1 : 0;
+inline int dense_mode(const acs_settings& set, int m, bool full_rows = false) {
+    if (set.projection == ACS_PROJ_DENSE) return m <= (full_rows ? kDenseRowsLimit : kDenseLimit) ? 1 : 0;
     if (set.projection != ACS_PROJ_AUTO) return 0;
+    // full rows (the dense workloads): M costs m^2 n / 2 + 2 m^3 / 3 FP64 multiply-adds at a
+    // rescaling (the tiled assembly, the factor, its inverse) against ~2 m n a CG iteration; the
+    // switch budget 0.3 m^3 / nnz = 0.3 m^2 / n CG iterations matches that ratio on this GPU, so
+    // the rule of the sparse case decides: the dense LPs (t = 9.2), whose rescaled M stalls
+    // Jacobi-CG, switch; the dense SOCPs (t = 1.7) mostly stay on CG
+    if (full_rows && m <= kDenseRowsLimit && m > set.dense_switch_max_m) return 2;
     if (m <= set.dense_max_m) return 1;
     if (set.dense_switch_cg > 0 && m <= set.dense_switch_max_m) return 2;
     return 0;

@@ -34,6 +34,8 @@ enum Phase : int {
     PH_CG_TCOMB,     // column-blocked CG: t = O^2 (A'u) from the partial sums, and u'Mu
     PH_RHS_COMB,     // FP32 outer passes: the projection residual from the partial sums
     PH_UPD_COMB,     // FP32 outer passes: q = A_hat' w from the partial sums and the update
+    PH_DENSE_ASSEMBLE,   // cached operator: M = A O^2 A' (PH_DENSE_FACTOR: its Cholesky steps)
+    PH_DENSE_INVERSE,    // cached operator: L^{-1}
     PH_COUNT
 };
 
@@ -160,6 +162,9 @@ struct IterParams {
     int outer32;                                      // FP32 outer passes (rhs, update) until the
     double outer32_tol;                               //   KKT residuals reach outer32_tol
     int admm;                                         // ADMM form of the splitting (Section III-B)
+    int full_rows;                                    // every row of A holds every column (dense
+                                                      // workloads): the cached operator's M is
+                                                      // assembled by a tiled product
 };
 
 struct PolishStats {
@@ -217,6 +222,7 @@ struct Problem {
     double seg_ms = 0.0;                     // a polished solve: its iteration launches' device time
     double polish_ms = 0.0;                  // ... and its polish launches' (or the last acs_polish's)
     bool polished_solve = false;             // the last acs_solve ran with polish_tol
+    bool full_rows = false;                  // nnz = m n: every row holds every column
 };
 
 // launches (acs_iter.cu)

@@ -236,9 +236,10 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
     Q.refine = P->set.cg_refine > 0 ? P->set.cg_refine : 1;
     Q.switch_ok = P->set.precision != ACS_PREC_FP64 ? 1 : 0;
     Q.dense = P->dense;
-    Q.switch_budget = acs::host::switch_budget(P->set, P->m, P->padded_A);
+    Q.switch_budget = acs::host::switch_budget(P->set, P->m, P->padded_A, P->full_rows);
     Q.extrap = P->set.extrapolation;
     Q.admm = P->set.splitting == ACS_SPLIT_ADMM ? 1 : 0;
+    Q.full_rows = P->full_rows ? 1 : 0;
     Q.dM = P->dM;
     Q.dX = P->dX;
     if (sizeof(T) == 4) {                 // column-blocked passes: FP32 loop only
@@ -362,7 +363,7 @@ int launch_polish(Problem* P, int rounds, double rel) {
     // the factored M = A_B A_B' (m <= kDenseLimit): the handle's cached-
     // operator scratch, else the polish's own
     double *dM = P->dM, *dX = P->dX;
-    if (!dM && m <= host::kDenseLimit) {
+    if (!dM && m <= (P->full_rows ? host::kDenseRowsLimit : host::kDenseLimit)) {
         if (!P->pdM) {
             void *a = nullptr, *b = nullptr;
             if (cudaMalloc(&a, sizeof(double) * (size_t)m * m) != cudaSuccess) return ACS_ERR_OOM;

@@ -62,3 +62,25 @@ def test_dense_first_iterates(kind, n, h):
             xr = ref.x_history[k - 1]
             err = np.linalg.norm(xs - xr) / np.linalg.norm(xr)
             assert err <= rtol, (prec, k, err)
+
+
+def test_dense_lp_with_full_rows_above_the_sparse_limit():
+    """m = 1200 > dense_switch_max_m: with full rows the solve may switch to
+    the cached operator (its M assembled by the tiled FP64 product) when CG
+    stalls; end result against the oracle's objective, and, with the cached
+    operator from the first iteration, the oracle's exact first iterates."""
+    x, sched, L, t = _case("lp", 1500)
+    A = x.to_scipy()
+    ref = alg.algorithm2(A, x.b, x.c, x.n_orth, x.soc_dims, t=t, L=L, max_iter=20000, tol=2e-7, check_every=10,
+                         keep_x=10)
+    assert ref.status == "solved"
+    with capi.Solver(x, **sched) as s:
+        st = s.solve(tol=2e-7, max_iter=20000)
+        _, xs, ys, zs, iters, res = s.get()
+        pc = capi.acs_debug_pass_counts(s.h)
+    assert st == capi.SOLVED
+    ours = kkt.residuals(A, x.b, x.c, xs, ys, zs, x.n_orth, x.soc_dims)
+    assert kkt.max_residual(ours) <= 1e-6, ours
+    assert abs(ours["obj_p"] - ref.res["obj_p"]) <= 1e-6 * (1 + abs(ref.res["obj_p"]))
+    st, xs, _, _, _ = _solve(x, 0.0, 10, precision=capi.PREC_FP64, projection=capi.PROJ_DENSE, **sched)
+    assert np.linalg.norm(xs - ref.x_history[9]) <= 1e-9 * np.linalg.norm(ref.x_history[9])
