@@ -332,6 +332,13 @@ int acs_debug_barrier_timeout(acs_problem* p, double* waited_ms);
  * g, stored entries}; perm[m], sptr[slices + 1], slen[slices] (chunks of 32
  * entries per slice), col / val[stored] are written where not NULL (call
  * once with NULL arrays for the sizes).  Errors: ACS_ERR_ARG, ACS_ERR_CSR. */
+/* The sliced-ELLPACK image of A (which = 0) or A' (which = 1) that a
+ * problem holds on the device, read back: info[4] = {rows, slices, lanes
+ * per row, stored entries}; sptr[slices + 1], slen[slices], col and val
+ * (FP64) and v32 (FP32 copy, if the problem keeps one) [stored entries];
+ * any array may be NULL.  Errors: ACS_ERR_ARG, ACS_ERR_CUDA. */
+int acs_debug_images(acs_problem* p, int32_t which, int32_t* info, int32_t* sptr, int32_t* slen, int32_t* col,
+                     double* val, float* v32);
 /* Host-only check of the BF16 storage of A (a_storage = ACS_STORE_BF16):
  * out[k] = the BF16 bit pattern stored for the finite value v[k], i.e. its
  * FP32 value rounded to the nearest BF16 value, ties to even.  Errors:

@@ -103,6 +103,7 @@ def lib():
         L.acs_set_state.argtypes = [P, dp, dp, dp, C.c_int32, dp]
         L.acs_polish.argtypes = [P, C.c_int32, dp]
         L.acs_last_polish_ms.argtypes = [P, dp]
+        L.acs_debug_images.argtypes = [P, C.c_int32, ip, ip, ip, ip, dp, C.POINTER(C.c_float)]
         L.acs_problem_destroy.argtypes = [P]
         L.acs_problem_destroy.restype = None
         L.acs_status_string.argtypes = [C.c_int]
@@ -822,6 +823,27 @@ def acs_debug_sell(m, n, row_ptr, col, val, which: int, warps: int) -> dict:
         raise AcsError(rc, "acs_debug_sell")
     return dict(rows=rows, slices=slices, g=g, stored=stored, perm=perm, sptr=sptr, slen=slen[:slices],
                 col=oc[:stored], val=ov[:stored])
+
+
+def acs_debug_images(h, which: int) -> dict:
+    """The sliced-ELLPACK image of A (which=0) or A' (which=1) held on the device."""
+    info = np.zeros(4, dtype=np.int32)
+    rc = lib().acs_debug_images(C.c_void_p(h), int(which), _ptr(info, C.c_int32), None, None, None, None, None)
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_images")
+    rows, slices, g, stored = (int(v) for v in info)
+    sptr = np.zeros(slices + 1, dtype=np.int32)
+    slen = np.zeros(max(slices, 1), dtype=np.int32)
+    oc = np.zeros(max(stored, 1), dtype=np.int32)
+    ov = np.zeros(max(stored, 1), dtype=np.float64)
+    o32 = np.full(max(stored, 1), np.nan, dtype=np.float32)
+    rc = lib().acs_debug_images(C.c_void_p(h), int(which), _ptr(info, C.c_int32), _ptr(sptr, C.c_int32),
+                                _ptr(slen, C.c_int32), _ptr(oc, C.c_int32), _ptr(ov, C.c_double),
+                                _ptr(o32, C.c_float))
+    if rc != 0:
+        raise AcsError(rc, "acs_debug_images")
+    return dict(rows=rows, slices=slices, g=g, stored=stored, sptr=sptr, slen=slen[:slices], col=oc[:stored],
+                val=ov[:stored], v32=o32[:stored])
 
 
 def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas: int) -> dict:

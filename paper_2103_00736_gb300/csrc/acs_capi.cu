@@ -3,7 +3,10 @@
 
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <chrono>
 
 #include <algorithm>
 #include <climits>
@@ -44,6 +47,23 @@ int upload(Problem* P, T* dst, const T* src, size_t count) {
     return ACS_SOLVED;
 }
 
+// The narrow copies of the uploaded FP64 values, on the device: FP32 by the
+// conversion's round-to-nearest, BF16 as the upper half of the FP32 value
+// rounded to nearest even (the same bit rule as the host's to_bf16).
+__global__ void narrow_f32(const double* __restrict__ v64, float* __restrict__ v32, long long tot) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x)
+        v32[k] = (float)v64[k];
+}
+__global__ void narrow_bf16(const double* __restrict__ v64, unsigned short* __restrict__ v16, long long tot) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        unsigned u = __float_as_uint((float)v64[k]);
+        u += 0x7FFFu + ((u >> 16) & 1u);
+        v16[k] = (unsigned short)(u >> 16);
+    }
+}
+
 // FP64 values always; for the FP32 correction CG either FP32 values or,
 // with BF16 storage of A, BF16 bit patterns (v32 is then NULL).  narrow =
 // false: no FP32 copy (the FP32 passes use the column-blocked image).
@@ -59,29 +79,42 @@ int upload_sell(Problem* P, const HostSell& H, acs::SellMat& M, bool narrow = tr
     rc |= upload(P, sptr, H.sptr.data(), H.sptr.size());
     rc |= upload(P, slen, H.slen.data(), H.slen.size());
     rc |= upload(P, col, H.col.data(), tot);
-    // the narrow copy of the values, converted over parts of the image in parallel
-    const int T = acs::host::host_threads((long long)tot);
-    if (!narrow) {
-    } else if (bf16) {
-        acs::host::raw_vector<unsigned short> h(tot);
-        acs::host::parallel_for(T, [&](int t) {
-            const size_t k1 = (size_t)acs::host::part_lo((long long)tot, t + 1, T);
-            for (size_t k = (size_t)acs::host::part_lo((long long)tot, t, T); k < k1; ++k)
-                h[k] = acs::host::to_bf16(H.val[k]);
-        });
-        rc |= upload(P, v16, h.data(), tot);
-    } else {
-        acs::host::raw_vector<float> f(tot);
-        acs::host::parallel_for(T, [&](int t) {
-            const size_t k1 = (size_t)acs::host::part_lo((long long)tot, t + 1, T);
-            for (size_t k = (size_t)acs::host::part_lo((long long)tot, t, T); k < k1; ++k) f[k] = (float)H.val[k];
-        });
-        rc |= upload(P, v32, f.data(), tot);
-    }
     rc |= upload(P, v64, H.val.data(), tot);
+    // the narrow copy of the values, converted on the device from the FP64 upload
+    if (narrow && tot > 0) {
+        const long long nb = std::min<long long>(((long long)tot + 255) / 256, 4096);
+        if (bf16) narrow_bf16<<<(unsigned)nb, 256, 0, P->stream>>>(v64, v16, (long long)tot);
+        else narrow_f32<<<(unsigned)nb, 256, 0, P->stream>>>(v64, v32, (long long)tot);
+        rc |= cudaGetLastError() != cudaSuccess;
+    }
     // the pageable source buffers are released when this function returns
     if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
     M.nrows = H.nrows; M.nslices = H.nslices; M.g = H.g;
+    M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64; M.v16 = v16;
+    return ACS_SOLVED;
+}
+
+// A device-built image (acs_devbuild.cu): its slice tables uploaded and the
+// narrow copy of the values converted from the FP64 ones.
+int adopt_device_sell(Problem* P, int nrows, int g, const std::vector<int>& sptr_h, const std::vector<int>& slen_h,
+                      int* col, double* v64, long long tot, acs::SellMat& M) {
+    int* sptr = nullptr; int* slen = nullptr;
+    float* v32 = nullptr; unsigned short* v16 = nullptr;
+    const bool bf16 = P->set.a_storage == ACS_STORE_BF16;
+    if (dalloc(P, &sptr, sptr_h.size()) || dalloc(P, &slen, slen_h.size()) ||
+        (bf16 ? dalloc(P, &v16, (size_t)tot) : dalloc(P, &v32, (size_t)tot)))
+        return ACS_ERR_OOM;
+    int rc = 0;
+    rc |= upload(P, sptr, sptr_h.data(), sptr_h.size());
+    rc |= upload(P, slen, slen_h.data(), slen_h.size());
+    if (tot > 0) {
+        const long long nb = std::min<long long>((tot + 255) / 256, 4096);
+        if (bf16) narrow_bf16<<<(unsigned)nb, 256, 0, P->stream>>>(v64, v16, tot);
+        else narrow_f32<<<(unsigned)nb, 256, 0, P->stream>>>(v64, v32, tot);
+        rc |= cudaGetLastError() != cudaSuccess;
+    }
+    if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) return ACS_ERR_CUDA;
+    M.nrows = nrows; M.nslices = (int)slen_h.size(); M.g = g;
     M.sptr = sptr; M.slen = slen; M.col = col; M.v32 = v32; M.v64 = v64; M.v16 = v16;
     return ACS_SOLVED;
 }
@@ -368,8 +401,19 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     acs_settings set;
     if (settings) set = *settings; else acs_settings_default(&set);
     if (!acs::host::valid_settings(set)) return ACS_ERR_ARG;
+    // ACS_TRACE_CREATE set: the host time of each step on stderr
+    const bool trace = getenv("ACS_TRACE_CREATE") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto step = [&](const char* what) {
+        if (!trace) return;
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "acs create: %-10s %8.2f ms\n", what,
+                std::chrono::duration<double, std::milli>(t - t_last).count());
+        t_last = t;
+    };
     const int vrc = acs::host::no_throw(
         [&] { return acs::host::validate(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims); });
+    step("validate");
     if (vrc != ACS_SOLVED) return vrc;
     if (set.polish_tol > 0 && n_soc > 0) return ACS_ERR_ARG;     // the polish is for LPs
     const int nnz = (int)row_ptr[m];
@@ -389,17 +433,53 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     }
     int rc = ACS_SOLVED;
     if (acs::occupancy_grid(P) != ACS_SOLVED) { free_all(P); delete P; return ACS_ERR_CUDA; }
+    step("stream");
     const long long warps = (long long)P->grid32 * acs::kThreads / 32;
     acs::host::HostProblem H;
     acs::host::HostTranspose HT_csr;
     P->full_rows = (long long)nnz == (long long)m * (long long)n;
     P->dense = acs::host::dense_mode(set, m, P->full_rows);
     const bool cb = cb_wanted(set, P->dense);
-    const int brc = acs::host::no_throw([&] {
-        return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H,
-                                cb ? &HT_csr : nullptr);
-    });
-    if (brc != ACS_SOLVED) { free_all(P); delete P; return brc; }
+    // without the column-blocked layout the images are built on the device
+    // (the host does the relabelling and the O(m + n) slice tables); a column
+    // too long for the device sort falls back to the host builder
+    bool on_device = false;
+    if (!cb) {
+        const int mrc = acs::host::no_throw([&] {
+            acs::host::build_meta(m, n, row_ptr, b, c, n_orthant, n_soc, soc_dims, H);
+            return ACS_SOLVED;
+        });
+        if (mrc != ACS_SOLVED) { free_all(P); delete P; return mrc; }
+        step("relabel");
+        const int gA = acs::host::choose_g(m, nnz, warps), gAT = acs::host::choose_g(n, nnz, warps);
+        acs::DeviceSell D;
+        int drc = ACS_ERR_OOM;
+        try {
+            drc = acs::device_sell(P, row_ptr, col, val, H.perm, gA, gAT, D);
+        } catch (...) {
+            drc = ACS_ERR_OOM;
+        }
+        if (drc == ACS_SOLVED) {
+            if (adopt_device_sell(P, m, gA, D.sptrA, D.slenA, D.colA, D.valA, D.totA, P->A) ||
+                adopt_device_sell(P, n, gAT, D.sptrT, D.slenT, D.colT, D.valT, D.totT, P->AT)) {
+                free_all(P); delete P; return ACS_ERR_OOM;
+            }
+            P->padded_A = D.totA;
+            P->padded_AT = D.totT;
+            on_device = true;
+        } else if (drc != 1) {
+            free_all(P); delete P; return drc;
+        }
+        step("device build");
+    }
+    if (!on_device) {
+        const int brc = acs::host::no_throw([&] {
+            return acs::host::build(m, n, row_ptr, col, val, b, c, n_orthant, n_soc, soc_dims, warps, warps, H,
+                                    cb ? &HT_csr : nullptr);
+        });
+        if (brc != ACS_SOLVED) { free_all(P); delete P; return brc; }
+        step("build");
+    }
     // column-blocked images of A (rows relabelled as above) and A'
     acs::host::HostCb CA, CT;
     bool cb_ok = false;
@@ -422,8 +502,10 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         HT_csr = acs::host::HostTranspose();
     }
     P->perm = H.perm;
-    P->padded_A = (long long)H.A.col.size();
-    P->padded_AT = (long long)H.AT.col.size();
+    if (!on_device) {
+        P->padded_A = (long long)H.A.col.size();
+        P->padded_AT = (long long)H.AT.col.size();
+    }
     P->bnorm = H.bnorm;
     P->cnorm = H.cnorm;
     const HostSell& HA = H.A;
@@ -431,10 +513,11 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     const std::vector<double>& bperm = H.bperm;
     const std::vector<int>& off = H.soc_off;
 
-    if (acs::host::no_throw([&] { return upload_sell(P, HA, P->A, !cb_ok); }) ||
-        acs::host::no_throw([&] { return upload_sell(P, HT, P->AT, !cb_ok); })) {
+    if (!on_device && (acs::host::no_throw([&] { return upload_sell(P, HA, P->A, !cb_ok); }) ||
+                       acs::host::no_throw([&] { return upload_sell(P, HT, P->AT, !cb_ok); }))) {
         free_all(P); delete P; return ACS_ERR_OOM;
     }
+    step("upload A");
     if (cb_ok) {
         if (acs::host::no_throw([&] { return upload_cb(P, CA, P->Acb); }) ||
             acs::host::no_throw([&] { return upload_cb(P, CT, P->ATcb); })) {
@@ -473,6 +556,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         cudaEventCreate(&P->ev_polish[0]) != cudaSuccess || cudaEventCreate(&P->ev_polish[1]) != cudaSuccess) {
         free_all(P); delete P; return ACS_ERR_CUDA;
     }
+    step("allocate");
     rc = 0;
     rc |= upload(P, P->soc_off, off.data(), n_soc + 1);
     rc |= upload(P, P->b, bperm.data(), m);
@@ -484,6 +568,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     rc |= cudaMemsetAsync(P->ctl, 0, sizeof(acs::Control), P->stream) != cudaSuccess;
     if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) { free_all(P); delete P; return ACS_ERR_CUDA; }
     if (P->grid32 > P->max_ctas || P->grid64 > P->max_ctas || P->grid32 > 256 || P->grid64 > 256) { free_all(P); delete P; return ACS_ERR_CUDA; }
+    step("finish");
     *out = reinterpret_cast<acs_problem*>(P);
     return ACS_SOLVED;
 }
@@ -609,6 +694,24 @@ int acs_debug_sell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* 
         if (out_val) std::copy(S.val.begin(), S.val.end(), out_val);
         return ACS_SOLVED;
     });
+}
+
+int acs_debug_images(acs_problem* h, int32_t which, int32_t* info, int32_t* sptr, int32_t* slen, int32_t* out_col,
+                     double* out_val, float* out_v32) {
+    Problem* P = reinterpret_cast<Problem*>(h);
+    if (!P || !info || (which != 0 && which != 1)) return ACS_ERR_ARG;
+    const acs::SellMat& M = which == 0 ? P->A : P->AT;
+    const long long tot = which == 0 ? P->padded_A : P->padded_AT;
+    info[0] = M.nrows; info[1] = M.nslices; info[2] = M.g; info[3] = (int32_t)tot;
+    if (cudaSetDevice(P->device) != cudaSuccess || cudaStreamSynchronize(P->stream) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    if ((sptr && cudaMemcpy(sptr, M.sptr, sizeof(int) * (M.nslices + 1), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (slen && cudaMemcpy(slen, M.slen, sizeof(int) * M.nslices, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (out_col && cudaMemcpy(out_col, M.col, sizeof(int) * tot, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (out_val && cudaMemcpy(out_val, M.v64, sizeof(double) * tot, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (out_v32 && M.v32 && cudaMemcpy(out_v32, M.v32, sizeof(float) * tot, cudaMemcpyDeviceToHost) != cudaSuccess))
+        return ACS_ERR_CUDA;
+    return ACS_SOLVED;
 }
 
 int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,

@@ -225,6 +225,29 @@ struct HostSell {
 // Rows are given by (beg[r], end[r]) ranges into (cols, vals); padding
 // entries repeat column 0 with value 0.  nslices = -1 if the padded size
 // does not fit 32-bit offsets.
+// Slice table of a sliced-ELLPACK image with g lanes per row for rows of the
+// given lengths (len(r), r < nrows): chunks per slice (slen) and the start
+// of each slice (sptr, nslices + 1 entries); returns the image's size in
+// entries (>= INT32_MAX: does not fit 32-bit offsets).
+template <typename Len>
+long long sell_shape(int nrows, int g, const Len& len, std::vector<int>& sptr, std::vector<int>& slen) {
+    const int h = 32 / g;                     // rows per slice
+    const int nslices = (nrows + h - 1) / h;
+    sptr.assign(nslices + 1, 0);
+    slen.assign(nslices, 0);
+    long long total = 0;
+    for (int sl = 0; sl < nslices; ++sl) {
+        long long mx = 0;
+        for (int r = sl * h; r < std::min(nrows, sl * h + h); ++r) mx = std::max<long long>(mx, len(r));
+        const long long chunks = (mx + g - 1) / g;
+        slen[sl] = (int)chunks;
+        sptr[sl] = (int)std::min<long long>(total, INT32_MAX);
+        total += 32 * chunks;
+    }
+    sptr[nslices] = (int)std::min<long long>(total, INT32_MAX);
+    return total;
+}
+
 inline HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, const std::vector<long long>& end,
                            const int* cols, const double* vals, int threads = 1) {
     HostSell H;
@@ -232,18 +255,7 @@ inline HostSell build_sell(int nrows, int g, const std::vector<long long>& beg, 
     H.nrows = nrows;
     H.g = g;
     H.nslices = (nrows + h - 1) / h;
-    H.sptr.assign(H.nslices + 1, 0);
-    H.slen.assign(H.nslices, 0);
-    long long total = 0;
-    for (int sl = 0; sl < H.nslices; ++sl) {
-        long long mx = 0;
-        for (int r = sl * h; r < std::min(nrows, sl * h + h); ++r) mx = std::max(mx, end[r] - beg[r]);
-        const long long chunks = (mx + g - 1) / g;
-        H.slen[sl] = (int)chunks;
-        H.sptr[sl] = (int)std::min<long long>(total, INT32_MAX);
-        total += 32 * chunks;
-    }
-    H.sptr[H.nslices] = (int)std::min<long long>(total, INT32_MAX);
+    const long long total = sell_shape(nrows, g, [&](int r) { return end[r] - beg[r]; }, H.sptr, H.slen);
     if (total >= INT32_MAX) { H.col.clear(); H.nslices = -1; return H; }
     H.col.resize(total);
     H.val.resize(total);
@@ -396,21 +408,45 @@ struct HostTranspose {
     raw_vector<double> vals;
 };
 
+// Everything of the host preparation but the matrix images: the relabelling
+// (rows sorted by length, descending, within windows, so that the rows of a
+// slice have similar lengths and padding is small), b in that order, the cone
+// offsets and the norms of b and c.
+inline void build_meta(int32_t m, int32_t n, const int64_t* row_ptr, const double* b, const double* c,
+                       int32_t n_orthant, int32_t n_soc, const int32_t* soc_dims, HostProblem& H) {
+    const long long nnz = row_ptr[m];
+    std::vector<int>& perm = H.perm;
+    perm.resize(m);
+    const int T = host_threads(nnz);
+    const int nwin = (m + kSortWindow - 1) / kSortWindow;
+    const int tt = std::min(T, nwin);
+    parallel_for(tt, [&](int t) {                            // windows are independent
+        for (int w = (int)part_lo(nwin, t, tt); w < (int)part_lo(nwin, t + 1, tt); ++w) {
+            const int w0 = w * kSortWindow, w1 = std::min(m, w0 + kSortWindow);
+            for (int i = w0; i < w1; ++i) perm[i] = i;
+            std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b2) {
+                return (row_ptr[a + 1] - row_ptr[a]) > (row_ptr[b2 + 1] - row_ptr[b2]);
+            });
+        }
+    });
+    H.bperm.resize(m);
+    for (int r = 0; r < m; ++r) H.bperm[r] = b[perm[r]];
+    H.soc_off.resize(n_soc + 1);
+    H.soc_off[0] = n_orthant;
+    for (int i = 0; i < n_soc; ++i) H.soc_off[i + 1] = H.soc_off[i] + soc_dims[i];
+    double bn = 0, cn = 0;
+    for (int i = 0; i < m; ++i) bn += b[i] * b[i];
+    for (int j = 0; j < n; ++j) cn += c[j] * c[j];
+    H.bnorm = sqrt(bn);
+    H.cnorm = sqrt(cn);
+}
+
 inline int build(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                  const double* b, const double* c, int32_t n_orthant, int32_t n_soc, const int32_t* soc_dims,
                  long long warps_A, long long warps_AT, HostProblem& H, HostTranspose* keep_T = nullptr) {
     const int nnz = (int)row_ptr[m];
-    // relabel the constraints: sort rows by length (descending) within windows,
-    // so that the rows of a slice have similar lengths and padding is small
-    std::vector<int>& perm = H.perm;
-    perm.resize(m);
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int w0 = 0; w0 < m; w0 += kSortWindow) {
-        const int w1 = std::min(m, w0 + kSortWindow);
-        std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b2) {
-            return (row_ptr[a + 1] - row_ptr[a]) > (row_ptr[b2 + 1] - row_ptr[b2]);
-        });
-    }
+    build_meta(m, n, row_ptr, b, c, n_orthant, n_soc, soc_dims, H);
+    const std::vector<int>& perm = H.perm;
     const int T = host_threads(nnz);
     {
         std::vector<long long> beg(m), end(m);
@@ -431,16 +467,6 @@ inline int build(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* co
         }
     }
     if (H.A.nslices < 0 || H.AT.nslices < 0) return ACS_ERR_CSR;
-    H.bperm.resize(m);
-    for (int r = 0; r < m; ++r) H.bperm[r] = b[perm[r]];
-    H.soc_off.resize(n_soc + 1);
-    H.soc_off[0] = n_orthant;
-    for (int i = 0; i < n_soc; ++i) H.soc_off[i + 1] = H.soc_off[i] + soc_dims[i];
-    double bn = 0, cn = 0;
-    for (int i = 0; i < m; ++i) bn += b[i] * b[i];
-    for (int j = 0; j < n; ++j) cn += c[j] * c[j];
-    H.bnorm = sqrt(bn);
-    H.cnorm = sqrt(cn);
     return ACS_SOLVED;
 }
 

@@ -227,6 +227,18 @@ struct Problem {
 
 // launches (acs_iter.cu)
 int launch_solve(Problem* P, double tol, int max_iter);
+// Sliced-ELLPACK images of A (rows in the order perm) and A' built on the
+// device (acs_devbuild.cu): device col/value arrays (owned by P) and the
+// host slice tables.  Returns ACS_SOLVED, 1 if a column is too long for the
+// device sort (build on the host instead), or an error.
+struct DeviceSell {
+    std::vector<int> sptrA, slenA, sptrT, slenT;
+    int *colA = nullptr, *colT = nullptr;
+    double *valA = nullptr, *valT = nullptr;
+    long long totA = 0, totT = 0;
+};
+int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const double* val,
+                const std::vector<int>& perm, int gA, int gAT, DeviceSell& out);
 // LP crossover polish of the current iterate into px, pw, pz; pres[0..5] its
 // residuals, pres[8..12] {|B|, CG iterations x, y, 1 = completed, 1 =
 // factored}.  rel: the solves stop at rel times their first residual (or at
