@@ -660,10 +660,13 @@ def gpu_arm(args) -> None:
             t_e2e += time.perf_counter() - t0
             if st2 != capi.SOLVED:
                 raise RuntimeError("e2e solve did not converge")
-        pa, pat = info["padded_A"], info["padded_AT"]
-        h2d = 16 * (pa + pat) + 8 * (inst.m + inst.n) + 4 * (len(inst.soc_dims) + 1)
-        h2d += 4 * ((inst.m + inst.n) // 8 + 4)          # slice tables (upper bound)
-        d2h = 8 * (2 * inst.n + inst.m) + 256
+        # the create step uploads the CSR's columns and values (the images of A
+        # and A' are built on the device), each relabelled row's start and
+        # length, the column offsets of A', slice tables, b, c, cone offsets;
+        # it reads back the column counts of A'
+        h2d = 12 * inst.nnz + 12 * inst.m + 8 * (inst.n + 1) + 8 * (inst.m + inst.n)
+        h2d += 4 * (len(inst.soc_dims) + 1) + 4 * ((inst.m + inst.n) // 8 + 4)   # slice tables (upper bound)
+        d2h = 8 * (2 * inst.n + inst.m) + 4 * inst.n + 256
         t_e2e = max_over_ranks(t_e2e, pg, "cuda")
         e2e = {"value": replica_throughput(world, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
