@@ -465,14 +465,21 @@ def polish_tol(args) -> float:
     return POLISH_TOL.get(args.workload, 0.0)
 
 
-def polish_bytes(m: int, n: int, nnz: int, corrections: int, attempts: int) -> float:
-    """Algorithmic bytes of the crossover polishes of one solve: per CG
-    iteration an FP64 pass over A' and one over A (12 bytes a nonzero, the
-    vectors once) and the vector step; per polish about 14 further FP64 passes
-    (support, Jacobi, the rounds' residuals and q refreshes, z_y, z, KKT)."""
-    per_cg = 2 * (12.0 * nnz) + 16.0 * (m + n) + 56.0 * m
-    per_pass = 12.0 * nnz + 16.0 * (m + n)
-    return corrections * per_cg + attempts * 14 * per_pass
+def polish_bytes(m: int, n: int, nnz: int, corrections: int, attempts: int, support: int = 0,
+                 support_entries: int = 0) -> float:
+    """Algorithmic bytes of the crossover polishes of one solve.  Their CG
+    passes read only the support's part of the matrix (A_B, and the rows of A'
+    on B): per CG iteration 2 x 12 bytes per entry of A_B, the support's
+    vectors and the m-vectors of the vector step; per polish about 10 passes
+    on the support (support, Jacobi, the rounds' residuals and q refreshes)
+    and 4 over all of A (z_y, z, KKT), FP64.  Without the support figures
+    (support_entries = 0: the factored path) every pass counts all of A."""
+    nb = support_entries if support_entries > 0 else nnz
+    nB = support if support_entries > 0 else n
+    per_cg = 2 * (12.0 * nb) + 16.0 * (m + nB) + 56.0 * m
+    per_support_pass = 12.0 * nb + 16.0 * (m + nB)
+    per_full_pass = 12.0 * nnz + 16.0 * (m + n)
+    return corrections * per_cg + attempts * (10 * per_support_pass + 4 * per_full_pass)
 
 
 def solver_overrides(args) -> dict:
@@ -716,12 +723,16 @@ def gpu_arm(args) -> None:
                 "attempts": passes["polish_attempts"], "taken": passes["polish_taken"],
                 "cg_iterations": passes["polish_corrections"], "factored": passes["polish_factored"],
                 "iteration_launch_ms": launch_ms, "polish_ms": polish_ms,
+                "support": passes["polish_support"], "support_entries": passes["polish_support_entries"],
                 "roofline": roofline_entry("polish_kernel", polish_bytes(inst.m, inst.n, inst.nnz,
                                                                          passes["polish_corrections"],
-                                                                         passes["polish_attempts"]),
+                                                                         passes["polish_attempts"],
+                                                                         passes["polish_support"],
+                                                                         passes["polish_support_entries"]),
                                            polish_ms, None,
-                                           bytes_formula="per CG iteration 24 nnz + 16 (m+n) + 56 m, "
-                                                         "per polish 14 x (12 nnz + 16 (m+n))")
+                                           bytes_formula="per CG iteration 24 nnz_B + 16 (m+|B|) + 56 m, per "
+                                                         "polish 10 x (12 nnz_B + 16 (m+|B|)) + 4 x (12 nnz + "
+                                                         "16 (m+n)); nnz_B = stored entries of A_B")
                 if polish_ms > 0 else None}
             line["no_polish"] = plain
         if subs:

@@ -378,7 +378,9 @@ int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
  * of the FP32-to-FP64 CG hand-over}; n >= 12; with n >= 16 also {polishes
  * tried, polishes taken, their CG iterations (factored M: corrections), polishes
  * that factored M} of the last solve with polish_tol (or of acs_polish calls
- * since).  Counters of a polished solve add up all its segments.  Waits for
+ * since); with n >= 18 also {|B| of the last polish, stored entries of its
+ * A_B (the rows of A on B's columns, which its CG passes read; 0 when it
+ * factored M)}.  Counters of a polished solve add up all its segments.  Waits for
  * queued work.
  * acs_debug_layout: out[10] = {column-blocked layout in use, blocks of A,
  * width, stored entries, blocks of A', width, stored entries, dynamic shared

@@ -880,12 +880,13 @@ def acs_debug_cbsell(m, n, row_ptr, col, val, which: int, width_limit: int, ctas
 
 PASS_COUNTS = ("cg_A", "cg_At", "fp64_A", "fp64_At", "rescalings", "checks", "fp32_outer_A",
                "fp32_outer_At", "outer32_end", "iterations", "cg_iterations", "cg_switch_at",
-               "polish_attempts", "polish_taken", "polish_corrections", "polish_factored")
+               "polish_attempts", "polish_taken", "polish_corrections", "polish_factored",
+               "polish_support", "polish_support_entries")
 
 
 def acs_debug_pass_counts(h) -> dict:
-    out = np.zeros(16, dtype=np.int64)
-    rc = lib().acs_debug_pass_counts(C.c_void_p(h), _ptr(out, C.c_int64), 16)
+    out = np.zeros(len(PASS_COUNTS), dtype=np.int64)
+    rc = lib().acs_debug_pass_counts(C.c_void_p(h), _ptr(out, C.c_int64), len(PASS_COUNTS))
     if rc < 0:
         raise AcsError(rc, "acs_debug_pass_counts")
     return {k: int(out[i]) for i, k in enumerate(PASS_COUNTS)}

@@ -245,6 +245,8 @@ int polish_once(Problem* P, int rounds, double rel, double* info7) {
     P->pol.taken += take ? 1 : 0;
     P->pol.corrections += (long long)(h16[9] + h16[10]);
     P->pol.factored += h16[12] == 1.0 ? 1 : 0;
+    P->pol.support = (long long)h16[8];
+    P->pol.support_entries = h16[12] == 1.0 ? 0 : P->padded_B;
     return take ? ACS_SOLVED : ACS_POLISH_KEPT;
 }
 
@@ -770,7 +772,9 @@ int acs_debug_pass_counts(acs_problem* h, int64_t* out, int32_t n) {
     out[8] = C.outer32_end; out[9] = C.l; out[10] = C.cg_iters; out[11] = C.switched_at;
     if (n < 16) return 12;
     out[12] = P->pol.attempts; out[13] = P->pol.taken; out[14] = P->pol.corrections; out[15] = P->pol.factored;
-    return 16;
+    if (n < 18) return 16;
+    out[16] = P->pol.support; out[17] = P->pol.support_entries;
+    return 18;
 }
 
 int acs_bench_passes(acs_problem* h, int32_t kind, int32_t reps, int32_t smem_bytes, double* us_per_rep) {

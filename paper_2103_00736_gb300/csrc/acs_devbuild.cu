@@ -155,7 +155,122 @@ inline unsigned grid_for(long long work, int per_block) {
     return (unsigned)std::max<long long>(1, std::min<long long>((work + per_block - 1) / per_block, 152LL * 16));
 }
 
+// The support's indicator O_j = (x_j > z_j) (the crossover polish's B).
+__global__ void support_indicator(int n, const double* __restrict__ x, const double* __restrict__ z,
+                                  double* __restrict__ O) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        O[j] = x[j] > z[j] ? 1.0 : 0.0;
+}
+
+// Entries of each row of A kept in A_B (nonzero value, column in the support).
+__global__ void count_support_entries(const SellMat A, const double* __restrict__ O, int* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int g = A.g, h = 32 / g;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices; sl += nw) {
+        const int len = A.slen[sl];
+        long long idx = A.sptr[sl] + lane;
+        int c = 0;
+        for (int k = 0; k < len; ++k, idx += 32) c += (A.v64[idx] != 0.0 && O[A.col[idx]] != 0.0) ? 1 : 0;
+        for (int o = g / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        const long long row = sl * h + lane / g;
+        if ((lane & (g - 1)) == 0 && row < A.nrows) cnt[row] = c;
+    }
+}
+
+// A_B in the layout of A (same lanes per row, its own slice table): each
+// row's kept entries in their order in A, placed by a prefix count over the
+// row's lanes chunk by chunk.
+__global__ void pack_support_entries(const SellMat A, const double* __restrict__ O, const int* __restrict__ sptrB,
+                                     int* __restrict__ colB, double* __restrict__ valB) {
+    const int lane = threadIdx.x & 31;
+    const int g = A.g, h = 32 / g, lr = lane / g, t = lane % g;
+    const unsigned gmask = g == 32 ? 0xffffffffu : ((1u << g) - 1u);
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices; sl += nw) {
+        const int len = A.slen[sl];
+        long long idx = A.sptr[sl] + lane;
+        const long long base = sptrB[sl];
+        int run = 0;                                    // kept entries of this lane's row so far
+        for (int k = 0; k < len; ++k, idx += 32) {
+            const double v = A.v64[idx];
+            const int j = A.col[idx];
+            const bool keep = v != 0.0 && O[j] != 0.0;
+            const unsigned bits = (__ballot_sync(0xffffffffu, keep) >> (lr * g)) & gmask;
+            if (keep) {
+                const int pos = run + __popc(bits & ((1u << t) - 1u));
+                const long long out = base + 32LL * (pos / g) + (long long)lr * g + (pos % g);
+                colB[out] = j;
+                valB[out] = v;
+            }
+            run += __popc(bits);
+        }
+        (void)h;
+    }
+}
+
 }  // namespace
+
+// A_B: the rows of A restricted to the columns of the support x > z of the
+// problem's current iterate, built on the device into the polish's buffers
+// (allocated at the first call, sized like A's image).  Sets X.O to the
+// support's indicator.  out: the image (FP64 values only).
+int support_rows(Problem* P, SellMat& out) {
+    const int m = P->m, n = P->n;
+    const SellMat& A = P->A;
+    cudaStream_t st = P->stream;
+    if (!P->bcol) {
+        void* a[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t sz[5] = {sizeof(int) * (size_t)std::max<long long>(P->padded_A, 1),
+                              sizeof(double) * (size_t)std::max<long long>(P->padded_A, 1),
+                              sizeof(int) * (size_t)(A.nslices + 1), sizeof(int) * (size_t)std::max(A.nslices, 1),
+                              sizeof(int) * (size_t)m};
+        for (int k = 0; k < 5; ++k) {
+            if (cudaMalloc(&a[k], sz[k]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int q = 0; q < k; ++q) cudaFree(a[q]);
+                return ACS_ERR_OOM;
+            }
+        }
+        for (int k = 0; k < 5; ++k) P->allocations.push_back(a[k]);
+        P->bcol = (int*)a[0];
+        P->bval = (double*)a[1];
+        P->bsptr = (int*)a[2];
+        P->bslen = (int*)a[3];
+        P->bcnt = (int*)a[4];
+    }
+    support_indicator<<<grid_for(n, 256), 256, 0, st>>>(n, P->x, P->z, P->X.O);
+    count_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bcnt);
+    std::vector<int> cnt(m);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(cnt.data(), P->bcnt, sizeof(int) * m, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    std::vector<int> sptr, slen;
+    const long long tot = host::sell_shape(m, A.g, [&](int r) { return (long long)cnt[r]; }, sptr, slen);
+    if (tot > P->padded_A) return ACS_ERR_CSR;             // cannot happen: a subset of A's entries
+    if (cudaMemcpyAsync(P->bsptr, sptr.data(), sizeof(int) * sptr.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(P->bslen, slen.data(), sizeof(int) * slen.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(P->bcol, 0, sizeof(int) * std::max<long long>(tot, 1), st) != cudaSuccess ||
+        cudaMemsetAsync(P->bval, 0, sizeof(double) * std::max<long long>(tot, 1), st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    pack_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bsptr, P->bcol, P->bval);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return ACS_ERR_CUDA;
+    out = SellMat{};
+    out.nrows = m;
+    out.nslices = A.nslices;
+    out.g = A.g;
+    out.sptr = P->bsptr;
+    out.slen = P->bslen;
+    out.col = P->bcol;
+    out.v64 = P->bval;
+    out.v32 = nullptr;
+    out.v16 = nullptr;
+    P->padded_B = tot;
+    return ACS_SOLVED;
+}
 
 int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const double* val,
                 const std::vector<int>& perm, int gA, int gAT, DeviceSell& out) {

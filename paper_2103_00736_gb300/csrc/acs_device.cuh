@@ -1736,6 +1736,45 @@ static __device__ __noinline__ void phase_polish_z(const IterParams<double>& P, 
     sell_rows<double>(P.AT, gather, epi);
 }
 
+// Products over the rows of A' restricted to the support: a lane whose row
+// j has O_j = 0 issues no loads (its result is 0), so a pass costs about the
+// support's share of the matrix stream and gathers.  Plain loop (one chunk
+// at a time); FP64 values.
+template <typename Epi, typename Gather>
+__device__ __forceinline__ void sell_rows_active(const SellMat& M, const double* __restrict__ O, Gather gather,
+                                                 Epi epi) {
+    const int lane = threadIdx.x & 31;
+    const int g = M.g, h = 32 / g;
+    for (int sl = global_warp(); sl < M.nslices; sl += global_warps()) {
+        const int row = sl * h + lane / g;
+        const bool act = row < M.nrows && O[row] != 0.0;
+        const int len = __ldg(M.slen + sl);
+        int idx = __ldg(M.sptr + sl) + lane;
+        double acc = 0.0;
+        if (act)
+            for (int k = 0; k < len; ++k, idx += 32) acc = fma(ld_stream(M.v64 + idx), gather(ld_stream(M.col + idx)), acc);
+        for (int o = g / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((lane & (g - 1)) == 0 && row < M.nrows) epi(row, act ? acc : 0.0);
+    }
+}
+
+// The polish's CG half-step t = O^2 A'u and its q refresh q = O A'w,
+// g = O (p + q), on the support's rows only (O is the support's indicator).
+static __device__ __noinline__ void phase_polish_cg_At(const IterParams<double>& P) {
+    const double* u = P.V.u;
+    sell_rows_active(P.AT, P.X.O, [u](int i) { return u[i]; },
+                     [&](int j, double sum) { P.V.t[j] = P.V.O2[j] * sum; });
+}
+static __device__ __noinline__ void phase_polish_q(const IterParams<double>& P) {
+    const double* w = P.X.w;
+    sell_rows_active(P.AT, P.X.O, [w](int i) { return w[i]; }, [&](int j, double sum) {
+        const double o = P.X.O[j];
+        const double q = o * sum;
+        P.X.q[j] = q;
+        P.X.g[j] = o * (P.X.p[j] + q);
+    });
+}
+
 // The projection residual r0 = b_tilde - A g with its rounding floor: the
 // partials are r0' J^{-1} r0 and sum_i J^{-1}_i (b_tilde_i^2 + sum_j A_ij^2
 // h_j^2), h (in c_hat) the magnitudes whose rounding the residual carries
@@ -1773,7 +1812,7 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
     double gam_last = INFINITY, target = 0.0;
     for (int round = 0; round < rounds; ++round) {
         if (round > 0) {
-            phase_update(P, false, false);
+            phase_polish_q(P);
             if (!grid_sync(&P.ctl->err)) return false;
         }
         phase_polish_rhs(P);
@@ -1809,7 +1848,7 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
         while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
             double dl[1];
             const int op1[1] = {0};
-            phase_cg_At(P);
+            phase_polish_cg_At(P);
             if (!grid_sync(&P.ctl->err)) return false;
             phase_cg_A(P);
             if (!grid_sync(&P.ctl->err)) return false;
@@ -1835,7 +1874,7 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
         }
         cg_total += k;
     }
-    phase_update(P, false, false);
+    phase_polish_q(P);
     return grid_sync(&P.ctl->err);
 }
 

@@ -169,6 +169,7 @@ struct IterParams {
 
 struct PolishStats {
     long long attempts = 0, taken = 0, corrections = 0, factored = 0;
+    long long support = 0, support_entries = 0;   // |B| and stored entries of A_B of the last polish
 };
 
 struct Problem {
@@ -206,6 +207,9 @@ struct Problem {
     bool state_clobbered = false;        // a polish overwrote the iteration state
     double *px = nullptr, *pw = nullptr, *pz = nullptr, *pwork = nullptr, *pres = nullptr;   // polish (lazy)
     double *pdM = nullptr, *pdX = nullptr;   // polish's factored A_B A_B' when the handle has no scratch
+    int *bcol = nullptr, *bsptr = nullptr, *bslen = nullptr, *bcnt = nullptr;   // A_B of the polish (lazy)
+    double* bval = nullptr;
+    long long padded_B = 0;
     double* psaveO = nullptr;                 // the scaling O and the multiplier w kept across a
     double* psaveW = nullptr;                 //   polish of a polished solve
     PolishStats pol;                          // polish attempts of the last solve (or acs_polish calls)
@@ -239,6 +243,9 @@ struct DeviceSell {
 };
 int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const double* val,
                 const std::vector<int>& perm, int gA, int gAT, DeviceSell& out);
+// The crossover polish's A_B (rows of A on the support x > z of the current
+// iterate) on the device; sets X.O to the support's indicator.
+int support_rows(Problem* P, SellMat& out);
 // LP crossover polish of the current iterate into px, pw, pz; pres[0..5] its
 // residuals, pres[8..12] {|B|, CG iterations x, y, 1 = completed, 1 =
 // factored}.  rel: the solves stop at rel times their first residual (or at

@@ -386,7 +386,17 @@ int launch_polish(Problem* P, int rounds, double rel) {
     Q.X.w = P->pwork;                     // the solves' w: the iterate's w stays
     Q.dM = dM;
     Q.dX = dX;
-    IterParams<double> Qk = Q;
+    IterParams<double> Qk = Q;            // the residuals of the polished point: all of A
+    if (!dM) {
+        // CG corrections: the passes over the rows of A run on A_B, the rows of
+        // A restricted to the support's columns (the other columns carry
+        // O_j = 0); those over A' skip the rows off the support
+        SellMat AB;
+        const int rc = support_rows(P, AB);
+        if (rc != ACS_SOLVED) return rc;
+        Q.A = AB;
+        Q.full_rows = 0;
+    }
     Qk.x = P->px;
     Qk.z = P->pz;
     Qk.X.w = P->pw;
