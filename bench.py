@@ -85,7 +85,7 @@ DENSE_N = {"dense_lp": 10000, "dense_socp": 2900}
 # LP crossover polish inside the solve (setting polish_tol): on for the sparse
 # LPs, whose supports settle early; off for the dense LP, whose polish systems
 # (square A_B of m = 8000 > 4096, CG) do not converge, and for cones
-POLISH_TOL = {"large_lp": 1e-2, "small_lp": 1e-2}
+POLISH_TOL = {"large_lp": 2e-2, "small_lp": 1e-2}
 BATCH_MAX_ITER = 5000       # per member; members not solved by then count as unsolved
 def nproc() -> int:
     try:
@@ -706,8 +706,12 @@ def gpu_arm(args) -> None:
                                                      " + checks*24 nnz + rescalings*8 nnz"),
             "clocks": clk,
             "e2e": e2e,
+            # per solve: 6 launches per iteration segment (4 resets/initialisations, the FP32 and the
+            # FP64 persistent launch); per polish 2 (barrier reset, polish kernel) and 3 more that
+            # build A_B when its corrections run CG (no factored M)
             "gpu_launches": (6 * (1 + max(passes.get("polish_attempts", 0) - passes.get("polish_taken", 0), 0))
-                             + 2 * passes.get("polish_attempts", 0)) * args.steps,
+                             + (5 if passes.get("polish_support_entries", 0) > 0 else 2)
+                             * passes.get("polish_attempts", 0)) * args.steps,
             "cpu_baseline": cpu,
             "layout": layout,
             "passes": passes,
@@ -1069,7 +1073,7 @@ def main():
     ap.add_argument("--dense-n", type=int, default=None, help="n of the dense workloads")
     ap.add_argument("--cone-h", type=int, default=10, help="Lorentz cone size of the dense SOCP")
     ap.add_argument("--polish-tol", type=float, default=None,
-                    help="LP crossover polish level inside the solve (default per workload: large_lp and "
+                    help="LP crossover polish level inside the solve (default per workload: large_lp 2e-2, "
                          "small_lp 1e-2, else off)")
     ap.add_argument("--no-polish", action="store_true", help="Algorithm 2 alone (no crossover polish)")
     ap.add_argument("--lp-scale", type=float, default=1.0,
