@@ -182,7 +182,7 @@ __global__ void count_support_entries(const SellMat A, const double* __restrict_
 // row's kept entries in their order in A, placed by a prefix count over the
 // row's lanes chunk by chunk.
 __global__ void pack_support_entries(const SellMat A, const double* __restrict__ O, const int* __restrict__ sptrB,
-                                     int* __restrict__ colB, double* __restrict__ valB) {
+                                     int* __restrict__ colB, double* __restrict__ valB, float* __restrict__ valB32) {
     const int lane = threadIdx.x & 31;
     const int g = A.g, h = 32 / g, lr = lane / g, t = lane % g;
     const unsigned gmask = g == 32 ? 0xffffffffu : ((1u << g) - 1u);
@@ -202,6 +202,7 @@ __global__ void pack_support_entries(const SellMat A, const double* __restrict__
                 const long long out = base + 32LL * (pos / g) + (long long)lr * g + (pos % g);
                 colB[out] = j;
                 valB[out] = v;
+                if (valB32) valB32[out] = A.v32[idx];
             }
             run += __popc(bits);
         }
@@ -215,7 +216,7 @@ __global__ void pack_support_entries(const SellMat A, const double* __restrict__
 // problem's current iterate, built on the device into the polish's buffers
 // (allocated at the first call, sized like A's image).  Sets X.O to the
 // support's indicator.  out: the image (FP64 values only).
-int support_rows(Problem* P, SellMat& out) {
+int support_rows(Problem* P, SellMat& out, bool with_f32) {
     const int m = P->m, n = P->n;
     const SellMat& A = P->A;
     cudaStream_t st = P->stream;
@@ -239,6 +240,15 @@ int support_rows(Problem* P, SellMat& out) {
         P->bslen = (int*)a[3];
         P->bcnt = (int*)a[4];
     }
+    if (with_f32 && !P->bval32) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, sizeof(float) * (size_t)std::max<long long>(P->padded_A, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return ACS_ERR_OOM;
+        }
+        P->allocations.push_back(q);
+        P->bval32 = (float*)q;
+    }
     support_indicator<<<grid_for(n, 256), 256, 0, st>>>(n, P->x, P->z, P->X.O);
     count_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bcnt);
     std::vector<int> cnt(m);
@@ -256,7 +266,10 @@ int support_rows(Problem* P, SellMat& out) {
         cudaMemsetAsync(P->bcol, 0, sizeof(int) * std::max<long long>(tot, 1), st) != cudaSuccess ||
         cudaMemsetAsync(P->bval, 0, sizeof(double) * std::max<long long>(tot, 1), st) != cudaSuccess)
         return ACS_ERR_CUDA;
-    pack_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bsptr, P->bcol, P->bval);
+    if (with_f32 && cudaMemsetAsync(P->bval32, 0, sizeof(float) * std::max<long long>(tot, 1), st) != cudaSuccess)
+        return ACS_ERR_CUDA;
+    pack_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bsptr, P->bcol, P->bval,
+                                                                          with_f32 ? P->bval32 : nullptr);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return ACS_ERR_CUDA;
     out = SellMat{};
     out.nrows = m;
@@ -266,7 +279,7 @@ int support_rows(Problem* P, SellMat& out) {
     out.slen = P->bslen;
     out.col = P->bcol;
     out.v64 = P->bval;
-    out.v32 = nullptr;
+    out.v32 = with_f32 ? P->bval32 : nullptr;
     out.v16 = nullptr;
     P->padded_B = tot;
     return ACS_SOLVED;

@@ -1672,13 +1672,14 @@ struct PolishOut {
 };
 
 // O = indicator of B, p = O x, q = 0, g = O (p + q), w = 0, and the count |B|.
-static __device__ __noinline__ void phase_polish_init(const IterParams<double>& P) {
+static __device__ __noinline__ void phase_polish_init(const IterParams<double>& P, float* O2_32) {
     double nb = 0.0;
     for (int j = global_tid(); j < P.n; j += global_threads()) {
         const double o = P.x[j] > P.z[j] ? 1.0 : 0.0;
         nb += o;
         P.X.O[j] = o;
         P.V.O2[j] = o;
+        if (O2_32) O2_32[j] = (float)o;
         const double pj = o * P.x[j];
         P.X.p[j] = pj;
         P.X.q[j] = 0.0;
@@ -1692,13 +1693,14 @@ static __device__ __noinline__ void phase_polish_init(const IterParams<double>& 
 }
 
 // b_tilde = b and J^{-1} = 1 / diag(A_B A_B') (1 on rows without an entry in B).
-static __device__ __noinline__ void phase_polish_jacobi(const IterParams<double>& P) {
+template <typename T>
+__device__ __noinline__ void phase_polish_jacobi(const IterParams<T>& P) {
     const double* O = P.X.O;
     auto g1 = [](int) { return 0.0; };
     auto g2 = [O](int j) { return O[j]; };
     auto epi = [&](int i, double, double s2) {
         P.X.btil[i] = P.b[i];
-        P.V.jinv[i] = s2 > 0.0 ? 1.0 / s2 : 1.0;
+        P.V.jinv[i] = (T)(s2 > 0.0 ? 1.0 / s2 : 1.0);
     };
     sell_rows2(P.A, g1, g2, epi);
 }
@@ -1740,34 +1742,36 @@ static __device__ __noinline__ void phase_polish_z(const IterParams<double>& P, 
 // j has O_j = 0 issues no loads (its result is 0), so a pass costs about the
 // support's share of the matrix stream and gathers.  Plain loop (one chunk
 // at a time); FP64 values.
-template <typename Epi, typename Gather>
+template <typename T, typename Epi, typename Gather>
 __device__ __forceinline__ void sell_rows_active(const SellMat& M, const double* __restrict__ O, Gather gather,
                                                  Epi epi) {
     const int lane = threadIdx.x & 31;
     const int g = M.g, h = 32 / g;
+    const T* __restrict__ val = sell_vals<T>(M);
     for (int sl = global_warp(); sl < M.nslices; sl += global_warps()) {
         const int row = sl * h + lane / g;
         const bool act = row < M.nrows && O[row] != 0.0;
         const int len = __ldg(M.slen + sl);
         int idx = __ldg(M.sptr + sl) + lane;
-        double acc = 0.0;
+        T acc = T(0);
         if (act)
-            for (int k = 0; k < len; ++k, idx += 32) acc = fma(ld_stream(M.v64 + idx), gather(ld_stream(M.col + idx)), acc);
+            for (int k = 0; k < len; ++k, idx += 32) acc = fma(ld_stream(val + idx), gather(ld_stream(M.col + idx)), acc);
         for (int o = g / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((lane & (g - 1)) == 0 && row < M.nrows) epi(row, act ? acc : 0.0);
+        if ((lane & (g - 1)) == 0 && row < M.nrows) epi(row, act ? acc : T(0));
     }
 }
 
 // The polish's CG half-step t = O^2 A'u and its q refresh q = O A'w,
 // g = O (p + q), on the support's rows only (O is the support's indicator).
-static __device__ __noinline__ void phase_polish_cg_At(const IterParams<double>& P) {
-    const double* u = P.V.u;
-    sell_rows_active(P.AT, P.X.O, [u](int i) { return u[i]; },
-                     [&](int j, double sum) { P.V.t[j] = P.V.O2[j] * sum; });
+template <typename T>
+__device__ __noinline__ void phase_polish_cg_At(const IterParams<T>& P) {
+    const T* u = P.V.u;
+    sell_rows_active<T>(P.AT, P.X.O, [u](int i) { return u[i]; },
+                        [&](int j, T sum) { P.V.t[j] = P.V.O2[j] * sum; });
 }
 static __device__ __noinline__ void phase_polish_q(const IterParams<double>& P) {
     const double* w = P.X.w;
-    sell_rows_active(P.AT, P.X.O, [w](int i) { return w[i]; }, [&](int j, double sum) {
+    sell_rows_active<double>(P.AT, P.X.O, [w](int i) { return w[i]; }, [&](int j, double sum) {
         const double o = P.X.O[j];
         const double q = o * sum;
         P.X.q[j] = q;
@@ -1779,7 +1783,8 @@ static __device__ __noinline__ void phase_polish_q(const IterParams<double>& P) 
 // partials are r0' J^{-1} r0 and sum_i J^{-1}_i (b_tilde_i^2 + sum_j A_ij^2
 // h_j^2), h (in c_hat) the magnitudes whose rounding the residual carries
 // (|x_B| for the x solve, |c_B| + |A_B'y| for the y solve).
-static __device__ __noinline__ void phase_polish_rhs(const IterParams<double>& P) {
+template <typename T>
+__device__ __noinline__ void phase_polish_rhs(const IterParams<T>& P) {
     double gam = 0.0, fl = 0.0;
     const double* g = P.X.g;
     const double* h = P.X.chat;
@@ -1807,15 +1812,16 @@ static __device__ __noinline__ void phase_polish_rhs(const IterParams<double>& P
 // part outside range(M) that no correction removes: the floor ends the
 // solve there instead of letting CG drift on it.  Returns false on a failed
 // barrier or a non-finite residual.
-static __device__ bool polish_solve(const IterParams<double>& P, int rounds, double rel, bool dense,
-                                    long long& cg_total) {
+template <typename T>
+__device__ bool polish_solve(const IterParams<double>& P, const IterParams<T>& PT, int rounds, double rel,
+                             bool dense, long long& cg_total) {
     double gam_last = INFINITY, target = 0.0;
     for (int round = 0; round < rounds; ++round) {
         if (round > 0) {
             phase_polish_q(P);
             if (!grid_sync(&P.ctl->err)) return false;
         }
-        phase_polish_rhs(P);
+        phase_polish_rhs(PT);
         if (!grid_sync(&P.ctl->err)) return false;
         double gam, floor_r;
         {
@@ -1830,7 +1836,7 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
         floor_r = fmax(floor_r, target);
         if (!(sqrt(fmax(gam, 0.0)) > floor_r) || (round > 0 && gam > 0.01 * gam_last)) break;
         gam_last = gam;
-        if (dense) {                                   // one exact correction: dw = X'(X r0)
+        if (sizeof(T) == 8 && dense) {                 // one exact correction: dw = X'(X r0)
             phase_dense_y(P);
             if (!grid_sync(&P.ctl->err)) return false;
             phase_dense_x(P);
@@ -1838,7 +1844,9 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
             ++cg_total;
             continue;
         }
-        const double thr = fmax(1e-13 * sqrt(gam), floor_r);
+        // an FP32 correction goes down to ~1e-5 of its round's residual; the
+        // next round's FP64 residual refines it
+        const double thr = fmax((sizeof(T) == 4 ? 1e-5 : 1e-13) * sqrt(gam), floor_r);
         double gam_prev = 1.0, alpha_prev = 1.0;
         // and, should the floor underestimate that part, the round ends
         // when the smallest residual so far has not halved in kPolishWindow
@@ -1848,16 +1856,16 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
         while (sqrt(fmax(gam, 0.0)) > thr && k < P.cg_max) {
             double dl[1];
             const int op1[1] = {0};
-            phase_polish_cg_At(P);
+            phase_polish_cg_At(PT);
             if (!grid_sync(&P.ctl->err)) return false;
-            phase_cg_A(P);
+            phase_cg_A(PT);
             if (!grid_sync(&P.ctl->err)) return false;
             grid_combine<1>(P.partials, op1, dl);
             const double beta = (k == 0) ? 0.0 : gam / gam_prev;
             const double denom = dl[0] - ((k == 0) ? 0.0 : beta * gam / alpha_prev);
             if (!(denom > 0.0)) break;                  // attainable accuracy reached
             const double alpha = gam / denom;
-            phase_cg_vec<double, false>(P, alpha, beta);
+            phase_cg_vec<T, false>(PT, alpha, (T)beta);
             if (!grid_sync(&P.ctl->err)) return false;
             double gn[1];
             grid_combine<1>(P.partials, op1, gn);
@@ -1879,8 +1887,11 @@ static __device__ bool polish_solve(const IterParams<double>& P, int rounds, dou
 }
 
 // The whole polish; Q is P with x = px, z = pz, w = pw (its KKT residuals).
-static __device__ __noinline__ void polish_loop(const IterParams<double>& P, const IterParams<double>& Q,
-                                         const PolishOut& out, int rounds, double rel) {
+// fp32: the corrections by FP32 CG on P32 (the same state, FP32 CG vectors
+// and values), refined by the FP64 residual of every round.
+static __device__ __noinline__ void polish_loop(const IterParams<double>& P, const IterParams<float>& P32,
+                                         const IterParams<double>& Q, const PolishOut& out, int rounds,
+                                         double rel, bool fp32) {
     const bool owner = blockIdx.x == 0 && threadIdx.x == 0;
     long long cg_x = 0, cg_y = 0;
     double nb[1] = {0.0};
@@ -1891,13 +1902,15 @@ static __device__ __noinline__ void polish_loop(const IterParams<double>& P, con
     bool dense = sync_smem().dM != nullptr;
     double used_dense = 0.0;
     do {
-        phase_polish_init(P);
+        if (dense) fp32 = false;
+        phase_polish_init(P, fp32 ? P32.V.O2 : nullptr);
         if (!grid_sync(&P.ctl->err)) break;
         {
             const int op[1] = {0};
             grid_combine<1>(P.partials, op, nb);
         }
-        phase_polish_jacobi(P);
+        if (fp32) phase_polish_jacobi(P32);
+        else phase_polish_jacobi(P);
         if (!grid_sync(&P.ctl->err)) break;
         if (dense) {
             phase_dense_assemble(P);
@@ -1917,10 +1930,12 @@ static __device__ __noinline__ void polish_loop(const IterParams<double>& P, con
                 used_dense = 1.0;
             }
         }
-        if (!polish_solve(P, rounds, rel, dense, cg_x)) break; // x~ = g
+        if (!(fp32 ? polish_solve(P, P32, rounds, rel, false, cg_x)
+                   : polish_solve(P, P, rounds, rel, dense, cg_x))) break;     // x~ = g
         phase_polish_ystart(P, out);
         if (!grid_sync(&P.ctl->err)) break;
-        if (!polish_solve(P, rounds, rel, dense, cg_y)) break; // d = w
+        if (!(fp32 ? polish_solve(P, P32, rounds, rel, false, cg_y)
+                   : polish_solve(P, P, rounds, rel, dense, cg_y))) break;     // d = w
         for (int i = global_tid(); i < P.m; i += global_threads()) out.pw[i] += P.mu * P.X.w[i];
         if (!grid_sync(&P.ctl->err)) break;
         phase_polish_z(P, out);

@@ -209,6 +209,7 @@ struct Problem {
     double *pdM = nullptr, *pdX = nullptr;   // polish's factored A_B A_B' when the handle has no scratch
     int *bcol = nullptr, *bsptr = nullptr, *bslen = nullptr, *bcnt = nullptr;   // A_B of the polish (lazy)
     double* bval = nullptr;
+    float* bval32 = nullptr;                  // A_B's FP32 values (FP32 polish corrections)
     long long padded_B = 0;
     double* psaveO = nullptr;                 // the scaling O and the multiplier w kept across a
     double* psaveW = nullptr;                 //   polish of a polished solve
@@ -245,7 +246,7 @@ int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const do
                 const std::vector<int>& perm, int gA, int gAT, DeviceSell& out);
 // The crossover polish's A_B (rows of A on the support x > z of the current
 // iterate) on the device; sets X.O to the support's indicator.
-int support_rows(Problem* P, SellMat& out);
+int support_rows(Problem* P, SellMat& out, bool with_f32);
 // LP crossover polish of the current iterate into px, pw, pz; pres[0..5] its
 // residuals, pres[8..12] {|B|, CG iterations x, y, 1 = completed, 1 =
 // factored}.  rel: the solves stop at rel times their first residual (or at

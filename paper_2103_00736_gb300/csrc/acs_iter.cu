@@ -143,11 +143,13 @@ __global__ void __launch_bounds__(kThreads, 1) iter_kernel(const __grid_constant
 
 // LP crossover polish of the current iterate (FP64; see polish_loop).
 __global__ void __launch_bounds__(kThreads, 1) polish_kernel(const __grid_constant__ IterParams<double> P,
+                                                             const __grid_constant__ IterParams<float> P32,
                                                              const __grid_constant__ IterParams<double> Q,
-                                                             const PolishOut out, int rounds, double rel) {
+                                                             const PolishOut out, int rounds, double rel,
+                                                             int fp32) {
     team_set(blockIdx.x, gridDim.x, &P.ctl->bar_count64, P.partials, P.dM, P.dX);
     sync_init(P.ctl->bar_gen);
-    polish_loop(P, Q, out, rounds, rel);
+    polish_loop(P, P32, Q, out, rounds, rel, fp32 != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,21 +389,31 @@ int launch_polish(Problem* P, int rounds, double rel) {
     Q.dM = dM;
     Q.dX = dX;
     IterParams<double> Qk = Q;            // the residuals of the polished point: all of A
+    // the corrections by FP32 CG (refined by FP64 rounds) when the target
+    // leaves room for it, on the problem's FP32 values
+    int fp32 = !dM && rel > 1e-10 && P->A.v32 && P->AT.v32 ? 1 : 0;
+    IterParams<float> Q32 = make_params<float>(P, 0.0, 1, P->V32);
+    Q32.dense = 0;
+    Q32.X.w = P->pwork;
+    Q32.Acb.nblocks = Q32.ATcb.nblocks = 0;
+    Q32.outer32 = 0;
     if (!dM) {
         // CG corrections: the passes over the rows of A run on A_B, the rows of
         // A restricted to the support's columns (the other columns carry
         // O_j = 0); those over A' skip the rows off the support
         SellMat AB;
-        const int rc = support_rows(P, AB);
+        const int rc = support_rows(P, AB, fp32 != 0);
         if (rc != ACS_SOLVED) return rc;
         Q.A = AB;
         Q.full_rows = 0;
+        Q32.A = AB;
+        Q32.full_rows = 0;
     }
     Qk.x = P->px;
     Qk.z = P->pz;
     Qk.X.w = P->pw;
     PolishOut out{P->px, P->pw, P->pz, P->pres, P->pres + 8};
-    void* args[] = {(void*)&Q, (void*)&Qk, (void*)&out, (void*)&rounds, (void*)&rel};
+    void* args[] = {(void*)&Q, (void*)&Q32, (void*)&Qk, (void*)&out, (void*)&rounds, (void*)&rel, (void*)&fp32};
     if (cudaLaunchCooperativeKernel((const void*)polish_kernel, dim3(P->grid64), dim3(kThreads), args, 0, st) !=
         cudaSuccess)
         return ACS_ERR_CUDA;
