@@ -1161,9 +1161,12 @@ __device__ __noinline__ void phase_cg_vec(const IterParams<T>& P, double alpha, 
 // q = O (A' w) over the rows of A' (FP64); with update: s <- (s + p)/2 -
 // mu c_hat + q (steps 18-19) and, if want_xz, x = O (p + s)/2 and
 // z = (p - s)/(2 mu O) (steps 20-21).  Partials ||s_new - s||^2, ||s_new||^2.
+// fuse_abs (orthant-only problems, no extrapolation, no rescaling next):
+// also step 17 of the next iteration, p = |s_new| and g = O (p + q) with the
+// q just formed -- the values phase_abs would compute there.
 template <typename T>
 __device__ __forceinline__ void update_epi(const IterParams<T>& P, int j, double sum, bool update, bool want_xz,
-                                           double& ds2, double& ss2) {
+                                           double& ds2, double& ss2, bool fuse_abs = false) {
     const double Oj = P.X.O[j];
     const double qj = Oj * sum;
     P.X.q[j] = qj;
@@ -1204,6 +1207,11 @@ __device__ __forceinline__ void update_epi(const IterParams<T>& P, int j, double
             P.x[j] = Oj * (pj + sj) * 0.5;
             P.z[j] = (pj - sj) / (2.0 * P.mu * Oj);
         }
+        if (fuse_abs) {
+            const double pn = fabs(sj);
+            P.X.p[j] = pn;
+            P.X.g[j] = Oj * (pn + qj);
+        }
     }
 }
 
@@ -1219,11 +1227,11 @@ __device__ __forceinline__ void update_partials(double ds2, double ss2, bool upd
 }
 
 template <typename T>
-__device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, bool want_xz) {
+__device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, bool want_xz, bool fuse_abs = false) {
     double ds2 = 0.0, ss2 = 0.0;
     const double* w = P.X.w;
     auto gather = [w](int i) { return w[i]; };
-    auto epi = [&](int j, double sum) { update_epi(P, j, sum, update, want_xz, ds2, ss2); };
+    auto epi = [&](int j, double sum) { update_epi(P, j, sum, update, want_xz, ds2, ss2, fuse_abs); };
     sell_rows<double>(P.AT, gather, epi);
     update_partials(ds2, ss2, update, P.partials);
 }
@@ -1236,9 +1244,10 @@ __device__ __noinline__ void phase_update_cb(const IterParams<T>& P) {
 }
 // ... and the update from its partial sums.
 template <typename T>
-__device__ __noinline__ void phase_update_comb(const IterParams<T>& P, bool want_xz) {
+__device__ __noinline__ void phase_update_comb(const IterParams<T>& P, bool want_xz, bool fuse_abs = false) {
     double ds2 = 0.0, ss2 = 0.0;
-    cb_combine(P.ATcb, &P.ctl->err, [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2); });
+    cb_combine(P.ATcb, &P.ctl->err,
+               [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2, fuse_abs); });
     update_partials(ds2, ss2, true, P.partials);
 }
 
@@ -2032,6 +2041,7 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     long long win_cg = __ldcg(&ctl->win_cg);
     int win_it = __ldcg(&ctl->win_it);
     long long ndense = 0, nfactor = 0;
+    bool abs_fused = false;                             // p, g of the next iteration already formed
 
 // grid barrier that ends phase `ph`; leaves the enclosing loop on error
 #define ACS_SYNC(ph)                                                      \
@@ -2124,9 +2134,13 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
         }
 
         // extrapolated start, valid once the previous iteration ran in the
-        // same scaling (not on an iteration that rescales)
-        phase_abs(P, (extrap_ok && !cond) ? P.extrap : 0.0);   // step 17
-        ACS_SYNC(PH_ABS);
+        // same scaling (not on an iteration that rescales); skipped when the
+        // previous update already formed p and g (and nothing changed O or g since)
+        if (!(abs_fused && !cond && !refresh)) {
+            phase_abs(P, (extrap_ok && !cond) ? P.extrap : 0.0);   // step 17
+            ACS_SYNC(PH_ABS);
+        }
+        abs_fused = false;
         extrap_ok = true;
         // Projection solve: `refine` rounds of (FP64 residual, correction CG in
         // precision T); a round after the first refreshes q = A_hat' w first.
@@ -2233,17 +2247,21 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
 
         const bool check = (lnext % P.check_every == 0) || (lnext == P.max_iter);
         const bool want_xz = check || in_schedule(P, lnext + 1);
+        // step 17 of the next iteration in this pass's epilogue (orthant-only,
+        // no extrapolation, no rescaling at the next iteration)
+        const bool fuse_abs = P.n_soc == 0 && !P.admm && P.extrap == 0.0 && !in_schedule(P, lnext + 1);
         if (outer32) {                                          // steps 18-21, FP32 product
             phase_update_cb(P);
             ++nAT32;
             ACS_SYNC(PH_UPDATE);
-            phase_update_comb(P, want_xz);
+            phase_update_comb(P, want_xz, fuse_abs);
             ACS_SYNC(PH_UPD_COMB);
         } else {
-            phase_update(P, true, want_xz);                     // steps 18-21
+            phase_update(P, true, want_xz, fuse_abs);          // steps 18-21
             ++nAT64;
             ACS_SYNC(PH_UPDATE);
         }
+        abs_fused = fuse_abs;
         {
             double d2[3];
             const int op[3] = {0, 0, 1};
