@@ -280,7 +280,18 @@ int acs_set_state(acs_problem* p, const double* s_dr, const double* O, const dou
  */
 int acs_polish(acs_problem* p, int32_t rounds, double* info);
 
-/* Release every device buffer of the handle.  NULL is ignored. */
+/* Device memory of the single-problem API comes from a per-device cache:
+ * the buffers of a destroyed handle (and the scratch of a create) are kept,
+ * up to ACS_DEVICE_CACHE_MB megabytes (environment, default 4096), and reused
+ * by later handles for requests of 80-100 % of a kept block's size, so that
+ * repeated create/destroy cycles do not pay cudaMalloc/cudaFree.
+ * acs_device_cache_trim returns the kept blocks of a device (-1: all) to the
+ * driver; acs_device_cache_stats: out3 = {bytes kept, allocations served
+ * from the cache, allocations that went to cudaMalloc} of a device. */
+int acs_device_cache_trim(int32_t device);
+int acs_device_cache_stats(int32_t device, int64_t* out3);
+
+/* Release every device buffer of the handle (to the cache above).  NULL is ignored. */
 void acs_problem_destroy(acs_problem* p);
 
 /* Static string for a status code. */

@@ -104,6 +104,8 @@ def lib():
         L.acs_polish.argtypes = [P, C.c_int32, dp]
         L.acs_last_polish_ms.argtypes = [P, dp]
         L.acs_debug_images.argtypes = [P, C.c_int32, ip, ip, ip, ip, dp, C.POINTER(C.c_float)]
+        L.acs_device_cache_trim.argtypes = [C.c_int32]
+        L.acs_device_cache_stats.argtypes = [C.c_int32, C.POINTER(C.c_int64)]
         L.acs_problem_destroy.argtypes = [P]
         L.acs_problem_destroy.restype = None
         L.acs_status_string.argtypes = [C.c_int]
@@ -823,6 +825,21 @@ def acs_debug_sell(m, n, row_ptr, col, val, which: int, warps: int) -> dict:
         raise AcsError(rc, "acs_debug_sell")
     return dict(rows=rows, slices=slices, g=g, stored=stored, perm=perm, sptr=sptr, slen=slen[:slices],
                 col=oc[:stored], val=ov[:stored])
+
+
+def acs_device_cache_trim(device: int = -1) -> None:
+    """Return the device-memory cache's kept blocks to the driver."""
+    rc = lib().acs_device_cache_trim(int(device))
+    if rc != 0:
+        raise AcsError(rc, "acs_device_cache_trim")
+
+
+def acs_device_cache_stats(device: int = 0) -> dict:
+    out = np.zeros(3, dtype=np.int64)
+    rc = lib().acs_device_cache_stats(int(device), _ptr(out, C.c_int64))
+    if rc != 0:
+        raise AcsError(rc, "acs_device_cache_stats")
+    return {"bytes": int(out[0]), "hits": int(out[1]), "misses": int(out[2])}
 
 
 def acs_debug_images(h, which: int) -> dict:

@@ -27,16 +27,7 @@ constexpr const char* kVersion = "acs-gb300 0.1 (sm_103a)";
 
 template <typename T>
 int dalloc(Problem* P, T** ptr, size_t count) {
-    *ptr = nullptr;
-    if (count == 0) count = 1;
-    void* p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return ACS_ERR_OOM;
-    }
-    P->allocations.push_back(p);
-    *ptr = static_cast<T*>(p);
-    return ACS_SOLVED;
+    return P->alloc(ptr, count) ? ACS_SOLVED : ACS_ERR_OOM;
 }
 
 template <typename T>
@@ -179,7 +170,8 @@ int alloc_outer(Problem* P, acs::Outer& X) {
 
 void free_all(Problem* P) {
     if (!P) return;
-    for (void* p : P->allocations) cudaFree(p);
+    if (P->stream) cudaStreamSynchronize(P->stream);    // the blocks go back to the cache idle
+    for (auto& a : P->allocations) acs::dev_release(P->device, a.first, a.second);
     P->allocations.clear();
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
     P->ctl_host = nullptr;

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "acs_host.cuh"
@@ -133,21 +134,24 @@ __global__ void sort_long(const int* __restrict__ cols, const long long* __restr
     }
 }
 
-// scratch released on every return
+// scratch from the device cache, released on every return (after the
+// stream that used it has been synchronised, or when nothing was launched)
 struct Scratch {
-    std::vector<void*> p;
+    int device;
+    cudaStream_t stream;
+    std::vector<std::pair<void*, size_t>> p;
+    Scratch(int d, cudaStream_t s) : device(d), stream(s) {}
     template <typename T>
     T* get(size_t count) {
-        void* q = nullptr;
-        if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        p.push_back(q);
+        size_t got = 0;
+        void* q = dev_alloc(device, std::max<size_t>(count, 1) * sizeof(T), &got);
+        if (!q) return nullptr;
+        p.emplace_back(q, got);
         return static_cast<T*>(q);
     }
     ~Scratch() {
-        for (void* q : p) cudaFree(q);
+        cudaStreamSynchronize(stream);               // nothing in flight still uses the blocks
+        for (auto& a : p) dev_release(device, a.first, a.second);
     }
 };
 
@@ -221,34 +225,15 @@ int support_rows(Problem* P, SellMat& out, bool with_f32) {
     const SellMat& A = P->A;
     cudaStream_t st = P->stream;
     if (!P->bcol) {
-        void* a[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t sz[5] = {sizeof(int) * (size_t)std::max<long long>(P->padded_A, 1),
-                              sizeof(double) * (size_t)std::max<long long>(P->padded_A, 1),
-                              sizeof(int) * (size_t)(A.nslices + 1), sizeof(int) * (size_t)std::max(A.nslices, 1),
-                              sizeof(int) * (size_t)m};
-        for (int k = 0; k < 5; ++k) {
-            if (cudaMalloc(&a[k], sz[k]) != cudaSuccess) {
-                cudaGetLastError();
-                for (int q = 0; q < k; ++q) cudaFree(a[q]);
-                return ACS_ERR_OOM;
-            }
-        }
-        for (int k = 0; k < 5; ++k) P->allocations.push_back(a[k]);
-        P->bcol = (int*)a[0];
-        P->bval = (double*)a[1];
-        P->bsptr = (int*)a[2];
-        P->bslen = (int*)a[3];
-        P->bcnt = (int*)a[4];
-    }
-    if (with_f32 && !P->bval32) {
-        void* q = nullptr;
-        if (cudaMalloc(&q, sizeof(float) * (size_t)std::max<long long>(P->padded_A, 1)) != cudaSuccess) {
-            cudaGetLastError();
+        const size_t pa = (size_t)std::max<long long>(P->padded_A, 1);
+        if (!P->alloc(&P->bcol, pa) || !P->alloc(&P->bval, pa) || !P->alloc(&P->bsptr, (size_t)A.nslices + 1) ||
+            !P->alloc(&P->bslen, (size_t)std::max(A.nslices, 1)) || !P->alloc(&P->bcnt, (size_t)m)) {
+            P->bcol = nullptr;
             return ACS_ERR_OOM;
         }
-        P->allocations.push_back(q);
-        P->bval32 = (float*)q;
     }
+    if (with_f32 && !P->bval32 && !P->alloc(&P->bval32, (size_t)std::max<long long>(P->padded_A, 1)))
+        return ACS_ERR_OOM;
     support_indicator<<<grid_for(n, 256), 256, 0, st>>>(n, P->x, P->z, P->X.O);
     count_support_entries<<<grid_for(32LL * A.nslices, 256), 256, 0, st>>>(A, P->X.O, P->bcnt);
     std::vector<int> cnt(m);
@@ -290,7 +275,7 @@ int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const do
     const int m = P->m, n = P->n;
     const long long nnz = row_ptr[m];
     cudaStream_t st = P->stream;
-    Scratch S;
+    Scratch S(P->device, st);
     // A: relabelled rows
     std::vector<long long> begA(m);
     std::vector<int> lenA(m);
@@ -339,14 +324,9 @@ int device_sell(Problem* P, const int64_t* row_ptr, const int32_t* col, const do
     // the images themselves belong to the problem
     int *colA = nullptr, *colT = nullptr;
     double *valA = nullptr, *valT = nullptr;
-    if (cudaMalloc(&colA, sizeof(int) * std::max<long long>(totA, 1)) != cudaSuccess) return ACS_ERR_OOM;
-    P->allocations.push_back(colA);
-    if (cudaMalloc(&valA, sizeof(double) * std::max<long long>(totA, 1)) != cudaSuccess) return ACS_ERR_OOM;
-    P->allocations.push_back(valA);
-    if (cudaMalloc(&colT, sizeof(int) * std::max<long long>(totT, 1)) != cudaSuccess) return ACS_ERR_OOM;
-    P->allocations.push_back(colT);
-    if (cudaMalloc(&valT, sizeof(double) * std::max<long long>(totT, 1)) != cudaSuccess) return ACS_ERR_OOM;
-    P->allocations.push_back(valT);
+    if (!P->alloc(&colA, (size_t)std::max<long long>(totA, 1)) || !P->alloc(&valA, (size_t)std::max<long long>(totA, 1)) ||
+        !P->alloc(&colT, (size_t)std::max<long long>(totT, 1)) || !P->alloc(&valT, (size_t)std::max<long long>(totT, 1)))
+        return ACS_ERR_OOM;
     if (cudaMemcpyAsync(d_rpT, rpT.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_long, longc.data(), sizeof(int) * longc.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||

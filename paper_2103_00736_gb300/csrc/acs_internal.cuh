@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <utility>
 #include <vector>
 
 #include "../../include/acs.h"
@@ -172,6 +173,11 @@ struct PolishStats {
     long long support = 0, support_entries = 0;   // |B| and stored entries of A_B of the last polish
 };
 
+// Device memory of the single-problem API through a per-device cache of
+// released blocks (acs_alloc.cu): *got receives the block's size.
+void* dev_alloc(int device, size_t bytes, size_t* got);
+void dev_release(int device, void* p, size_t bytes);
+
 struct Problem {
     int m = 0, n = 0, nnz = 0, n_orth = 0, n_soc = 0;
     int device = 0;
@@ -221,7 +227,17 @@ struct Problem {
     double *dM = nullptr, *dX = nullptr; // its scratch, [m * m] each
     CbMat Acb{}, ATcb{};                 // column-blocked FP32 images (nblocks = 0: not built)
     int cb_smem = 0;                     // dynamic shared memory of the FP32 launch (bytes)
-    std::vector<void*> allocations;
+    std::vector<std::pair<void*, size_t>> allocations;   // device blocks owned (address, size)
+    // count elements of T from the device cache, owned by the problem
+    template <typename T>
+    bool alloc(T** out, size_t count) {
+        size_t got = 0;
+        void* q = dev_alloc(device, (count > 0 ? count : 1) * sizeof(T), &got);
+        *out = static_cast<T*>(q);
+        if (!q) return false;
+        allocations.emplace_back(q, got);
+        return true;
+    }
     cudaEvent_t ev_launch[2] = {nullptr, nullptr};   // bracket the last persistent launch
     cudaEvent_t ev_polish[2] = {nullptr, nullptr};   // bracket the last polish launch
     double seg_ms = 0.0;                     // a polished solve: its iteration launches' device time

@@ -346,34 +346,22 @@ int launch_polish(Problem* P, int rounds, double rel) {
     cudaStream_t st = P->stream;
     const int n = P->n, m = P->m;
     if (!P->px) {
-        void* a[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t sz[5] = {sizeof(double) * n, sizeof(double) * m, sizeof(double) * n, sizeof(double) * m,
-                              sizeof(double) * 16};
-        for (int k = 0; k < 5; ++k) {
-            if (cudaMalloc(&a[k], sz[k]) != cudaSuccess) {
-                for (int q = 0; q < k; ++q) cudaFree(a[q]);
-                return ACS_ERR_OOM;
-            }
+        // owned by the problem from here on (released with it, also if a later one fails)
+        if (!P->alloc(&P->px, n) || !P->alloc(&P->pw, m) || !P->alloc(&P->pz, n) || !P->alloc(&P->pwork, m) ||
+            !P->alloc(&P->pres, 16)) {
+            P->px = nullptr;
+            return ACS_ERR_OOM;
         }
-        for (int k = 0; k < 5; ++k) P->allocations.push_back(a[k]);
-        P->px = (double*)a[0];
-        P->pw = (double*)a[1];
-        P->pz = (double*)a[2];
-        P->pwork = (double*)a[3];
-        P->pres = (double*)a[4];
     }
     // the factored M = A_B A_B' (m <= kDenseLimit): the handle's cached-
     // operator scratch, else the polish's own
     double *dM = P->dM, *dX = P->dX;
     if (!dM && m <= (P->full_rows ? host::kDenseRowsLimit : host::kDenseLimit)) {
         if (!P->pdM) {
-            void *a = nullptr, *b = nullptr;
-            if (cudaMalloc(&a, sizeof(double) * (size_t)m * m) != cudaSuccess) return ACS_ERR_OOM;
-            if (cudaMalloc(&b, sizeof(double) * (size_t)m * m) != cudaSuccess) { cudaFree(a); return ACS_ERR_OOM; }
-            P->allocations.push_back(a);
-            P->allocations.push_back(b);
-            P->pdM = (double*)a;
-            P->pdX = (double*)b;
+            if (!P->alloc(&P->pdM, (size_t)m * m) || !P->alloc(&P->pdX, (size_t)m * m)) {
+                P->pdM = P->pdX = nullptr;
+                return ACS_ERR_OOM;
+            }
         }
         dM = P->pdM;
         dX = P->pdX;

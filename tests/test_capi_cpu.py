@@ -356,3 +356,14 @@ def test_bf16_storage_rounds_to_nearest_even(capi):
     ties = (np.array([0x3F808000, 0x3F818000, 0xBF808000, 0xC0418000], np.uint32)).view(np.float32)
     got = capi.acs_debug_to_bf16(ties.astype(np.float64))
     assert list(got) == [0x3F80, 0x3F82, 0xBF80, 0xC042]
+
+
+def test_device_cache_api_on_the_host(capi):
+    """The cache's bookkeeping needs no GPU: nothing kept, trim is a no-op,
+    a negative device is an argument error for the statistics."""
+    st = capi.acs_device_cache_stats(0)
+    assert st["bytes"] == 0
+    capi.acs_device_cache_trim(-1)
+    with pytest.raises(capi.AcsError) as e:
+        capi.acs_device_cache_stats(-1)
+    assert e.value.code == capi.ERR_ARG

@@ -56,3 +56,24 @@ def test_device_images_equal_the_host_builder(name):
             np.testing.assert_array_equal(dev["col"], host["col"])
             np.testing.assert_array_equal(dev["val"], host["val"])
             np.testing.assert_array_equal(dev["v32"], host["val"].astype(np.float32))
+
+
+def test_device_cache_reuses_the_blocks_of_a_destroyed_handle():
+    """Create/solve/destroy twice: the second create's buffers come from the
+    cache, its result equals the first; trim returns the blocks."""
+    capi.acs_device_cache_trim(-1)
+    inst = I.large_lp(scale=0.02)
+    out = []
+    for k in range(2):
+        before = capi.acs_device_cache_stats(0)
+        with capi.Solver(inst) as s:
+            st = s.solve(tol=1e-6, max_iter=20000)
+            _, x, y, z, iters, res = s.get()
+        after = capi.acs_device_cache_stats(0)
+        out.append((st, x, iters, after["hits"] - before["hits"], after["misses"] - before["misses"]))
+    assert out[0][0] == capi.SOLVED and out[1][0] == capi.SOLVED and out[0][2] == out[1][2]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[1][3] > 0 and out[1][4] < out[0][4], out
+    assert capi.acs_device_cache_stats(0)["bytes"] > 0
+    capi.acs_device_cache_trim(-1)
+    assert capi.acs_device_cache_stats(0)["bytes"] == 0
