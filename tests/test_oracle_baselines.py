@@ -145,3 +145,22 @@ def test_section_iii_a_comparison():
         for other in ("none", "sk", "ruiz"):
             assert it[other] is not None and it[other] >= 5 * it["ac"], (alg_name, it)
         assert it["sk"] >= it["none"], (alg_name, it)
+
+
+def test_admm_iterates_leave_the_rescaling_rule_nothing_to_work_with():
+    """ADMM's x = proj_K(a) and z = proj_K(-a)/mu are exactly complementary,
+    so step 8's ratio o is 0, inf or nan on every coordinate: the reason the
+    ADMM form runs without rescaling."""
+    rng = np.random.default_rng(5)
+    n_orth, dims = 6, [3, 4]
+    a = rng.standard_normal(n_orth + sum(dims))
+    mu = 0.7
+    x = C.proj_K(a, n_orth, dims)
+    z = C.proj_K(-a, n_orth, dims) / mu
+    o = alg.conditioning_vector(x, z, n_orth, dims)
+    assert all((v == 0.0) or np.isinf(v) or np.isnan(v) for v in o), o
+    # while DR's pair (x, z) = ((p + s)/2, (p - s)/(2 mu)) from two different s is not
+    s_old, s_new = a, rng.standard_normal(a.size)
+    p = C.abs_K(s_old, n_orth, dims)
+    od = alg.conditioning_vector((p + s_new) / 2, (p - s_new) / (2 * mu), n_orth, dims)
+    assert np.isfinite(od).any() and (od[np.isfinite(od)] > 0).any()
