@@ -123,12 +123,14 @@ def survey_bytes(m: int, n: int, nnz: int, iters: int, cg_iters: int, checks: in
             + checks * 24.0 * nnz + conds * 8.0 * nnz)
 
 
-def algorithmic_bytes(m: int, n: int, nnz: int, counters, iters: int) -> float:
+def algorithmic_bytes(m: int, n: int, nnz: int, counters, iters: int, n32_A: int = 0, n32_AT: int = 0) -> float:
     """This implementation's own byte model: every pass it actually runs
     (pass counters of the solve), with its FP64 outer passes at 12 bytes a
-    nonzero."""
+    nonzero and FP32 outer passes (n32_A, n32_AT) at 8."""
     n_cg_A, n_cg_AT, n64_A, n64_AT, n_cond, n_chk = [int(v) for v in counters]
     b = 0.0
+    b += n32_A * (8.0 * nnz + 8 * n + 20 * m)            # FP32 outer passes over A (rhs)
+    b += n32_AT * (8.0 * nnz + 8 * m + 48 * n)           # FP32 outer passes over A' (update)
     b += n_cg_AT * (8.0 * nnz + 4 * m + 8 * n)          # t = O^2 A'u: val+col, u gathered, O2 in, t out
     b += n_cg_A * (8.0 * nnz + 4 * n + 8 * m)           # au = A t: val+col, t gathered, au out, u in
     b += n_cg_A * 52.0 * m                               # CG vector step (p, sv, r r/w; au, jinv in; u out; w FP64 r/w)
@@ -611,7 +613,8 @@ def gpu_arm(args) -> None:
     # besides four small initialisation launches; its FP64 continuation
     # launch returns at once unless the FP32 loop handed over): the scope
     # table's byte formula, and beside it the implementation's own model
-    own_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters)
+    own_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters, passes.get("fp32_outer_A", 0),
+                                  passes.get("fp32_outer_At", 0))
     alg_bytes = survey_bytes(inst.m, inst.n, inst.nnz, iters, int(res[6]), int(counters[5]), int(counters[4]))
     # every stored entry of every matrix pass costs one random gather from an
     # L2-resident vector: the rate that actually bounds these passes

@@ -272,7 +272,12 @@ int solve_polished(Problem* P, double tol, int max_iter) {
     int st = ACS_ERR_CUDA;
     for (;;) {
         const double target = fmax(tol, level);
+        // a segment that ends at a polish level runs its outer products in
+        // FP32 (the polish, not the iteration, sets the final accuracy); the
+        // last segment, to tol itself, in FP64
+        P->outer_f32 = target > tol;
         int rc = acs::launch_solve(P, target, max_iter);
+        P->outer_f32 = false;
         if (rc != ACS_SOLVED) return rc;
         if (cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(acs::Control), cudaMemcpyDeviceToHost, P->stream) !=
                 cudaSuccess ||

@@ -1061,6 +1061,21 @@ __device__ __noinline__ void phase_rhs(const IterParams<T>& P) {
     block_partials<1>(v, op, P.partials);
 }
 
+// FP32 outer products on the L2-gather layout (a segment that need only reach
+// a polish level): the projection residual from FP32 values and g rounded to
+// FP32, summed in FP32.
+template <typename T>
+__device__ __noinline__ void phase_rhs_f32(const IterParams<T>& P) {
+    double gam = 0.0;
+    const double* g = P.X.g;
+    auto gather = [g](int j) { return (float)g[j]; };
+    auto epi = [&](int i, float sum) { rhs_epi(P, i, (double)sum, gam); };
+    sell_rows<float>(P.A, gather, epi);
+    const double v[1] = {gam};
+    const int op[1] = {0};
+    block_partials<1>(v, op, P.partials);
+}
+
 // FP32 outer passes: the product A g of the projection residual as a
 // column-blocked FP32 pass (g rounded to FP32 as it is staged) ...
 template <typename T>
@@ -1234,6 +1249,17 @@ __device__ __noinline__ void phase_update(const IterParams<T>& P, bool update, b
     auto epi = [&](int j, double sum) { update_epi(P, j, sum, update, want_xz, ds2, ss2, fuse_abs); };
     sell_rows<double>(P.AT, gather, epi);
     update_partials(ds2, ss2, update, P.partials);
+}
+
+// The update from an FP32 product A'w on the L2-gather layout (see phase_rhs_f32).
+template <typename T>
+__device__ __noinline__ void phase_update_f32(const IterParams<T>& P, bool want_xz, bool fuse_abs) {
+    double ds2 = 0.0, ss2 = 0.0;
+    const double* w = P.X.w;
+    auto gather = [w](int i) { return (float)w[i]; };
+    auto epi = [&](int j, float sum) { update_epi(P, j, (double)sum, true, want_xz, ds2, ss2, fuse_abs); };
+    sell_rows<float>(P.AT, gather, epi);
+    update_partials(ds2, ss2, true, P.partials);
 }
 
 // FP32 outer passes: A'w as a column-blocked FP32 pass (w rounded to FP32 as
@@ -2042,6 +2068,9 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
     int win_it = __ldcg(&ctl->win_it);
     long long ndense = 0, nfactor = 0;
     bool abs_fused = false;                             // p, g of the next iteration already formed
+    // FP32 outer products on the L2-gather layout (FP32 loop, a segment that
+    // ends at a polish level)
+    const bool outer32_l2 = sizeof(T) == 4 && P.outer32_l2 != 0 && !cbcg && P.A.v32 && P.AT.v32;
 
 // grid barrier that ends phase `ph`; leaves the enclosing loop on error
 #define ACS_SYNC(ph)                                                      \
@@ -2168,6 +2197,10 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
                 ACS_SYNC(PH_RHS);
                 phase_rhs_comb(P);
                 ACS_SYNC(PH_RHS_COMB);
+            } else if (outer32_l2) {
+                phase_rhs_f32(P);                               // r0 from an FP32 product
+                ++nA32;
+                ACS_SYNC(PH_RHS);
             } else {
                 phase_rhs(P);                                   // r0 in FP64
                 ++nA64;
@@ -2256,6 +2289,10 @@ __device__ __noinline__ int solve_loop(const IterParams<T>& P, int status0) {
             ACS_SYNC(PH_UPDATE);
             phase_update_comb(P, want_xz, fuse_abs);
             ACS_SYNC(PH_UPD_COMB);
+        } else if (outer32_l2) {
+            phase_update_f32(P, want_xz, fuse_abs);             // steps 18-21, FP32 product
+            ++nAT32;
+            ACS_SYNC(PH_UPDATE);
         } else {
             phase_update(P, true, want_xz, fuse_abs);          // steps 18-21
             ++nAT64;

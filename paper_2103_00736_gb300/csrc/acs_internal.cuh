@@ -163,6 +163,8 @@ struct IterParams {
     int outer32;                                      // FP32 outer passes (rhs, update) until the
     double outer32_tol;                               //   KKT residuals reach outer32_tol
     int admm;                                         // ADMM form of the splitting (Section III-B)
+    int outer32_l2;                                   // FP32 outer products on the L2-gather layout
+                                                      // (FP32 loop of a segment ending at a polish level)
     int full_rows;                                    // every row of A holds every column (dense
                                                       // workloads): the cached operator's M is
                                                       // assembled by a tiled product
@@ -244,6 +246,7 @@ struct Problem {
     double polish_ms = 0.0;                  // ... and its polish launches' (or the last acs_polish's)
     bool polished_solve = false;             // the last acs_solve ran with polish_tol
     bool full_rows = false;                  // nnz = m n: every row holds every column
+    bool outer_f32 = false;                  // the next launch's FP32 loop uses FP32 outer products
 };
 
 // launches (acs_iter.cu)

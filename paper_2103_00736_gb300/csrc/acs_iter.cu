@@ -249,6 +249,7 @@ static IterParams<T> make_params(Problem* P, double tol, int max_iter, const Inn
         Q.ATcb = P->ATcb;
         Q.outer32 = P->set.precision == ACS_PREC_FP32 && P->Acb.nblocks > 0 ? 1 : 0;
         Q.outer32_tol = P->set.outer32_tol;
+        Q.outer32_l2 = P->outer_f32 ? 1 : 0;
     }
     return Q;
 }
