@@ -619,7 +619,9 @@ def gpu_arm(args) -> None:
     # every stored entry of every matrix pass costs one random gather from an
     # L2-resident vector: the rate that actually bounds these passes
     n_cg_A, n_cg_AT, n64_A, n64_AT = (int(v) for v in counters[:4])
-    gathers = float(n_cg_A + n64_A) * info["padded_A"] + float(n_cg_AT + n64_AT) * info["padded_AT"]
+    n32_A, n32_AT = passes.get("fp32_outer_A", 0), passes.get("fp32_outer_At", 0)
+    gathers = (float(n_cg_A + n64_A + n32_A) * info["padded_A"]
+               + float(n_cg_AT + n64_AT + n32_AT) * info["padded_AT"])
     traffic = args.traffic
     # the device's random-gather rate, measured now (4 MB vector, L2-resident)
     gather_probe = capi.acs_bench_gather(1 << 20, 0, device=local)
