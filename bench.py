@@ -468,17 +468,18 @@ def polish_tol(args) -> float:
 
 
 def polish_bytes(m: int, n: int, nnz: int, corrections: int, attempts: int, support: int = 0,
-                 support_entries: int = 0) -> float:
+                 support_entries: int = 0, cg_entry_bytes: float = 12.0) -> float:
     """Algorithmic bytes of the crossover polishes of one solve.  Their CG
     passes read only the support's part of the matrix (A_B, and the rows of A'
-    on B): per CG iteration 2 x 12 bytes per entry of A_B, the support's
-    vectors and the m-vectors of the vector step; per polish about 10 passes
-    on the support (support, Jacobi, the rounds' residuals and q refreshes)
-    and 4 over all of A (z_y, z, KKT), FP64.  Without the support figures
+    on B): per CG iteration 2 x cg_entry_bytes per entry of A_B (12 with FP64
+    corrections, 8 with the FP32 ones of a polished solve), the support's
+    vectors and the m-vectors of the vector step; per polish about 10 FP64
+    passes on the support (support, Jacobi, the rounds' residuals and q
+    refreshes) and 4 over all of A (z_y, z, KKT).  Without the support figures
     (support_entries = 0: the factored path) every pass counts all of A."""
     nb = support_entries if support_entries > 0 else nnz
     nB = support if support_entries > 0 else n
-    per_cg = 2 * (12.0 * nb) + 16.0 * (m + nB) + 56.0 * m
+    per_cg = 2 * (cg_entry_bytes * nb) + 16.0 * (m + nB) + 56.0 * m
     per_support_pass = 12.0 * nb + 16.0 * (m + nB)
     per_full_pass = 12.0 * nnz + 16.0 * (m + n)
     return corrections * per_cg + attempts * (10 * per_support_pass + 4 * per_full_pass)
@@ -737,11 +738,14 @@ def gpu_arm(args) -> None:
                                                                          passes["polish_corrections"],
                                                                          passes["polish_attempts"],
                                                                          passes["polish_support"],
-                                                                         passes["polish_support_entries"]),
+                                                                         passes["polish_support_entries"],
+                                                                         8.0 if passes["polish_support_entries"]
+                                                                         else 12.0),
                                            polish_ms, None,
-                                           bytes_formula="per CG iteration 24 nnz_B + 16 (m+|B|) + 56 m, per "
-                                                         "polish 10 x (12 nnz_B + 16 (m+|B|)) + 4 x (12 nnz + "
-                                                         "16 (m+n)); nnz_B = stored entries of A_B")
+                                           bytes_formula="per CG iteration 16 nnz_B (FP32 corrections) + "
+                                                         "16 (m+|B|) + 56 m, per polish 10 x (12 nnz_B + 16 "
+                                                         "(m+|B|)) + 4 x (12 nnz + 16 (m+n)); nnz_B = stored "
+                                                         "entries of A_B")
                 if polish_ms > 0 else None}
             line["no_polish"] = plain
         if subs:
