@@ -113,9 +113,9 @@ def make_instance(name: str, dense_n: int | None = None, cone_h: int = 10, lp_sc
 # algorithmic bytes
 # ---------------------------------------------------------------------------
 
-def survey_bytes(m: int, n: int, nnz: int, iters: int, cg_iters: int, checks: int, conds: int) -> float:
-    """The hot path's algorithmic bytes of one solve by the fixed formula of
-    the scope table (FP32 values and int32 indices of A and A' stored, each
+def path_bytes(m: int, n: int, nnz: int, iters: int, cg_iters: int, checks: int, conds: int) -> float:
+    """The hot path's algorithmic bytes of one solve by a fixed formula
+    (FP32 values and int32 indices of A and A' stored, each
     read once per pass): per outer iteration 16 nnz + 20 n + 12 m (the A and
     A' passes, abs_K, the update), per CG iteration 16 nnz + 8 n + 20 m, per
     KKT check 24 nnz (the FP64 pair of passes), per rescaling 8 nnz."""
@@ -616,7 +616,7 @@ def gpu_arm(args) -> None:
     # table's byte formula, and beside it the implementation's own model
     own_bytes = algorithmic_bytes(inst.m, inst.n, inst.nnz, counters, iters, passes.get("fp32_outer_A", 0),
                                   passes.get("fp32_outer_At", 0))
-    alg_bytes = survey_bytes(inst.m, inst.n, inst.nnz, iters, int(res[6]), int(counters[5]), int(counters[4]))
+    alg_bytes = path_bytes(inst.m, inst.n, inst.nnz, iters, int(res[6]), int(counters[5]), int(counters[4]))
     # every stored entry of every matrix pass costs one random gather from an
     # L2-resident vector: the rate that actually bounds these passes
     n_cg_A, n_cg_AT, n64_A, n64_AT = (int(v) for v in counters[:4])
@@ -647,7 +647,7 @@ def gpu_arm(args) -> None:
         plain_ms = max_over_ranks(p0.elapsed_time(p1), pg, "cuda")
         pc = capi.acs_debug_counters(h)
         plaunch = capi.acs_last_launch_ms(h)
-        pbytes = survey_bytes(inst.m, inst.n, inst.nnz, piters, int(pres[6]), int(pc[5]), int(pc[4]))
+        pbytes = path_bytes(inst.m, inst.n, inst.nnz, piters, int(pres[6]), int(pc[5]), int(pc[4]))
         plain = {"what": "Algorithm 2 alone (no polish), same handle and instance",
                  "value": replica_throughput(world, args.steps, plain_ms / 1e3), "unit": UNIT,
                  "ms_per_step": plain_ms / args.steps, "iterations": piters, "cg_iterations": int(pres[6]),
@@ -708,7 +708,7 @@ def gpu_arm(args) -> None:
                                "(acs_bench_gather)"},
             "roofline": roofline_entry("iter_kernel<float>", alg_bytes, launch_ms, traffic, own_bytes=own_bytes,
                                        step_ms_median=statistics.median(step_ms),
-                                       bytes_formula="survey: iters*(16 nnz+20 n+12 m) + cg*(16 nnz+8 n+20 m)"
+                                       bytes_formula="path: iters*(16 nnz+20 n+12 m) + cg*(16 nnz+8 n+20 m)"
                                                      " + checks*24 nnz + rescalings*8 nnz"),
             "clocks": clk,
             "e2e": e2e,

@@ -22,9 +22,9 @@ ADMM is Douglas-Rachford with the two proximal steps swapped, on the
 variable zeta = x1 + z_prev/mu: zeta <- zeta + proj_K(2 prox_g(zeta) - zeta)
 - prox_g(zeta), with x2 = prox_g(zeta) (the textbook identity, used as a pin).
 
-Ruiz equilibration (the survey's stand-in for an equilibrating
-preconditioner that the paper does not print): row and column infinity norms
-of DAE driven to 1 by repeated square-root scalings.
+Ruiz equilibration (a standard equilibrating preconditioner that the code
+computes itself, beside the printed Sinkhorn-Knopp scalings): row and column
+infinity norms of DAE driven to 1 by repeated square-root scalings.
 
 Pinned by: DR's z reproduces Algorithm 1's s (Section III-B's splitting is
 the one Algorithm 1 runs), ADMM's x2 reproduces the swapped DR, both reach
