@@ -153,8 +153,9 @@ typedef struct {
                                 0 (default) = off.  With polish_tol > tol, acs_solve iterates
                                 until every KKT residual is <= polish_tol and polishes; if the
                                 polished point meets tol the solve ends there (ACS_SOLVED),
-                                else the iteration resumes from its state (the polish restores
-                                the scaling) and the polish is tried again at a ten times
+                                else the iteration resumes from its state (the scaling, the
+                                multiplier and x, z as they were: as if uninterrupted) and
+                                the polish is tried again at a ten times
                                 lower level, until the iteration itself reaches tol.  These
                                 polishes need only meet tol: their solves stop at 1e-3 tol /
                                 polish_tol of their first residual (acs_polish itself goes

@@ -269,6 +269,8 @@ int solve_polished(Problem* P, double tol, int max_iter) {
     const int n = P->n;
     if (!P->psaveO && dalloc(P, &P->psaveO, (size_t)n)) return ACS_ERR_OOM;
     if (!P->psaveW && dalloc(P, &P->psaveW, (size_t)P->m)) return ACS_ERR_OOM;
+    if (!P->psaveX && dalloc(P, &P->psaveX, (size_t)n)) return ACS_ERR_OOM;
+    if (!P->psaveZ && dalloc(P, &P->psaveZ, (size_t)n)) return ACS_ERR_OOM;
     int st = ACS_ERR_CUDA;
     for (;;) {
         const double target = fmax(tol, level);
@@ -296,7 +298,9 @@ int solve_polished(Problem* P, double tol, int max_iter) {
         if (cudaMemcpyAsync(P->psaveO, P->X.O, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(P->psaveW, P->X.w, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, P->stream) !=
-                cudaSuccess)
+                cudaSuccess ||
+            cudaMemcpyAsync(P->psaveX, P->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess ||
+            cudaMemcpyAsync(P->psaveZ, P->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
             return ACS_ERR_CUDA;
         // the polished point need only meet tol: its solves stop at 1e-3 tol /
         // polish_tol of their first residual (the iterate's, about polish_tol)
@@ -305,13 +309,16 @@ int solve_polished(Problem* P, double tol, int max_iter) {
         P->state_clobbered = true;                           // until the next segment starts
         if (rc < 0) return rc;
         if (rc == ACS_SOLVED && info[4] <= tol) break;       // polished to tol: st = ACS_SOLVED
-        // resume: the scaling and the multiplier back (a polished point that
-        // was better but not good enough replaced w), the iteration state as
-        // it was; x and z are rewritten before anything reads them again
+        // resume: the scaling, the multiplier and the iterate's x, z back (a
+        // polished point that was better but not good enough replaced w, x, z;
+        // a rescaling at the next iteration reads x and z), so that the
+        // iteration continues as if uninterrupted
         if (cudaMemcpyAsync(P->X.O, P->psaveO, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(P->X.w, P->psaveW, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, P->stream) !=
-                cudaSuccess)
+                cudaSuccess ||
+            cudaMemcpyAsync(P->x, P->psaveX, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess ||
+            cudaMemcpyAsync(P->z, P->psaveZ, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
             return ACS_ERR_CUDA;
         P->warm = true;
         P->warm_l = seg.l;

@@ -219,8 +219,9 @@ struct Problem {
     double* bval = nullptr;
     float* bval32 = nullptr;                  // A_B's FP32 values (FP32 polish corrections)
     long long padded_B = 0;
-    double* psaveO = nullptr;                 // the scaling O and the multiplier w kept across a
-    double* psaveW = nullptr;                 //   polish of a polished solve
+    double* psaveO = nullptr;                 // the scaling O, the multiplier w and the iterate's
+    double* psaveW = nullptr;                 //   x, z kept across a polish of a polished solve
+    double *psaveX = nullptr, *psaveZ = nullptr;
     PolishStats pol;                          // polish attempts of the last solve (or acs_polish calls)
     int warm_l = 0;
     double warm_ds = INFINITY, warm_snorm = 0.0, warm_eta = 0.3;
