@@ -125,3 +125,29 @@ def test_a_worse_polish_is_rejected():
     xk, yk, zk, ok, before, after = X.polish_if_better(A, b, c, x, y, z)
     assert not ok and kkt.max_residual(after) > kkt.max_residual(before)
     assert (xk == x).all() and (yk == y).all() and (zk == z).all()
+
+
+def test_empty_support_and_ties():
+    """B = {x > z} is strict: ties x_j = z_j stay out, and with B empty the
+    affine set {u = 0, A u = b} leaves x~ = 0, y~ = y (no constraint
+    A_B' v = c_B to meet) and z~ = c - A'y."""
+    rng = np.random.default_rng(9)
+    m, n = 3, 6
+    A = rng.standard_normal((m, n))
+    b, c, y = rng.standard_normal(m), rng.standard_normal(n), rng.standard_normal(m)
+    x = rng.uniform(0.0, 1.0, n)
+    assert not X.support(x, x).any()
+    xt, yt, zt, B = X.polish(A, b, c, x, y, x.copy())
+    assert not B.any()
+    assert (xt == 0.0).all()
+    np.testing.assert_array_equal(yt, y)
+    np.testing.assert_allclose(zt, c - A.T @ y, atol=1e-14)
+    # one tie broken the other way enters B alone: x~ is then b's least-squares
+    # multiple of that column
+    z = x.copy()
+    z[2] = x[2] - 0.1
+    xt, _, _, B = X.polish(A, b, c, x, y, z)
+    assert np.flatnonzero(B).tolist() == [2]
+    a = A[:, 2]
+    assert xt[2] == pytest.approx(a @ b / (a @ a), rel=1e-12)
+    assert (xt[np.arange(n) != 2] == 0.0).all()
