@@ -215,3 +215,29 @@ def test_polished_solve_resumes_the_iteration():
     assert kkt.max_residual(ours) <= 1e-9, ours
     assert st2 == capi.SOLVED and it2 == it3
     np.testing.assert_allclose(x2, x3, rtol=0, atol=1e-12)
+
+
+def test_empty_support():
+    """b = 0, c > 0: the optimum is x* = 0, and after 7 iterations x < z on
+    every column (in the oracle's iterate by at least 0.04), so the support B
+    is empty: both projections start on a zero residual, x~ = 0, y~ = y (no
+    constraint A_B' v = c_B to meet) and z~ = c - A'y, a point whose
+    residuals are at rounding level, so the polish is taken."""
+    rng = np.random.default_rng(31)
+    m, n = 20, 60
+    A = rng.standard_normal((m, n)) * (rng.uniform(size=(m, n)) < 0.3)
+    b, c = np.zeros(m), rng.uniform(0.5, 1.5, n)
+    inst = _dense_inst(A, b, c)
+    with capi.Solver(inst) as s:
+        s.solve(tol=0.0, max_iter=7)
+        _, x, y, z, _, res = s.get()
+        pst, info = s.polish()
+        _, xp, yp, zp, _, res2 = s.get()
+    assert not X.support(x, z).any() and (z - x).min() > 0.01
+    assert pst == capi.SOLVED and info[0] == 0 and info[5] == 1.0
+    assert (xp == 0.0).all()
+    np.testing.assert_array_equal(yp, y)
+    xo, yo, zo, B = X.polish(A, b, c, x, y, z)
+    assert not B.any()
+    _close(zp, zo, 1e-12)
+    assert max(res2[:4]) <= 1e-13 < max(res[:4])
