@@ -485,6 +485,19 @@ def polish_bytes(m: int, n: int, nnz: int, corrections: int, attempts: int, supp
     return corrections * per_cg + attempts * (10 * per_support_pass + 4 * per_full_pass)
 
 
+def pinned_copy(a, keep: list):
+    """A copy of the numpy array a in page-locked host memory: the numpy view
+    of a pinned torch buffer, which is appended to keep (the view's owner)."""
+    import numpy as np
+    import torch
+    a = np.ascontiguousarray(a)
+    t = torch.empty(a.shape, dtype=getattr(torch, a.dtype.name), pin_memory=True)
+    keep.append(t)
+    v = t.numpy()
+    v[...] = a
+    return v
+
+
 def solver_overrides(args) -> dict:
     """Settings chosen on the command line (precision mode, column blocks,
     crossover polish)."""
@@ -659,30 +672,39 @@ def gpu_arm(args) -> None:
     # solve, read back x, y, s
     e2e = None
     if not args.no_e2e:
+        # the step's inputs sit in page-locked host memory (filled once, before
+        # the timed region), so that the create step's uploads are DMA copies
+        keep = []
+        row_ptr_h, col_h, val_h, b_h, c_h = (pinned_copy(a, keep) for a in
+                                             (inst.row_ptr, inst.col, inst.val, inst.b, inst.c))
         torch.cuda.synchronize()
         t_e2e = 0.0
-        for k in range(args.steps):
+        # W untimed steps first, as in the device-timed loop: the first create
+        # takes its buffers from cudaMalloc, later ones from the device cache
+        for k in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            h2 = capi.acs_problem_create(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.b,
-                                         inst.c, inst.n_orth, inst.soc_dims,
+            h2 = capi.acs_problem_create(inst.m, inst.n, row_ptr_h, col_h, val_h, b_h,
+                                         c_h, inst.n_orth, inst.soc_dims,
                                          capi.acs_settings_default(device=local, **wl["settings"],
                                                                    **solver_overrides(args)))
             st2 = capi.acs_solve(h2, TOL, MAX_ITER)
             out = capi.acs_get(h2, inst.m, inst.n)
             capi.acs_problem_destroy(h2)
-            t_e2e += time.perf_counter() - t0
+            if k >= args.warmup:
+                t_e2e += time.perf_counter() - t0
             if st2 != capi.SOLVED:
                 raise RuntimeError("e2e solve did not converge")
-        # the create step uploads the CSR's columns and values (the images of A
-        # and A' are built on the device), each relabelled row's start and
-        # length, the column offsets of A', slice tables, b, c, cone offsets;
-        # it reads back the column counts of A'
-        h2d = 12 * inst.nnz + 12 * inst.m + 8 * (inst.n + 1) + 8 * (inst.m + inst.n)
-        h2d += 4 * (len(inst.soc_dims) + 1) + 4 * ((inst.m + inst.n) // 8 + 4)   # slice tables (upper bound)
-        d2h = 8 * (2 * inst.n + inst.m) + 4 * inst.n + 256
+        # the bytes the create step copied, as the library counted them (the
+        # CSR's columns and values, each relabelled row's start and length,
+        # slice tables, cone offsets, b, c; read back: A''s slice table and
+        # three counts), and x, y, s read back after the solve
+        h2d = layout["create_h2d_bytes"]
+        d2h = layout["create_d2h_bytes"] + 8 * (2 * inst.n + inst.m)
         t_e2e = max_over_ranks(t_e2e, pg, "cuda")
         e2e = {"value": replica_throughput(world, args.steps, t_e2e), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "inputs": "pinned host memory",
+               "not_counted": "the solve's status and counter record (about 0.5 KB), read about three "
+                              "times and written once per solve segment"}
     capi.acs_problem_destroy(h)
 
     cpu = oracle_baseline(args.workload, args, rank, world, iters)

@@ -397,7 +397,10 @@ int acs_debug_cbsell(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
  * acs_debug_layout: out[10] = {column-blocked layout in use, blocks of A,
  * width, stored entries, blocks of A', width, stored entries, dynamic shared
  * memory of the FP32 launch (bytes), stored entries of the sliced-ELLPACK A
- * and A'}; n >= 10.  Both return the number of values written or an error. */
+ * and A'}; n >= 10; with n >= 12 also {slices of the sliced-ELLPACK A, of A'};
+ * with n >= 14 also {bytes acs_problem_create copied host -> device, device ->
+ * host}.
+ * Both return the number of values written or an error. */
 int acs_debug_pass_counts(acs_problem* p, int64_t* out, int32_t n);
 int acs_debug_layout(acs_problem* p, int64_t* out, int32_t n);
 

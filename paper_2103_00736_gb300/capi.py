@@ -910,7 +910,8 @@ def acs_debug_pass_counts(h) -> dict:
 
 
 LAYOUT = ("col_blocked", "A_blocks", "A_width", "A_stored", "At_blocks", "At_width", "At_stored",
-          "dyn_smem", "sell_A_stored", "sell_At_stored")
+          "dyn_smem", "sell_A_stored", "sell_At_stored", "sell_A_slices", "sell_At_slices",
+          "create_h2d_bytes", "create_d2h_bytes")
 
 
 def acs_debug_layout(h) -> dict:

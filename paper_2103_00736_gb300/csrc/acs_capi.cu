@@ -35,6 +35,7 @@ int upload(Problem* P, T* dst, const T* src, size_t count) {
     if (count == 0) return ACS_SOLVED;
     if (cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
         return ACS_ERR_CUDA;
+    P->h2d_bytes += (long long)(count * sizeof(T));
     return ACS_SOLVED;
 }
 
@@ -465,6 +466,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         } catch (...) {
             drc = ACS_ERR_OOM;
         }
+        step("device build");
         if (drc == ACS_SOLVED) {
             if (adopt_device_sell(P, m, gA, D.sptrA, D.slenA, D.colA, D.valA, D.totA, P->A) ||
                 adopt_device_sell(P, n, gAT, D.sptrT, D.slenT, D.colT, D.valT, D.totT, P->AT)) {
@@ -476,7 +478,7 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
         } else if (drc != 1) {
             free_all(P); delete P; return drc;
         }
-        step("device build");
+        step("narrow copies");
     }
     if (!on_device) {
         const int brc = acs::host::no_throw([&] {
@@ -575,6 +577,8 @@ int acs_problem_create(int32_t m, int32_t n, const int64_t* row_ptr, const int32
     if (rc || cudaStreamSynchronize(P->stream) != cudaSuccess) { free_all(P); delete P; return ACS_ERR_CUDA; }
     if (P->grid32 > P->max_ctas || P->grid64 > P->max_ctas || P->grid32 > 256 || P->grid64 > 256) { free_all(P); delete P; return ACS_ERR_CUDA; }
     step("finish");
+    P->create_h2d = P->h2d_bytes;
+    P->create_d2h = P->d2h_bytes;
     *out = reinterpret_cast<acs_problem*>(P);
     return ACS_SOLVED;
 }
@@ -795,7 +799,11 @@ int acs_debug_layout(acs_problem* h, int64_t* out, int32_t n) {
     out[1] = P->Acb.nblocks; out[2] = P->Acb.width; out[3] = P->padded_Acb;
     out[4] = P->ATcb.nblocks; out[5] = P->ATcb.width; out[6] = P->padded_ATcb;
     out[7] = P->cb_smem; out[8] = P->padded_A; out[9] = P->padded_AT;
-    return 10;
+    if (n < 12) return 10;
+    out[10] = P->A.nslices; out[11] = P->AT.nslices;
+    if (n < 14) return 12;
+    out[12] = P->create_h2d; out[13] = P->create_d2h;
+    return 14;
 }
 
 int acs_debug_to_bf16(int64_t n, const double* v, uint16_t* out) {

@@ -219,6 +219,11 @@ struct Problem {
     double* bval = nullptr;
     float* bval32 = nullptr;                  // A_B's FP32 values (FP32 polish corrections)
     long long padded_B = 0;
+    // bytes copied host -> device and device -> host: running counts of the
+    // uploads and of the device build's copies, and their values when
+    // acs_problem_create returned
+    long long h2d_bytes = 0, d2h_bytes = 0;
+    long long create_h2d = 0, create_d2h = 0;
     double* psaveO = nullptr;                 // the scaling O, the multiplier w and the iterate's
     double* psaveW = nullptr;                 //   x, z kept across a polish of a polished solve
     double *psaveX = nullptr, *psaveZ = nullptr;
